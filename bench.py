@@ -1,0 +1,303 @@
+"""Benchmark of the FP64 GKS S2O4 step (hybrid DF + WENO-AO reconstruction) on GB300.
+
+Default workload: the seeded four-quadrant Riemann problem on a 400 x 400 mesh of [0,1]^2,
+GKS flux, time limiter on, outflow boundaries, CFL 0.5 (seed 2).  One benchmark "step" is one
+full S2O4 step of Algorithm 1 (CFL dt, ghost fill, two stages of sweeps + update), i.e. two
+cell-stage updates per cell.  Metric: FP64 cell-stage updates per second.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun every rank advances its own replica of the
+workload (independent problems, weak scaling); the timed region is bracketed by a barrier and
+a device synchronisation and the maximum time over ranks is used.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FP64 cell-stage updates/s (GKS S2O4 step, four-quadrant 400x400)"
+UNIT = "cell-stage/s"
+WORKLOAD = "quadrants_400x400_gks_seed2"
+
+# FP64 roofline denominator of this GPU: 152 SMs x 2 FP64 FMA units per SM per clock x 2 flops
+# x 2070 MHz maximum SM clock = 1258.6 GFLOP/s (the recipe's nominal 1.25 TFLOP/s FP64 rate).
+FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
+
+# FP64 flops the Gauss-point flux kernel executes per Gauss point (GKS, time-limited S2O4
+# settings), from ncu instruction counts 2*DFMA + DADD + DMUL of one launch divided by its Gauss
+# points (profiles/k_flux_gks_counts.txt).  None until measured.
+FLUX_GKS_FLOPS_PER_GP = None
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=40)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--n", type=int, default=400, help="mesh side of the four-quadrant workload")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    return p.parse_args()
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if os.environ.get("DFGKS_BENCH_GLOO") is None else "gloo")
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for k, name in enumerate(names):
+                if f[5 + k].lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def bench_ours(args, ws, rank, local):
+    import torch
+    from paper_2402_10914_gb300 import inputs as I
+    from paper_2402_10914_gb300.solver import Solver
+
+    torch.cuda.set_device(local)
+    w = I.quadrants(args.n, seed=2)
+    s = w.settings
+    cells = s.nx * s.ny
+    sol = Solver(s)
+    sol.set_ic(w.W0)
+    stream = sol.stream
+    flush = torch.empty(32 * 1024 * 1024, dtype=torch.float64, device="cuda")   # 256 MiB > 129 MB L2
+    # warm-up steps (untimed)
+    sol.step(args.warmup)
+    sol.set_timing(True)
+    sol.timing(reset=True)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(float(k))                     # evict the previous step's working set from L2
+        starts[k].record(stream)
+        done, _ = sol.step(1)
+        ends[k].record(stream)
+        assert done == 1
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if ws > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    total_ms = sum(step_ms)
+    if ws > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    timing = sol.timing()
+    sol.set_timing(False)
+    launches = sum(v["launches"] for v in timing.values())
+    units = 2.0 * cells * args.steps * ws            # cell-stages processed by all ranks
+    value = units / (total_ms * 1e-3)
+
+    # roofline of the dominant kernel (the Gauss-point flux kernel)
+    share = {k: v["ms"] for k, v in timing.items()}
+    dominant = max(share, key=share.get)
+    fl = timing["flux"]
+    avg_flux_ms = fl["ms"] / max(fl["timed"], 1)
+    gps_per_launch = 2.0 * (s.nx + 1) * s.ny       # x- and y-sweeps have the same count on a square mesh
+    roof = {"kernel": "k_flux<GKS> (Gauss-point flux)", "bound": "alu", "unit": "GFLOP/s",
+            "peak": round(FP64_PEAK_GFLOPS, 1), "peak_source": "derived: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz",
+            "avg_launch_ms": avg_flux_ms, "launches_timed": fl["timed"], "traffic": None,
+            "kernel_time_share": {k: round(v / max(sum(share.values()), 1e-30), 4) for k, v in share.items()},
+            "dominant_kernel_class": dominant}
+    if FLUX_GKS_FLOPS_PER_GP is not None:
+        achieved = FLUX_GKS_FLOPS_PER_GP * gps_per_launch / (avg_flux_ms * 1e-3) / 1e9
+        roof.update({"achieved": round(achieved, 2), "frac": round(achieved / FP64_PEAK_GFLOPS, 4),
+                     "flops_per_unit": FLUX_GKS_FLOPS_PER_GP, "unit_of_work": "Gauss point",
+                     "units_per_launch": gps_per_launch})
+    else:
+        roof.update({"achieved": None, "frac": None})
+    # FP64 probe as a cross-check of the denominator
+    try:
+        import ctypes
+        from paper_2402_10914_gb300 import _lib
+        g, ms = ctypes.c_double(), ctypes.c_double()
+        if _lib.lib().dfgks_probe_fp64(4000, ctypes.byref(g), ctypes.byref(ms)) == 0:
+            roof["fp64_probe_gflops"] = round(g.value, 1)
+    except Exception:
+        pass
+
+    # end to end through the C ABI with host buffers: H2D of the step's inputs from pinned memory,
+    # the step, D2H of the result, every step
+    e2e = None
+    if not args.no_e2e:
+        Wh = torch.empty((4, s.ny, s.nx), dtype=torch.float64, pin_memory=True).numpy()
+        ah = torch.empty((s.ny, s.nx), dtype=torch.float64, pin_memory=True).numpy()
+        W0, a0, t0, st0 = sol.get_state()
+        Wh[...] = W0
+        ah[...] = a0
+        ke = max(5, min(args.steps, 20))
+        torch.cuda.synchronize()
+        e0 = time.perf_counter()
+        t_cur, step_cur = t0, st0
+        for k in range(ke):
+            sol.set_state(Wh, ah, t_cur, step_cur)
+            sol.step(1)
+            Wr, ar, t_cur, step_cur = sol.get_state()
+            Wh[...] = Wr
+            ah[...] = ar
+        torch.cuda.synchronize()
+        e_ms = (time.perf_counter() - e0) * 1e3
+        nbytes = Wh.nbytes + ah.nbytes
+        e2e = {"value": 2.0 * cells * ke / (e_ms * 1e-3) * ws, "unit": UNIT, "steps": ke,
+               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
+    counters = sol.counters()
+    sol.close()
+    return {
+        "value": value, "ms_per_step": total_ms / args.steps, "wall_s": wall, "launches": launches,
+        "roofline": roof, "e2e": e2e, "clocks": clk, "counters": counters, "step_ms": step_ms,
+        "per_kernel_ms_per_step": {k: v["ms"] / args.steps for k, v in timing.items()},
+    }
+
+
+def oracle_sample(n_threads=None, steps=1, n=400):
+    """The CPU oracle as it stands on one full S2O4 step of the same workload."""
+    import oracle
+    from paper_2402_10914_gb300 import inputs as I
+    w = I.quadrants(n, seed=2)
+    if n_threads:
+        oracle.set_threads(n_threads)
+    cores = oracle.max_threads()
+    a0 = oracle.alpha0(w.settings, w.W0)
+    t0 = time.perf_counter()
+    rc, W, a, t, dts, st = oracle.run(w.settings, w.W0, a0, steps)
+    dtw = time.perf_counter() - t0
+    assert rc == 0
+    return 2.0 * n * n * steps / dtw, cores, dtw
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_init()
+    if args.impl == "reference":
+        # the reference arm is the CPU oracle, rank 0 only
+        if rank != 0:
+            return
+        import oracle
+        oracle.build()
+        cores = oracle.max_threads()
+        for _ in range(args.warmup):
+            oracle_sample(steps=1, n=args.n)
+        times = []
+        for _ in range(args.steps):
+            v, cores, dtw = oracle_sample(steps=1, n=args.n)
+            times.append(dtw)
+        total = sum(times)
+        value = 2.0 * args.n * args.n * args.steps / total
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+                "config": {"workload": WORKLOAD, "nx": args.n, "ny": args.n, "flux": "GKS", "time_limiter": 1,
+                           "cfl": 0.5, "bc": "outflow", "seed": 2},
+                "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                 "sample": "one full S2O4 step of the %dx%d workload per benchmark step" % (args.n, args.n)},
+                "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import __graft_entry__
+    __graft_entry__.build()
+    r = bench_ours(args, ws, rank, local)
+    if rank != 0:
+        return
+    cpu = None
+    if not args.no_cpu:
+        try:
+            v, cores, dtw = oracle_sample(steps=1, n=args.n)
+            cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                   "sample": "one full S2O4 step of the %dx%d workload (%.1f s)" % (args.n, args.n, dtw)}
+        except Exception as e:  # the benchmark line must still be printed
+            cpu = {"value": None, "unit": UNIT, "cores": None, "kind": "oracle", "sample": "failed: %s" % e}
+    line = {
+        "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nx": args.n, "ny": args.n, "flux": "GKS", "time_limiter": 1, "cfl": 0.5,
+                   "bc": "outflow", "seed": 2, "l2": "flushed before every timed step (256 MiB write)",
+                   "parallelism": "replica per GPU" if ws > 1 else "single GPU"},
+        "roofline": r["roofline"], "cpu_baseline": cpu, "e2e": r["e2e"], "gpu_launches": r["launches"],
+        "clocks": r["clocks"], "per_kernel_ms_per_step": r["per_kernel_ms_per_step"], "counters": r["counters"],
+    }
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,176 @@
+/*
+ * dfgks.h -- C ABI of the GB300 (sm_103a) FP64 solver for the hybrid DF + WENO-AO
+ * high-order finite-volume scheme of Zhang, Ji & Xu, "A robustness-enhanced reconstruction
+ * based on discontinuity feedback factor for high-order finite volume scheme"
+ * (arXiv 2402.10914).
+ *
+ * One handle = one 2-D structured-mesh Euler problem on one GPU and one CUDA stream.
+ * Every call returns a dfgks_status; nothing throws or aborts across this boundary.
+ *
+ * Conventions used throughout:
+ *   - All floating-point data is IEEE binary64 (double).
+ *   - Conserved variables W = (rho, rho U, rho V, rho E) (Sect. 2.1) are stored SoA as
+ *     [4][ny][nx], row-major, x fastest, interior cells only (no ghost layers).  Component k of
+ *     cell (i, j) is W[k*nx*ny + j*nx + i].
+ *   - The discontinuity feedback factor alpha (Sect. 3.2) is stored [ny][nx] the same way.
+ *   - Pointer arguments are borrowed for the duration of the call.  "device" pointers must be
+ *     CUDA device (or managed) memory of the current device; work is ordered on the handle's
+ *     stream, and calls that return data to host memory synchronise that stream.
+ *   - A handle is not thread-safe; use one handle per stream.
+ *   - Cell (i, j) has centre (x0 + (i+1/2) dx, y0 + (j+1/2) dy), dx = (x1-x0)/nx, dy = (y1-y0)/ny.
+ */
+#ifndef DFGKS_H
+#define DFGKS_H
+
+#if defined(__GNUC__)
+#define DFGKS_API __attribute__((visibility("default")))
+#else
+#define DFGKS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DFGKS_OK = 0,
+    DFGKS_EINVAL = 1,      /* bad argument: null handle/pointer, size out of range, unknown enum */
+    DFGKS_ENOMEM = 2,      /* a device or pinned allocation failed */
+    DFGKS_ECUDA = 3,       /* a CUDA runtime call failed; the handle should be destroyed */
+    DFGKS_ENONPHYS = 4,    /* initial/state data with rho <= 0, p <= 0 or a non-finite value */
+    DFGKS_ENONPOS = 5,     /* positivity (rho > 0, p > 0, finite) lost during a step */
+    DFGKS_ENAN = 6,        /* reserved: non-finite value outside the positivity check */
+    DFGKS_ETIMEOUT = 7,    /* a bounded device-side wait expired (batched persistent launch) */
+    DFGKS_ENOTSUP = 8      /* the requested combination is not implemented */
+} dfgks_status;
+
+typedef enum { DFGKS_FLUX_GKS = 0, DFGKS_FLUX_LF = 1 } dfgks_flux;
+
+/* Boundary conditions: periodic wrap; outflow = zero-gradient copy (the paper's "free" and
+ * "non-reflecting" boundaries, Sect. 4.3); reflecting wall = mirror with negated normal momentum. */
+typedef enum { DFGKS_BC_PERIODIC = 0, DFGKS_BC_OUTFLOW = 1, DFGKS_BC_REFLECT = 2 } dfgks_bc;
+
+typedef enum { DFGKS_TIME_S2O4 = 0, DFGKS_TIME_SSPRK3 = 1 } dfgks_time_scheme;
+
+typedef struct dfgks_config {
+    int nx, ny;                    /* interior cells, each >= 1 (>= 3 along a periodic direction) */
+    double x0, x1, y0, y1;         /* domain [x0,x1] x [y0,y1] */
+    double gamma;                  /* specific heat ratio; K = (4 - 2 gamma)/(gamma - 1) (Sect. 2.2) */
+    double cfl;                    /* dt = cfl * min over cells of min(dx/(|U|+c), dy/(|V|+c)) */
+    int bc_xlo, bc_xhi, bc_ylo, bc_yhi;   /* dfgks_bc */
+    double alpha_thres;            /* DF threshold of Eq. 34 (paper: 0.5) */
+    double dH, dL;                 /* WENO-AO linear-weight parameters (paper: 0.85, 0.85) */
+    double eps;                    /* WENO-Z and time-limiter epsilon (paper: 1e-6) */
+    double C1, C2;                 /* numerical collision time tau_n = C1 dt + C2 |dp/sum p| dt (0.01, 5) */
+    int time_limiter;              /* 1: S2O4 with the non-linear time limiter (Sect. 2.2) */
+    int tau_reading;               /* 0: physical tau = 0 outside the exponentials; 1: tau = tau_n */
+    int gp_fallback;               /* 1: Gauss-point states with rho <= 0 or p <= 0 use the cell average */
+    int time_scheme;               /* dfgks_time_scheme */
+} dfgks_config;
+
+typedef struct dfgks dfgks;        /* opaque; owns every device buffer it uses */
+
+/* Counters accumulated since the last dfgks_set_ic / dfgks_set_state. */
+typedef struct dfgks_counters {
+    unsigned long long fallbacks;      /* Gauss-point side states replaced by the cell average */
+    unsigned long long df_normal;      /* normal reconstructions (per face line side) on the DF branch */
+    unsigned long long df_tangential;  /* tangential reconstructions (per face side) on the DF branch */
+} dfgks_counters;
+
+/* Human-readable name of a status code (static storage). */
+DFGKS_API const char* dfgks_status_string(int status);
+
+/* Fill *cfg with the paper's constants (Sect. 2.2, 3.1, 3.3) for an nx x ny mesh on [0,1]^2 with
+ * outflow boundaries, gamma 1.4, CFL 0.5, S2O4 with the time limiter, tau reading 0, fallback on. */
+DFGKS_API dfgks_status dfgks_config_default(dfgks_config* cfg, int nx, int ny);
+
+/* Create a solver for cfg on the current CUDA device.  stream: a cudaStream_t to order all work
+ * on, or NULL to create a private non-blocking stream.  Allocates every device buffer the step
+ * needs (about 140 doubles per cell for the default path).  On success *out owns them. */
+DFGKS_API dfgks_status dfgks_create(const dfgks_config* cfg, void* stream, dfgks** out);
+
+/* Release every buffer and the private stream, if any.  Accepts NULL. */
+DFGKS_API dfgks_status dfgks_destroy(dfgks* h);
+
+/* Load the initial cell averages W [4][ny][nx] (host memory if on_device == 0, else device),
+ * set t = 0, step = 0, reset the counters, and compute alpha^0 as the product of the Gauss-point
+ * DF factors (Sect. 3.2) of a reconstruction of W with alpha = 1 (the paper leaves alpha^0 open).
+ * Returns DFGKS_ENONPHYS (state unchanged) if any cell has rho <= 0, p <= 0 or a non-finite value. */
+DFGKS_API dfgks_status dfgks_set_ic(dfgks* h, const double* W, int on_device);
+
+/* Copy out the current state.  W [4][ny][nx] and alpha [ny][nx] may each be NULL; they are host
+ * memory if on_device == 0, else device.  t and step may be NULL.  Synchronises the stream. */
+DFGKS_API dfgks_status dfgks_get_state(dfgks* h, double* W, double* alpha, double* t, long* step, int on_device);
+
+/* Replace the current state (checkpoint resume).  alpha may be NULL (then alpha^0 is recomputed
+ * as in dfgks_set_ic).  Returns DFGKS_ENONPHYS on non-physical W, leaving the state unchanged. */
+DFGKS_API dfgks_status dfgks_set_state(dfgks* h, const double* W, const double* alpha, double t, long step, int on_device);
+
+/* Algorithm 1, repeated: advance up to n steps with flux solver `flux`.
+ *   dt > 0: fixed step; dt <= 0: the CFL rule of dfgks_config.cfl, from W^n, every step.
+ *   t_end > 0: the step that would pass t_end is clipped to end exactly there (a remainder below
+ *   1e-12 |t_end| is absorbed) and no further steps are taken; t_end <= 0: no limit.
+ * Each step: dt (device-resident), ghost fill, then per stage the fused reconstruction + flux
+ * sweeps and the stage update (S2O4, Eq. 24 with the time limiter; or SSP-RK3, Sect. 2.3);
+ * alpha^{n+1} is the product of the DF factors at the last stage's Gauss points.
+ * dts_out (host, length n) receives each executed step's dt, may be NULL; *steps_done (may be
+ * NULL) receives the number of steps executed.  Synchronises the stream once, at the end.
+ * On a positivity failure returns DFGKS_ENONPOS with the state left at the last good step;
+ * dfgks_last_error_detail gives the failing step and cell. */
+DFGKS_API dfgks_status dfgks_step(dfgks* h, int n, double dt, int flux, double t_end, double* dts_out, int* steps_done);
+
+/* Single-stage operator of Eq. 2 with two-point Gauss quadrature (Sect. 2.1, 2.2, 3): from device
+ * W [4][ny][nx] and alpha [ny][nx], with ghosts filled by the handle's boundary conditions, write
+ * to device memory L = L(W), dtL = dL/dt (Eq. 27 summed as in Eq. 2), dtLt = the time-limited
+ * dL/dt (omega^t applied per face, Sect. 2.2), alpha_next = product of the Gauss-point DF factors.
+ * Any output may be NULL.  The GKS flux depends on dt through tau_n and the time integrals
+ * (Eqs. 25-27); L-F ignores dt.  Does not touch the handle's state. Asynchronous on the stream. */
+DFGKS_API dfgks_status dfgks_residual(dfgks* h, const double* W, const double* alpha, double dt, int flux,
+                            double* L, double* dtL, double* dtLt, double* alpha_next);
+
+/* Vector-Jacobian product of dfgks_residual with respect to W, with alpha, dt and every branch
+ * decision (DF switch, fallback, |.| and min/max kinks) held at the values of the forward pass:
+ *   W_bar += (dL/dW)^T L_bar + (d dtL/dW)^T dtL_bar + (d dtLt/dW)^T dtLt_bar.
+ * All pointers device; L_bar / dtL_bar / dtLt_bar may be NULL (treated as zero).  Not part of the
+ * paper (a hand-written reverse sweep of the same operator).  Asynchronous on the stream. */
+DFGKS_API dfgks_status dfgks_adjoint_residual(dfgks* h, const double* W, const double* alpha, double dt, int flux,
+                                    const double* L_bar, const double* dtL_bar, const double* dtLt_bar,
+                                    double* W_bar);
+
+/* Per-face intermediates of one stage, for diagnostics and kernel-by-kernel comparison.
+ * dir 0: x-faces, [ny][nx+1] (face index fastest); dir 1: y-faces, [nx][ny+1].
+ * Per face 59 doubles: F[4], dtF[4] (global frame, Gauss-averaged), omega^t, alpha_{p,1},
+ * alpha_{p,2}, then for side (left, right) x Gauss point (1, 2): W[4], W_n[4], W_t[4] in the
+ * face's local frame (Sect. 2.1).  W, alpha device; out is device memory of nfaces*59 doubles. */
+DFGKS_API dfgks_status dfgks_face_records(dfgks* h, const double* W, const double* alpha, double dt, int flux,
+                                int dir, double* out);
+
+/* Counters since the last set_ic/set_state (synchronises the stream). */
+DFGKS_API dfgks_status dfgks_get_counters(dfgks* h, dfgks_counters* out);
+
+/* Step index and cell of the first positivity failure reported by dfgks_step (-1 if none). */
+DFGKS_API dfgks_status dfgks_last_error_detail(dfgks* h, long* step, int* i, int* j);
+
+/* Per-kernel-class timing for profiling.  Classes, in order: 0 face-line normal reconstruction,
+ * 1 tangential reconstruction, 2 Gauss-point flux, 3 stage update, 4 other (ghost fill, dt,
+ * bookkeeping).  When enabled, dfgks_step records a CUDA event pair on the handle's stream around
+ * each launch of a class; kernels themselves are unchanged.  Synchronises the stream. */
+DFGKS_API dfgks_status dfgks_set_timing(dfgks* h, int enable);
+
+/* Accumulated event time (ms), number of timed launches and number of kernel launches issued by
+ * dfgks_step, per class (arrays of 5; each may be NULL).  reset != 0 clears the accumulators.
+ * Synchronises the stream. */
+DFGKS_API dfgks_status dfgks_get_timing(dfgks* h, double* total_ms, long long* timed, long long* launches, int reset);
+
+/* FP64 throughput probe on the current device: independent fused multiply-add chains (8 per
+ * thread, `iters` iterations, 8 blocks of 256 threads per SM), timed with CUDA events.  Writes the
+ * achieved GFLOP/s (2 per FMA) and the kernel time in ms (may be NULL).  Allocates 512 KiB. */
+DFGKS_API dfgks_status dfgks_probe_fp64(int iters, double* gflops, double* ms);
+
+/* Device bytes held by the handle. */
+DFGKS_API dfgks_status dfgks_device_bytes(dfgks* h, unsigned long long* bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DFGKS_H */

@@ -1,0 +1,456 @@
+// dfgks_device.cuh -- FP64 device arithmetic of the hybrid DF + WENO-AO finite-volume scheme
+// (Zhang, Ji & Xu, arXiv 2402.10914) for sm_103a.  Every routine works on one face line, one
+// face side or one Gauss point in that face's local frame (Sect. 2.1); the kernels in
+// dfgks_kernels.cu move data between them.
+//
+// Arithmetic choices (each algebraically identical to the paper's formulas):
+//   * characteristic projection L W and back-projection R Q in factored form (12 + 14 flops
+//     instead of two 4x4 products);
+//   * WENO-AO sub-stencil polynomials kept as cell-centred coefficients a1..a4 (the cell mean
+//     fixes a0), so smoothness indicators (Eq. 38) and every evaluation point share them;
+//   * S2O4 flux coefficients (Eq. 27) combined analytically per kinetic term before the moments
+//     are summed, using E(dt) = E(dt/2)^2, which avoids the cancellation of 4(F(dt)-2F(dt/2));
+//   * the GKS slope system <a psi> = b (Sect. 2.2) solved in closed form.
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+
+namespace dfk {
+
+constexpr int G = 3;                       // ghost layers: the normal stencil spans i-3 .. i+2
+constexpr double kGaussEta = 0.28867513459481288225;   // sqrt(3)/6: Gauss points at eta = -/+ this
+
+struct SchemeConsts {
+    double gamma, gm1, K;                  // gamma, gamma-1, internal degrees of freedom
+    double d[4];                           // WENO-AO linear weights d0..d3 (Sect. 3.1)
+    double inv_d3;
+    double eps, alpha_thres, C1, C2;
+    int time_limiter, tau_reading, gp_fallback;
+};
+
+// ------------------------------------------------------------------------------------------
+// Euler state helpers
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ double pressure_of(const double W[4], double gm1) {
+    return gm1 * (W[3] - 0.5 * (W[1] * W[1] + W[2] * W[2]) / W[0]);
+}
+
+// rotate a global-frame state into the local frame of a y-face (theta = pi/2): (rho, rhoV, -rhoU, rhoE)
+template <int DIR>
+__device__ __forceinline__ void to_local(double W[4]) {
+    if (DIR == 1) { double m = W[1]; W[1] = W[2]; W[2] = -m; }
+}
+// local-frame flux back to the global frame, F = T^{-1} F~
+template <int DIR>
+__device__ __forceinline__ void to_global(double F[4]) {
+    if (DIR == 1) { double a = F[1]; F[1] = -F[2]; F[2] = a; }
+}
+
+// ------------------------------------------------------------------------------------------
+// Characteristic basis of the local-frame x-direction Euler Jacobian at W = (W_l + W_r)/2
+// ------------------------------------------------------------------------------------------
+struct CharBasis { double u, v, c, ic, H, b1, b2, q2; };
+
+__device__ __forceinline__ CharBasis make_basis(const double Wl[4], const double Wr[4], const SchemeConsts& S) {
+    CharBasis B;
+    double r = 0.5 * (Wl[0] + Wr[0]), m = 0.5 * (Wl[1] + Wr[1]);
+    double n = 0.5 * (Wl[2] + Wr[2]), E = 0.5 * (Wl[3] + Wr[3]);
+    double ir = 1.0 / r;
+    B.u = m * ir;
+    B.v = n * ir;
+    B.q2 = 0.5 * (B.u * B.u + B.v * B.v);
+    double p = S.gm1 * (E - r * B.q2);
+    B.c = sqrt(S.gamma * p * ir);
+    B.ic = 1.0 / B.c;
+    B.H = (E + p) * ir;
+    B.b1 = S.gm1 * B.ic * B.ic;
+    B.b2 = B.q2 * B.b1;
+    return B;
+}
+
+// Q = L W; components ordered by eigenvalue u-c, u (entropy), u (shear), u+c
+__device__ __forceinline__ void project(const CharBasis& B, const double W[4], double Q[4]) {
+    double t = B.b1 * (B.u * W[1] + B.v * W[2] - W[3]);
+    double k = B.b2 * W[0] - t;
+    double m = (B.u * W[0] - W[1]) * B.ic;
+    Q[0] = 0.5 * (k + m);
+    Q[1] = W[0] - k;
+    Q[2] = W[2] - B.v * W[0];
+    Q[3] = 0.5 * (k - m);
+}
+
+// W = R Q
+__device__ __forceinline__ void back_project(const CharBasis& B, const double Q[4], double W[4]) {
+    double s = Q[0] + Q[3], d = Q[3] - Q[0];
+    W[0] = s + Q[1];
+    W[1] = B.u * W[0] + B.c * d;
+    W[2] = B.v * W[0] + Q[2];
+    W[3] = B.H * s + B.u * B.c * d + B.q2 * Q[1] + B.v * Q[2];
+}
+
+// ------------------------------------------------------------------------------------------
+// WENO-AO(5,3) of Sect. 3.1 on Q_{-2..2} (cell-centred xi in [-1/2, 1/2] of the centre cell).
+// Each sub-stencil polynomial is written p_k = Q_0 + a1 xi + a2 (xi^2 - 1/12) (+ a3 xi^3 + a4 (xi^4 - 1/80)
+// for the quartic), so its cell mean is Q_0 by construction.  The AO polynomial P = sum c_k p_k with
+// c3 = wb3/d3 and c_k = wb_k - c3 d_k sums to one, so P = Q_0 + A1 xi + A2 (xi^2-1/12) + c3 (a3 xi^3 + a4 (xi^4-1/80)).
+// ------------------------------------------------------------------------------------------
+struct AO {
+    double A1, A2;          // sum_k c_k a1_k, sum_k c_k a2_k
+    double c3a3, c3a4;      // c3 * a3, c3 * a4 of the quartic
+    double bmin, bmax, tauZ;  // for the time limiter
+};
+
+__device__ __forceinline__ AO weno_ao(const double q[5], const SchemeConsts& S, bool want_limiter) {
+    const double qm2 = q[0], qm1 = q[1], q0 = q[2], q1 = q[3], q2 = q[4];
+    // quadratic sub-stencils {i-2,i-1,i}, {i-1,i,i+1}, {i,i+1,i+2}
+    double a1_0 = 0.5 * qm2 - 2.0 * qm1 + 1.5 * q0;
+    double a2_0 = 0.5 * (qm2 - 2.0 * qm1 + q0);
+    double a1_1 = 0.5 * (q1 - qm1);
+    double a2_1 = 0.5 * (qm1 - 2.0 * q0 + q1);
+    double a1_2 = -1.5 * q0 + 2.0 * q1 - 0.5 * q2;
+    double a2_2 = 0.5 * (q0 - 2.0 * q1 + q2);
+    // quartic on the full stencil
+    double a1_3 = (5.0 * (qm2 - q2) - 34.0 * (qm1 - q1)) * (1.0 / 48.0);
+    double a2_3 = (-(qm2 + q2) + 12.0 * (qm1 + q1) - 22.0 * q0) * (1.0 / 16.0);
+    double a3_3 = (-(qm2 - q2) + 2.0 * (qm1 - q1)) * (1.0 / 12.0);
+    double a4_3 = ((qm2 + q2) - 4.0 * (qm1 + q1) + 6.0 * q0) * (1.0 / 24.0);
+    // smoothness indicators, Eq. 38 with dx^{2q-1} absorbed into the cell-centred coordinate
+    const double c13_3 = 13.0 / 3.0;
+    double b0 = a1_0 * a1_0 + c13_3 * a2_0 * a2_0;
+    double b1 = a1_1 * a1_1 + c13_3 * a2_1 * a2_1;
+    double b2 = a1_2 * a1_2 + c13_3 * a2_2 * a2_2;
+    double b3 = a1_3 * (a1_3 + 0.5 * a3_3) + c13_3 * a2_3 * a2_3 + (21.0 / 5.0) * a2_3 * a4_3
+              + (3129.0 / 80.0) * a3_3 * a3_3 + (87617.0 / 140.0) * a4_3 * a4_3;
+    // Eq. 37 and the WENO-Z weights
+    double tau = (fabs(b3 - b0) + fabs(b3 - b1) + fabs(b3 - b2)) * (1.0 / 3.0);
+    double r0 = tau / (b0 + S.eps), r1 = tau / (b1 + S.eps), r2 = tau / (b2 + S.eps), r3 = tau / (b3 + S.eps);
+    double w0 = S.d[0] * (1.0 + r0 * r0), w1 = S.d[1] * (1.0 + r1 * r1);
+    double w2 = S.d[2] * (1.0 + r2 * r2), w3 = S.d[3] * (1.0 + r3 * r3);
+    double iw = 1.0 / (w0 + w1 + w2 + w3);
+    double c3 = w3 * iw * S.inv_d3;
+    double c0 = w0 * iw - c3 * S.d[0], c1 = w1 * iw - c3 * S.d[1], c2 = w2 * iw - c3 * S.d[2];
+    AO o;
+    o.A1 = c0 * a1_0 + c1 * a1_1 + c2 * a1_2 + c3 * a1_3;
+    o.A2 = c0 * a2_0 + c1 * a2_1 + c2 * a2_2 + c3 * a2_3;
+    o.c3a3 = c3 * a3_3;
+    o.c3a4 = c3 * a4_3;
+    if (want_limiter) {
+        o.tauZ = tau;
+        o.bmin = fmin(fmin(b0, b1), fmin(b2, b3));
+        o.bmax = fmax(fmax(b0, b1), fmax(b2, b3));
+    }
+    return o;
+}
+
+// time-limiter ingredient 2 at2 / (at1 + at2) of one reconstruction (Sect. 2.2)
+__device__ __forceinline__ double limiter_alpha(const AO& o, double eps) {
+    double r1 = o.tauZ / (o.bmin + eps), r2 = o.tauZ / (o.bmax + eps);
+    double a1 = 1.0 + r1 * r1, a2 = 1.0 + r2 * r2;
+    return 2.0 * a2 / (a1 + a2);
+}
+
+// value and d/dxi of the AO polynomial at the right cell edge xi = +1/2
+__device__ __forceinline__ void ao_at_right_edge(const AO& o, double q0, double& val, double& slope) {
+    val = q0 + 0.5 * o.A1 + (1.0 / 6.0) * o.A2 + 0.125 * o.c3a3 + 0.05 * o.c3a4;
+    slope = o.A1 + o.A2 + 0.75 * o.c3a3 + 0.5 * o.c3a4;
+}
+
+// zero-mean DF quadratic of Sect. 3.3, p_DF = Q_0 + alpha (p1 - Q_0), at xi = +1/2
+__device__ __forceinline__ void df_at_right_edge(const double q[5], double alpha, double& val, double& slope) {
+    double a1 = 0.5 * (q[3] - q[1]);
+    double a2 = 0.5 * (q[1] - 2.0 * q[2] + q[3]);
+    val = q[2] + alpha * (0.5 * a1 + (1.0 / 6.0) * a2);
+    slope = alpha * (a1 + a2);
+}
+
+// values and d/deta at the two Gauss points eta = -g (m=1), +g (m=2), g = sqrt(3)/6
+__device__ __forceinline__ void ao_at_gauss(const AO& o, double q0, double val[2], double slope[2]) {
+    const double g = kGaussEta;
+    double E = q0 - (1.0 / 180.0) * o.c3a4;                 // even part: xi^2 = 1/12, xi^4 = 1/144
+    double O = g * (o.A1 + (1.0 / 12.0) * o.c3a3);          // odd part
+    double Es = o.A1 + 0.25 * o.c3a3;
+    double Os = g * (2.0 * o.A2 + (1.0 / 3.0) * o.c3a4);
+    val[0] = E - O; val[1] = E + O;
+    slope[0] = Es - Os; slope[1] = Es + Os;
+}
+
+__device__ __forceinline__ void df_at_gauss(const double q[5], double alpha, double val[2], double slope[2]) {
+    const double g = kGaussEta;
+    double a1 = 0.5 * (q[3] - q[1]);
+    double a2 = 0.5 * (q[1] - 2.0 * q[2] + q[3]);
+    double O = alpha * g * a1;                               // xi^2 - 1/12 vanishes at the Gauss points
+    double Es = alpha * a1, Os = alpha * 2.0 * g * a2;
+    val[0] = q[2] - O; val[1] = q[2] + O;
+    slope[0] = Es - Os; slope[1] = Es + Os;
+}
+
+// ------------------------------------------------------------------------------------------
+// Gas-kinetic flux at one Gauss point in the local frame (Sect. 2.2, 3.4; Eqs. 25-27).
+// Maxwellian moments are normalised by rho.  <u^k v^l xi^{2c}> = mu[k] mv[l] mx[c].
+// ------------------------------------------------------------------------------------------
+struct Mom {
+    double mu[7];   // <u^n>, full or half-space
+    double mv[6];   // <v^n>, full
+    double mx[3];   // <1>, <xi^2>, <xi^4>
+};
+
+struct Maxw { double rho, U, V, p, il2; };   // il2 = 1/(2 lambda) = p/rho
+
+__device__ __forceinline__ Maxw maxw_of(const double W[4], double gm1) {
+    Maxw s;
+    s.rho = W[0];
+    double ir = 1.0 / W[0];
+    s.U = W[1] * ir;
+    s.V = W[2] * ir;
+    s.p = gm1 * (W[3] - 0.5 * W[0] * (s.U * s.U + s.V * s.V));
+    s.il2 = s.p * ir;
+    return s;
+}
+
+// half: 0 full, +1 u>0, -1 u<0
+template <int HALF>
+__device__ __forceinline__ void fill_moments(const Maxw& s, double K, Mom& m) {
+    if (HALF == 0) {
+        m.mu[0] = 1.0;
+        m.mu[1] = s.U;
+    } else {
+        double sl = sqrt(0.5 / s.il2);                       // sqrt(lambda)
+        double x = sl * s.U;
+        double e = exp(-x * x) * (0.28209479177387814347 / sl);   // exp(-lambda U^2) / (2 sqrt(pi lambda))
+        if (HALF > 0) { m.mu[0] = 0.5 * erfc(-x); m.mu[1] = s.U * m.mu[0] + e; }
+        else          { m.mu[0] = 0.5 * erfc(x);  m.mu[1] = s.U * m.mu[0] - e; }
+    }
+#pragma unroll
+    for (int n = 2; n < 7; ++n) m.mu[n] = s.U * m.mu[n - 1] + (double)(n - 1) * s.il2 * m.mu[n - 2];
+    m.mv[0] = 1.0;
+    m.mv[1] = s.V;
+#pragma unroll
+    for (int n = 2; n < 6; ++n) m.mv[n] = s.V * m.mv[n - 1] + (double)(n - 1) * s.il2 * m.mv[n - 2];
+    m.mx[0] = 1.0;
+    m.mx[1] = K * s.il2;
+    m.mx[2] = K * (K + 2.0) * s.il2 * s.il2;
+}
+
+template <int k, int l, int c>
+__device__ __forceinline__ double M(const Mom& m) { return m.mu[k] * m.mv[l] * m.mx[c]; }
+
+// <u^k v^l xi^{2c} psi>, psi = (1, u, v, (u^2+v^2+xi^2)/2)
+template <int k, int l, int c>
+__device__ __forceinline__ void psi_mom(const Mom& m, double out[4]) {
+    out[0] = M<k, l, c>(m);
+    out[1] = M<k + 1, l, c>(m);
+    out[2] = M<k, l + 1, c>(m);
+    out[3] = 0.5 * (M<k + 2, l, c>(m) + M<k, l + 2, c>(m) + M<k, l, c + 1>(m));
+}
+
+// <u^k v^l a psi> with a = a0 + a1 u + a2 v + a3 (u^2+v^2+xi^2)/2
+template <int k, int l>
+__device__ __forceinline__ void a_mom(const Mom& m, const double a[4], double out[4]) {
+    double t0[4], t1[4], t2[4], t3[4], t4[4], t5[4];
+    psi_mom<k, l, 0>(m, t0);
+    psi_mom<k + 1, l, 0>(m, t1);
+    psi_mom<k, l + 1, 0>(m, t2);
+    psi_mom<k + 2, l, 0>(m, t3);
+    psi_mom<k, l + 2, 0>(m, t4);
+    psi_mom<k, l, 1>(m, t5);
+    double h = 0.5 * a[3];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) out[i] = a[0] * t0[i] + a[1] * t1[i] + a[2] * t2[i] + h * (t3[i] + t4[i] + t5[i]);
+}
+
+// closed-form solution of <a psi> = b for a Maxwellian (U, V, lambda)
+__device__ __forceinline__ void slope_solve(const Maxw& s, double K, const double b[4], double a[4]) {
+    double q = s.U * s.U + s.V * s.V + (K + 2.0) * s.il2;
+    double tl = 1.0 / s.il2;                          // 2 lambda
+    double f4 = tl * tl / (K + 2.0);                  // 4 lambda^2 / (K+2)
+    double R2 = b[1] - s.U * b[0], R3 = b[2] - s.V * b[0], R4 = 2.0 * b[3] - q * b[0];
+    a[3] = f4 * (R4 - 2.0 * s.U * R2 - 2.0 * s.V * R3);
+    a[2] = tl * R3 - s.V * a[3];
+    a[1] = tl * R2 - s.U * a[3];
+    a[0] = b[0] - s.U * a[1] - s.V * a[2] - 0.5 * a[3] * q;
+}
+
+struct GPState { double W[4], Wn[4], Wt[4]; };   // one side of one Gauss point, local frame
+
+__device__ __forceinline__ void gks_flux(const GPState& L, const GPState& R, double dt, const SchemeConsts& S,
+                                         double F[4], double dF[4]) {
+    const double K = S.K;
+    Maxw sl = maxw_of(L.W, S.gm1), sr = maxw_of(R.W, S.gm1);
+    Mom ml, mr;
+    fill_moments<+1>(sl, K, ml);
+    fill_moments<-1>(sr, K, mr);
+    double b[4], alx[4], aly[4], arx[4], ary[4];
+    double irl = 1.0 / sl.rho, irr = 1.0 / sr.rho;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) b[i] = L.Wn[i] * irl;
+    slope_solve(sl, K, b, alx);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) b[i] = L.Wt[i] * irl;
+    slope_solve(sl, K, b, aly);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) b[i] = R.Wn[i] * irr;
+    slope_solve(sr, K, b, arx);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) b[i] = R.Wt[i] * irr;
+    slope_solve(sr, K, b, ary);
+    // Sect. 3.4: equilibrium state and slopes by kinetic weighting
+    double Wc[4], Wcx[4], Wcy[4], t1[4], t2[4];
+    psi_mom<0, 0, 0>(ml, t1); psi_mom<0, 0, 0>(mr, t2);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) Wc[i] = sl.rho * t1[i] + sr.rho * t2[i];
+    a_mom<0, 0>(ml, alx, t1); a_mom<0, 0>(mr, arx, t2);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) Wcx[i] = sl.rho * t1[i] + sr.rho * t2[i];
+    a_mom<0, 0>(ml, aly, t1); a_mom<0, 0>(mr, ary, t2);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) Wcy[i] = sl.rho * t1[i] + sr.rho * t2[i];
+    Maxw sc = maxw_of(Wc, S.gm1);
+    Mom mc;
+    fill_moments<0>(sc, K, mc);
+    double acx[4], acy[4], Ac[4], irc = 1.0 / sc.rho;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) b[i] = Wcx[i] * irc;
+    slope_solve(sc, K, b, acx);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) b[i] = Wcy[i] * irc;
+    slope_solve(sc, K, b, acy);
+    // compatibility <A + a_x u + a_y v> = 0
+    a_mom<1, 0>(mc, acx, t1); a_mom<0, 1>(mc, acy, t2);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) b[i] = -(t1[i] + t2[i]);
+    slope_solve(sc, K, b, Ac);
+    // moments entering the flux
+    double Mc0[4], Mc1[4], Mc2[4], Ml0[4], Mr0[4], Ml1[4], Mr1[4];
+    psi_mom<1, 0, 0>(mc, Mc0);
+    a_mom<2, 0>(mc, acx, t1); a_mom<1, 1>(mc, acy, t2);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) Mc1[i] = t1[i] + t2[i];
+    a_mom<1, 0>(mc, Ac, Mc2);
+    psi_mom<1, 0, 0>(ml, Ml0);
+    psi_mom<1, 0, 0>(mr, Mr0);
+    a_mom<2, 0>(ml, alx, t1); a_mom<1, 1>(ml, aly, t2);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) Ml1[i] = t1[i] + t2[i];
+    a_mom<2, 0>(mr, arx, t1); a_mom<1, 1>(mr, ary, t2);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) Mr1[i] = t1[i] + t2[i];
+    // numerical collision time (Sect. 2.2) and the combined time coefficients of Eq. 27
+    double T = S.C1 * dt + S.C2 * fabs((sl.p - sr.p) / (sl.p + sr.p)) * dt;
+    double tau = (S.tau_reading == 1) ? T : 0.0;
+    double E2 = 0.0, r = 0.0;
+    if (T > 0.0) { E2 = exp(-0.5 * dt / T); r = T / dt; }
+    double E1 = E2 * E2;
+    double om = 1.0 - E2;
+    double S3 = om * (3.0 - E2);                       // 3 - 4 E2 + E1
+    double idt = 1.0 / dt;
+    // F-coefficients (4 G(dt/2) - G(dt)) / dt and dF-coefficients 4 (G(dt) - 2 G(dt/2)) / dt^2
+    double glrF = r * S3, glrD = -4.0 * r * om * om * idt;
+    double gcF = 1.0 - glrF, gcD = -glrD;
+    double TT = T * T + T * tau;
+    double acF = TT * S3 * idt - 2.0 * T * E2 + T * E1 - tau;
+    double acD = 4.0 * (-TT * om * om + T * dt * E2 * om) * idt * idt;
+    double AcF = -tau + tau * r * S3;
+    double AcD = 1.0 - 4.0 * T * tau * om * om * idt * idt;
+    double alrF = -acF - tau, alrD = -acD;
+    double AlrF = -T * tau * S3 * idt, AlrD = 4.0 * T * tau * om * om * idt * idt;
+    double Ml2[4] = {0, 0, 0, 0}, Mr2[4] = {0, 0, 0, 0};
+    if (S.tau_reading == 1) {
+        Mom mlF, mrF;
+        fill_moments<0>(sl, K, mlF);
+        fill_moments<0>(sr, K, mrF);
+        double Al[4], Ar[4];
+        a_mom<1, 0>(mlF, alx, t1); a_mom<0, 1>(mlF, aly, t2);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) b[i] = -(t1[i] + t2[i]);
+        slope_solve(sl, K, b, Al);
+        a_mom<1, 0>(mrF, arx, t1); a_mom<0, 1>(mrF, ary, t2);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) b[i] = -(t1[i] + t2[i]);
+        slope_solve(sr, K, b, Ar);
+        a_mom<1, 0>(ml, Al, Ml2);
+        a_mom<1, 0>(mr, Ar, Mr2);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        double c0 = sc.rho * Mc0[i], c1 = sc.rho * Mc1[i], c2 = sc.rho * Mc2[i];
+        double g0 = sl.rho * Ml0[i] + sr.rho * Mr0[i];
+        double g1 = sl.rho * Ml1[i] + sr.rho * Mr1[i];
+        double g2 = sl.rho * Ml2[i] + sr.rho * Mr2[i];
+        F[i] = gcF * c0 + acF * c1 + AcF * c2 + glrF * g0 + alrF * g1 + AlrF * g2;
+        dF[i] = gcD * c0 + acD * c1 + AcD * c2 + glrD * g0 + alrD * g1 + AlrD * g2;
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Lax-Friedrichs flux (Sect. 2.3) and its time derivative with frozen wave speed and
+// W_t = -(A W_n + B W_t) on each side (Cauchy-Kovalevskaya)
+// ------------------------------------------------------------------------------------------
+struct EulerPt { double u, v, p, c, H, q; };
+
+__device__ __forceinline__ EulerPt euler_pt(const double W[4], const SchemeConsts& S) {
+    EulerPt e;
+    double ir = 1.0 / W[0];
+    e.u = W[1] * ir;
+    e.v = W[2] * ir;
+    e.q = 0.5 * (e.u * e.u + e.v * e.v);
+    e.p = S.gm1 * (W[3] - W[0] * e.q);
+    e.c = sqrt(S.gamma * e.p * ir);
+    e.H = (W[3] + e.p) * ir;
+    return e;
+}
+
+// A X (x-flux Jacobian) and B X (y-flux Jacobian) at a state
+__device__ __forceinline__ void jac_x(const EulerPt& e, double gm1, const double X[4], double Y[4]) {
+    double dp = gm1 * (X[3] - e.u * X[1] - e.v * X[2] + e.q * X[0]);
+    Y[0] = X[1];
+    Y[1] = 2.0 * e.u * X[1] - e.u * e.u * X[0] + dp;
+    Y[2] = e.v * X[1] + e.u * X[2] - e.u * e.v * X[0];
+    Y[3] = e.u * (X[3] + dp) + e.H * (X[1] - e.u * X[0]);
+}
+__device__ __forceinline__ void jac_y(const EulerPt& e, double gm1, const double X[4], double Y[4]) {
+    double dp = gm1 * (X[3] - e.u * X[1] - e.v * X[2] + e.q * X[0]);
+    Y[0] = X[2];
+    Y[1] = e.v * X[1] + e.u * X[2] - e.u * e.v * X[0];
+    Y[2] = 2.0 * e.v * X[2] - e.v * e.v * X[0] + dp;
+    Y[3] = e.v * (X[3] + dp) + e.H * (X[2] - e.v * X[0]);
+}
+
+__device__ __forceinline__ void lf_flux(const GPState& L, const GPState& R, const SchemeConsts& S,
+                                        double F[4], double dF[4]) {
+    EulerPt el = euler_pt(L.W, S), er = euler_pt(R.W, S);
+    double FL[4] = {L.W[1], L.W[1] * el.u + el.p, L.W[1] * el.v, el.u * (L.W[3] + el.p)};
+    double FR[4] = {R.W[1], R.W[1] * er.u + er.p, R.W[1] * er.v, er.u * (R.W[3] + er.p)};
+    double s = fmax(fabs(el.u) + el.c, fabs(er.u) + er.c);
+    double t1[4], t2[4], WtL[4], WtR[4], AL[4], AR[4];
+    jac_x(el, S.gm1, L.Wn, t1); jac_y(el, S.gm1, L.Wt, t2);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) WtL[i] = -(t1[i] + t2[i]);
+    jac_x(er, S.gm1, R.Wn, t1); jac_y(er, S.gm1, R.Wt, t2);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) WtR[i] = -(t1[i] + t2[i]);
+    jac_x(el, S.gm1, WtL, AL);
+    jac_x(er, S.gm1, WtR, AR);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        F[i] = 0.5 * (FL[i] + FR[i]) - 0.5 * s * (R.W[i] - L.W[i]);
+        dF[i] = 0.5 * (AL[i] + AR[i]) - 0.5 * s * (WtR[i] - WtL[i]);
+    }
+}
+
+// DF factor of one Gauss point (Sect. 3.2), local-frame states
+__device__ __forceinline__ double df_alpha(const double WL[4], const double WR[4], const SchemeConsts& S) {
+    EulerPt l = euler_pt(WL, S), r = euler_pt(WR, S);
+    double jp = fabs(l.p - r.p);
+    double icl = 1.0 / l.c, icr = 1.0 / r.c;
+    double dn = l.u * icl - r.u * icr, dtg = l.v * icl - r.v * icr;
+    double D = jp / l.p + jp / r.p + dn * dn + dtg * dtg;
+    return 1.0 / (1.0 + D * D);
+}
+
+__device__ __forceinline__ bool physical_state(const double W[4], double gm1) {
+    if (!(W[0] > 0.0)) return false;
+    double p = gm1 * (W[3] - 0.5 * (W[1] * W[1] + W[2] * W[2]) / W[0]);
+    return p > 0.0;
+}
+
+}  // namespace dfk

@@ -1,0 +1,180 @@
+"""Python front end of the CUDA solver: a handle per problem, torch for device memory/streams.
+
+``Solver`` marshals arguments to the C ABI (``_lib``); all arithmetic runs in the CUDA library.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _lib
+from .inputs import Settings
+
+FACE_RECORD = 59
+
+
+def make_config(s: Settings) -> _lib.Config:
+    if s.dt_rule != 0:
+        raise ValueError("the CUDA path implements the per-direction CFL rule only (dt_rule=0)")
+    c = _lib.Config()
+    _lib.check(_lib.lib().dfgks_config_default(C.byref(c), int(s.nx), int(s.ny)), "dfgks_config_default")
+    for f in ("nx", "ny", "x0", "x1", "y0", "y1", "gamma", "cfl", "alpha_thres", "dH", "dL", "eps", "C1", "C2",
+              "time_limiter", "tau_reading", "gp_fallback", "time_scheme"):
+        setattr(c, f, getattr(s, f))
+    c.bc_xlo, c.bc_xhi, c.bc_ylo, c.bc_yhi = (int(b) for b in s.bc)
+    return c
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, torch.Tensor):
+        assert t.dtype == torch.float64 and t.is_contiguous()
+        return C.c_void_p(t.data_ptr())
+    assert isinstance(t, np.ndarray) and t.dtype == np.float64 and t.flags.c_contiguous
+    return C.c_void_p(t.ctypes.data)
+
+
+class Solver:
+    """One 2-D Euler problem on the current CUDA device, ordered on a torch stream."""
+
+    def __init__(self, settings: Settings, stream: torch.cuda.Stream | None = None):
+        self.settings = settings
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self._cfg = make_config(settings)
+        h = C.c_void_p()
+        _lib.check(_lib.lib().dfgks_create(C.byref(self._cfg), C.c_void_p(self.stream.cuda_stream), C.byref(h)),
+                   "dfgks_create")
+        self._h = h
+
+    # -- lifecycle ---------------------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.lib().dfgks_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def shape(self):
+        return (4, self.settings.ny, self.settings.nx)
+
+    # -- state -------------------------------------------------------------------------
+    def set_ic(self, W):
+        on_dev = isinstance(W, torch.Tensor) and W.is_cuda
+        W = W if on_dev else np.ascontiguousarray(np.asarray(W, dtype=np.float64))
+        assert tuple(W.shape) == self.shape
+        _lib.check(_lib.lib().dfgks_set_ic(self._h, _ptr(W), int(on_dev)), "dfgks_set_ic")
+
+    def set_state(self, W, alpha=None, t=0.0, step=0):
+        on_dev = isinstance(W, torch.Tensor) and W.is_cuda
+        if not on_dev:
+            W = np.ascontiguousarray(np.asarray(W, dtype=np.float64))
+            alpha = None if alpha is None else np.ascontiguousarray(np.asarray(alpha, dtype=np.float64))
+        _lib.check(_lib.lib().dfgks_set_state(self._h, _ptr(W), _ptr(alpha), float(t), int(step), int(on_dev)),
+                   "dfgks_set_state")
+
+    def get_state(self, device: bool = False):
+        if device:
+            W = torch.empty(self.shape, dtype=torch.float64, device="cuda")
+            a = torch.empty(self.shape[1:], dtype=torch.float64, device="cuda")
+        else:
+            W = np.empty(self.shape)
+            a = np.empty(self.shape[1:])
+        t = C.c_double()
+        st = C.c_long()
+        _lib.check(_lib.lib().dfgks_get_state(self._h, _ptr(W), _ptr(a), C.byref(t), C.byref(st), int(device)),
+                   "dfgks_get_state")
+        return W, a, t.value, st.value
+
+    # -- stepping ----------------------------------------------------------------------
+    def step(self, n: int, dt: float = 0.0, flux: int | None = None, t_end: float = 0.0, record_dts: bool = False):
+        """Advance up to n steps; returns (steps_done, dts or None).  Raises DfgksError on failure."""
+        flux = self.settings.flux if flux is None else flux
+        dts = np.zeros(max(n, 1)) if record_dts else None
+        done = C.c_int()
+        rc = _lib.lib().dfgks_step(self._h, int(n), float(dt or 0.0), int(flux), float(t_end or 0.0),
+                                   None if dts is None else dts.ctypes.data_as(C.POINTER(C.c_double)), C.byref(done))
+        _lib.check(rc, "dfgks_step")
+        return done.value, (dts[:done.value] if dts is not None else None)
+
+    def run(self, t_end: float | None = None, steps: int | None = None, dt: float = 0.0, chunk: int = 64,
+            record_dts: bool = False):
+        """Run to t_end (chunks of `chunk` steps) or for a fixed number of steps."""
+        total, all_dts = 0, []
+        if t_end is None:
+            done, d = self.step(steps, dt=dt, record_dts=record_dts)
+            return done, d
+        while True:
+            n = chunk if steps is None else min(chunk, steps - total)
+            if n <= 0:
+                break
+            done, d = self.step(n, dt=dt, t_end=t_end, record_dts=record_dts)
+            total += done
+            if d is not None:
+                all_dts.append(d)
+            if done < n:
+                break
+        return total, (np.concatenate(all_dts) if all_dts else None)
+
+    def last_error(self):
+        s, i, j = C.c_long(), C.c_int(), C.c_int()
+        _lib.check(_lib.lib().dfgks_last_error_detail(self._h, C.byref(s), C.byref(i), C.byref(j)),
+                   "dfgks_last_error_detail")
+        return s.value, i.value, j.value
+
+    def counters(self):
+        c = _lib.Counters()
+        _lib.check(_lib.lib().dfgks_get_counters(self._h, C.byref(c)), "dfgks_get_counters")
+        return {"fallbacks": c.fallbacks, "df_normal": c.df_normal, "df_tangential": c.df_tangential}
+
+    KERNEL_CLASSES = ("lines", "faces", "flux", "update", "other")
+
+    def set_timing(self, enable: bool) -> None:
+        _lib.check(_lib.lib().dfgks_set_timing(self._h, int(enable)), "dfgks_set_timing")
+
+    def timing(self, reset: bool = False) -> dict:
+        ms = np.zeros(5)
+        timed = np.zeros(5, dtype=np.int64)
+        launches = np.zeros(5, dtype=np.int64)
+        _lib.check(_lib.lib().dfgks_get_timing(self._h, C.c_void_p(ms.ctypes.data), C.c_void_p(timed.ctypes.data),
+                                               C.c_void_p(launches.ctypes.data), int(reset)), "dfgks_get_timing")
+        return {k: {"ms": float(ms[q]), "timed": int(timed[q]), "launches": int(launches[q])}
+                for q, k in enumerate(self.KERNEL_CLASSES)}
+
+    def device_bytes(self) -> int:
+        b = C.c_ulonglong()
+        _lib.check(_lib.lib().dfgks_device_bytes(self._h, C.byref(b)), "dfgks_device_bytes")
+        return b.value
+
+    # -- stage operator ------------------------------------------------------------------
+    def residual(self, W: torch.Tensor, alpha: torch.Tensor, dt: float, flux: int | None = None):
+        """(L, dL/dt, limited dL/dt, alpha_next) as new CUDA tensors."""
+        flux = self.settings.flux if flux is None else flux
+        L = torch.empty(self.shape, dtype=torch.float64, device="cuda")
+        dL, dLt = torch.empty_like(L), torch.empty_like(L)
+        an = torch.empty(self.shape[1:], dtype=torch.float64, device="cuda")
+        _lib.check(_lib.lib().dfgks_residual(self._h, _ptr(W), _ptr(alpha), float(dt), int(flux),
+                                             _ptr(L), _ptr(dL), _ptr(dLt), _ptr(an)), "dfgks_residual")
+        return L, dL, dLt, an
+
+    def face_records(self, W: torch.Tensor, alpha: torch.Tensor, dt: float, direction: int, flux: int | None = None):
+        flux = self.settings.flux if flux is None else flux
+        s = self.settings
+        nf, nt = (s.nx + 1, s.ny) if direction == 0 else (s.ny + 1, s.nx)
+        out = torch.empty((nt, nf, FACE_RECORD), dtype=torch.float64, device="cuda")
+        _lib.check(_lib.lib().dfgks_face_records(self._h, _ptr(W), _ptr(alpha), float(dt), int(flux),
+                                                 int(direction), _ptr(out)), "dfgks_face_records")
+        return out

@@ -1,0 +1,277 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle on the same seeded inputs.
+
+Bars (stated per test): one-step state <= 1e-12 relative (per component, floor 1e-3 of the
+component's maximum), full runs <= 1e-9 relative L1; branch counters identical.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2402_10914_gb300 import inputs as I
+from tests.parity_util import comp_rel_err, field_err, l1_rel
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def Solver(settings):
+    from paper_2402_10914_gb300.solver import Solver as S
+    return S(settings)
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy()
+
+
+def rough(nx, ny, seed, flux, bc=(I.OUTFLOW,) * 4, **kw):
+    return I.random_rough(nx, ny, seed, bc=bc, flux=flux, time_limiter=1 if flux == I.GKS else 0, **kw)
+
+
+# ---------------------------------------------------------------- kernel-level intermediates
+
+@pytest.mark.parametrize("direction", [0, 1])
+@pytest.mark.parametrize("flux", [I.GKS, I.LF])
+@pytest.mark.parametrize("kind", ["smooth", "rough", "rough_df"])
+def test_face_records(direction, flux, kind):
+    if kind == "smooth":
+        w = I.random_smooth(13, 11, seed=2, flux=flux)
+        alpha = np.ones((11, 13))
+    else:
+        w = rough(13, 11, seed=4, flux=flux)
+        rng = np.random.default_rng(5)
+        alpha = rng.uniform(0.0, 1.0, (11, 13)) if kind == "rough_df" else np.ones((11, 13))
+    s = w.settings.with_(time_limiter=1)
+    dt = 0.4 * oracle.cfl_dt(s, w.W0)
+    ref, _ = oracle.face_records(s, w.W0, alpha, dt, direction)
+    with Solver(s) as sol:
+        got = host(sol.face_records(dev(w.W0), dev(alpha), dt, direction, flux=flux))
+    # Gauss-point states (local frame), omega^t and alpha_{p,m}
+    assert field_err(got[..., 11:], ref[..., 11:]) < 1e-12
+    assert field_err(got[..., 8:11], ref[..., 8:11]) < 1e-12
+    # fluxes; the time derivative carries the oracle's cancellation in 4(F(dt)-2F(dt/2))/dt^2
+    assert field_err(got[..., 0:4], ref[..., 0:4]) < 1e-12
+    assert field_err(got[..., 4:8], ref[..., 4:8]) < 1e-9
+
+
+@pytest.mark.parametrize("flux", [I.GKS, I.LF])
+@pytest.mark.parametrize("bc", [(I.PERIODIC,) * 4, (I.OUTFLOW,) * 4, (I.REFLECT,) * 4, (I.PERIODIC, I.PERIODIC, I.REFLECT, I.OUTFLOW)])
+def test_stage_operator(flux, bc):
+    w = rough(17, 14, seed=11, flux=flux, bc=bc)
+    s = w.settings.with_(time_limiter=1)
+    alpha = np.random.default_rng(3).uniform(0.0, 1.0, (14, 17))
+    dt = 0.5 * oracle.cfl_dt(s, w.W0)
+    L, dL, dLt, an, st = oracle.residual(s, w.W0, alpha, dt)
+    with Solver(s) as sol:
+        gL, gdL, gdLt, gan = (host(t) for t in sol.residual(dev(w.W0), dev(alpha), dt, flux=flux))
+    assert comp_rel_err(gL, L) < 1e-11
+    assert comp_rel_err(gdL, dL) < 1e-8
+    assert comp_rel_err(gdLt, dLt) < 1e-8
+    assert comp_rel_err(gan[None], an[None], floor_frac=1e-12) < 1e-12
+
+
+# ---------------------------------------------------------------- one step / full runs
+
+def run_both(w, nsteps, t_end=0.0, dt_fixed=0.0):
+    s = w.settings
+    a0 = oracle.alpha0(s, w.W0)
+    rc, Wo, ao, to, dts_o, st = oracle.run(s, w.W0, a0, nsteps, dt_fixed=dt_fixed, t_end=t_end)
+    with Solver(s) as sol:
+        sol.set_ic(w.W0)
+        done, dts = sol.step(nsteps, dt=dt_fixed, t_end=t_end, record_dts=True)
+        W, a, t, step = sol.get_state()
+        cnt = sol.counters()
+    return (rc, Wo, ao, to, dts_o, st), (done, W, a, t, dts, cnt)
+
+
+@pytest.mark.parametrize("name", ["c1", "quadrants", "rough_periodic", "rough_reflect", "blast", "vortex", "ssprk3",
+                                  "tau_reading_a", "no_limiter_gks"])
+def test_one_step_parity(name):
+    if name == "c1":
+        w = I.sine_c1(40)
+    elif name == "quadrants":
+        w = I.quadrants(96, seed=2)
+    elif name == "rough_periodic":
+        w = rough(20, 18, seed=7, flux=I.GKS, bc=(I.PERIODIC,) * 4)
+    elif name == "rough_reflect":
+        w = rough(20, 18, seed=8, flux=I.GKS, bc=(I.REFLECT,) * 4)
+    elif name == "blast":
+        w = I.blast(64)
+    elif name == "vortex":
+        w = I.vortex(48)
+    elif name == "ssprk3":
+        w = rough(20, 18, seed=9, flux=I.LF)
+        w.settings = w.settings.with_(time_scheme=I.SSPRK3)
+    elif name == "tau_reading_a":
+        w = rough(20, 18, seed=10, flux=I.GKS)
+        w.settings = w.settings.with_(tau_reading=1)
+    else:
+        w = rough(20, 18, seed=12, flux=I.GKS)
+        w.settings = w.settings.with_(time_limiter=0)
+    (rc, Wo, ao, to, dts_o, st), (done, W, a, t, dts, cnt) = run_both(w, 1)
+    assert rc == 0 and done == 1
+    assert comp_rel_err(W, Wo) <= 1e-12, comp_rel_err(W, Wo)
+    assert comp_rel_err(a[None], ao[None], floor_frac=1e-12) <= 1e-11
+    assert abs(dts[0] - dts_o[0]) <= 1e-14 * dts_o[0]
+    assert cnt["fallbacks"] == st.fallbacks
+    assert cnt["df_normal"] == st.df_normal and cnt["df_tangential"] == st.df_tangential
+
+
+def test_one_step_parity_quadrants_full_size():
+    # the 400 x 400 four-quadrant GKS workload, one S2O4 step, every cell compared
+    w = I.quadrants(400, seed=2)
+    oracle.set_threads(oracle.max_threads())
+    (rc, Wo, ao, to, dts_o, st), (done, W, a, t, dts, cnt) = run_both(w, 1)
+    assert rc == 0 and done == 1
+    assert comp_rel_err(W, Wo) <= 1e-12
+    assert comp_rel_err(a[None], ao[None], floor_frac=1e-12) <= 1e-11
+
+
+def test_full_run_parity_c1():
+    w = I.sine_c1(40)
+    (rc, Wo, ao, to, dts_o, st), (done, W, a, t, dts, cnt) = run_both(w, w.steps)
+    assert rc == 0 and done == 20
+    assert l1_rel(W, Wo) <= 1e-9
+    assert comp_rel_err(W, Wo) <= 1e-11
+    assert np.allclose(dts, dts_o, rtol=1e-13, atol=0)
+
+
+def test_full_run_parity_quadrants_to_t_end():
+    # the four-quadrant GKS family on a 96 x 96 mesh run to t = 0.08 (data-dependent step count)
+    w = I.quadrants(96, seed=3, t_end=0.08)
+    (rc, Wo, ao, to, dts_o, st), (done, W, a, t, dts, cnt) = run_both(w, 100000, t_end=w.t_end)
+    assert rc == 0 and done == len(dts_o)
+    assert t == w.t_end and to == w.t_end
+    assert l1_rel(W, Wo) <= 1e-9, l1_rel(W, Wo)
+    assert cnt["df_normal"] == st.df_normal and cnt["fallbacks"] == st.fallbacks
+
+
+def test_full_run_parity_blast_steps():
+    w = I.blast(96)
+    (rc, Wo, ao, to, dts_o, st), (done, W, a, t, dts, cnt) = run_both(w, 30)
+    assert rc == 0 and done == 30
+    assert l1_rel(W, Wo) <= 1e-9, l1_rel(W, Wo)
+    g = w.settings.gamma
+    p = (g - 1) * (W[3] - 0.5 * (W[1] ** 2 + W[2] ** 2) / W[0])
+    assert W[0].min() > 0 and p.min() > 0
+
+
+# ---------------------------------------------------------------- invariants on the GPU
+
+@pytest.mark.parametrize("flux", [I.GKS, I.LF])
+def test_free_stream_bitwise(flux):
+    s = I.Settings(nx=33, ny=17, bc=(I.OUTFLOW,) * 4, flux=flux)
+    W0 = np.broadcast_to(I.conserved(0.7, 0.3, -0.4, 1.3)[:, None, None], (4, 17, 33)).copy()
+    with Solver(s) as sol:
+        sol.set_ic(W0)
+        sol.step(5)
+        W, a, _, _ = sol.get_state()
+    assert np.array_equal(W, W0)
+    assert np.all(a == 1.0)
+
+
+@pytest.mark.parametrize("flux", [I.GKS, I.LF])
+def test_conservation_periodic(flux):
+    w = rough(40, 36, seed=13, flux=flux, bc=(I.PERIODIC,) * 4)
+    with Solver(w.settings) as sol:
+        sol.set_ic(w.W0)
+        sol.step(10)
+        W, _, _, _ = sol.get_state()
+    tot0, tot = w.W0.sum(axis=(1, 2)), W.sum(axis=(1, 2))
+    assert np.all(np.abs(tot - tot0) <= 1e-13 * np.abs(w.W0).sum(axis=(1, 2)))
+
+
+def test_transpose_symmetry_gpu():
+    w = rough(24, 19, seed=14, flux=I.GKS)
+    s = w.settings
+    sT = s.with_(nx=s.ny, ny=s.nx)
+    T = lambda W: np.stack([W[0].T, W[2].T, W[1].T, W[3].T])
+    with Solver(s) as a, Solver(sT) as b:
+        a.set_ic(w.W0)
+        b.set_ic(T(w.W0))
+        dt = 0.5 * oracle.cfl_dt(s, w.W0)
+        a.step(3, dt=dt)
+        b.step(3, dt=dt)
+        Wa, _, _, _ = a.get_state()
+        Wb, _, _, _ = b.get_state()
+    assert comp_rel_err(Wb, T(Wa)) < 1e-12
+
+
+# ---------------------------------------------------------------- time control and errors
+
+def test_t_end_clipping_and_chunks():
+    w = I.quadrants(48, seed=5, t_end=0.03)
+    with Solver(w.settings) as sol:
+        sol.set_ic(w.W0)
+        total, dts = sol.run(t_end=w.t_end, chunk=7, record_dts=True)
+        _, _, t, step = sol.get_state()
+        more, _ = sol.step(5, t_end=w.t_end)
+    a0 = oracle.alpha0(w.settings, w.W0)
+    rc, Wo, _, to, dts_o, _ = oracle.run(w.settings, w.W0, a0, 100000, t_end=w.t_end)
+    assert t == w.t_end and step == total == len(dts_o) and more == 0
+    assert np.allclose(dts, dts_o, rtol=1e-12, atol=0)
+
+
+def test_set_ic_rejects_nonphysical_and_keeps_state():
+    w = rough(16, 12, seed=15, flux=I.GKS)
+    bad = w.W0.copy()
+    bad[3, 5, 7] = 0.1 * bad[3, 5, 7] - 10.0          # negative pressure
+    from paper_2402_10914_gb300 import _lib
+    with Solver(w.settings) as sol:
+        sol.set_ic(w.W0)
+        with pytest.raises(_lib.DfgksError) as e:
+            sol.set_ic(bad)
+        assert e.value.status == _lib.ENONPHYS
+        W, _, _, _ = sol.get_state()
+    assert np.array_equal(W, w.W0)
+
+
+def test_positivity_failure_leaves_last_good_state():
+    # 123 problem at Mach 20 without the Gauss-point fallback: the high-order update loses
+    # positivity within a few steps on both sides
+    n, ny = 100, 4
+    s = I.Settings(nx=n, ny=ny, x0=0, x1=1, y0=0, y1=ny / n, cfl=0.5, bc=(I.OUTFLOW, I.OUTFLOW, I.PERIODIC, I.PERIODIC),
+                   flux=I.GKS, gp_fallback=0)
+    xc, yc, _, _ = I.cell_centres(s)
+    X, _ = np.meshgrid(xc, yc)
+    p0 = 4.0 / (1.4 * 20.0 ** 2)
+    W0 = I.conserved(np.ones_like(X), np.where(X < 0.5, -2.0, 2.0), np.zeros_like(X), np.full_like(X, p0))
+    a0 = oracle.alpha0(s, W0)
+    rc, Wo, ao, to, dts_o, st = oracle.run(s, W0, a0, 50)
+    assert rc == 5
+    from paper_2402_10914_gb300 import _lib
+    with Solver(s) as sol:
+        sol.set_ic(W0)
+        with pytest.raises(_lib.DfgksError) as e:
+            sol.step(50)
+        assert e.value.status == _lib.ENONPOS
+        W, a, t, step = sol.get_state()
+        fstep, fi, fj = sol.last_error()
+    assert step == len(dts_o) == fstep
+    assert comp_rel_err(W, Wo) <= 1e-12
+    assert (fi, fj) == (st.fail_i, st.fail_j)
+
+
+def test_stage_operator_argument_errors():
+    from paper_2402_10914_gb300 import _lib
+    w = rough(8, 8, seed=1, flux=I.GKS)
+    with Solver(w.settings) as sol:
+        Wd, ad = dev(w.W0), dev(np.ones((8, 8)))
+        with pytest.raises(_lib.DfgksError):
+            sol.residual(Wd, ad, 0.0)
+        with pytest.raises(_lib.DfgksError):
+            sol.residual(Wd, ad, 1e-3, flux=7)
