@@ -1259,7 +1259,8 @@ int oracle_run(const oracle_cfg* cfg, double* W, double* alpha, double* t, int n
                 a_next = o3.alpha_next;
                 if (!check_state(C, Fnext, fi, fj)) fail = true;
             }
-            local.fallbacks += o1.cnt.fallbacks + o2.cnt.fallbacks + o3.cnt.fallbacks;
+            const Counters* cs[3] = {&o1.cnt, &o2.cnt, &o3.cnt};
+            for (const Counters* c : cs) { local.fallbacks += c->fallbacks; local.df_normal += c->df_n; local.df_tangential += c->df_t; }
         }
         if (fail) { local.fail_step = done; local.fail_i = fi; local.fail_j = fj; rc = 5; break; }
         for (int k = 0; k < 4; ++k) Fn.w[k] = Fnext.w[k];

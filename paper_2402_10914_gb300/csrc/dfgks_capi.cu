@@ -312,23 +312,23 @@ static void enqueue_step(dfgks* h, int s, double dt, int flux, double t_end, int
     if (h->cfg.time_scheme == DFGKS_TIME_S2O4) {
         for (int d = 0; d < 2; ++d) launch_sweep(d, m, S, flux, false, in, ain, dtp, h->B, h->st, halt, st, T);
         a.Win = in; a.Wout = h->Ws; a.acc = h->acc;
-        launch_update(UM_S2O4_1, m, S, a, h->B, dtp, h->st, halt, st);
+        launch_update(UM_S2O4_1, m, S, a, h->B, dtp, h->st, halt, st, T);
         launch_fill_ghosts(m, h->Ws, nullptr, halt, st, T);
         for (int d = 0; d < 2; ++d) launch_sweep(d, m, S, flux, false, h->Ws, ain, dtp, h->B, h->st, halt, st, T);
         a.Win = h->Ws; a.Wout = out; a.alpha_out = aout;
-        launch_update(UM_S2O4_2, m, S, a, h->B, dtp, h->st, halt, st);
+        launch_update(UM_S2O4_2, m, S, a, h->B, dtp, h->st, halt, st, T);
     } else {
         for (int d = 0; d < 2; ++d) launch_sweep(d, m, S, flux, false, in, ain, dtp, h->B, h->st, halt, st, T);
         a.Win = in; a.Wout = h->Ws;
-        launch_update(UM_RK_1, m, S, a, h->B, dtp, h->st, halt, st);
+        launch_update(UM_RK_1, m, S, a, h->B, dtp, h->st, halt, st, T);
         launch_fill_ghosts(m, h->Ws, nullptr, halt, st, T);
         for (int d = 0; d < 2; ++d) launch_sweep(d, m, S, flux, false, h->Ws, ain, dtp, h->B, h->st, halt, st, T);
         a.Wn = in; a.Win = h->Ws; a.Wout = out;
-        launch_update(UM_RK_2, m, S, a, h->B, dtp, h->st, halt, st);
+        launch_update(UM_RK_2, m, S, a, h->B, dtp, h->st, halt, st, T);
         launch_fill_ghosts(m, out, nullptr, halt, st, T);
         for (int d = 0; d < 2; ++d) launch_sweep(d, m, S, flux, false, out, ain, dtp, h->B, h->st, halt, st, T);
         a.Wn = in; a.Win = out; a.Wout = out; a.alpha_out = aout;
-        launch_update(UM_RK_3, m, S, a, h->B, dtp, h->st, halt, st);
+        launch_update(UM_RK_3, m, S, a, h->B, dtp, h->st, halt, st, T);
     }
     launch_end_step(h->st, t_end, st, T);
 }
@@ -398,9 +398,14 @@ extern "C" dfgks_status dfgks_residual(dfgks* h, const double* W, const double* 
 
 extern "C" dfgks_status dfgks_face_records(dfgks* h, const double* W, const double* alpha, double dt, int flux,
                                            int dir, double* out) {
-    if (!h || !out || (dir != 0 && dir != 1)) return DFGKS_EINVAL;
-    dfgks_status r = run_stage_operator(h, W, alpha, dt, flux);
-    if (r) return r;
+    if (!h || !out || !W || !alpha || (dir != 0 && dir != 1) || !(dt > 0.0) || (flux != 0 && flux != 1))
+        return DFGKS_EINVAL;
+    // only the requested direction is swept: the Gauss-point buffer is shared by both directions
+    launch_dense_to_ghosted(h->mesh, W, 4, h->Ws, h->stream);
+    launch_dense_to_ghosted(h->mesh, alpha, 1, h->As, h->stream);
+    launch_fill_ghosts(h->mesh, h->Ws, h->As, nullptr, h->stream);
+    launch_set_scalar(h->dt_scratch, dt, h->stream);
+    launch_sweep(dir, h->mesh, h->S, flux, false, h->Ws, h->As, h->dt_scratch, h->B, nullptr, nullptr, h->stream);
     launch_pack_faces(dir, h->mesh, h->B, out, h->stream);
     CK_LAUNCH();
     return DFGKS_OK;

@@ -30,3 +30,25 @@ def field_err(a, b, floor_frac=1e-3):
     a = np.moveaxis(np.asarray(a, dtype=np.float64), -1, 0)
     b = np.moveaxis(np.asarray(b, dtype=np.float64), -1, 0)
     return comp_rel_err(a, b, floor_frac)
+
+
+def oracle_envelope(settings, W0, nsteps, t_end=0.0, dt_fixed=0.0, seeds=(101, 202)):
+    """The oracle's own response to rounding-level input noise.
+
+    Runs the oracle from W0 and from W0 * (1 + 1e-15 N(0,1)) (one run per seed) and returns
+    (reference run, max per-component relative difference, max relative L1 difference).  Where
+    the step map amplifies rounding (the time limiter, strong jumps), no second implementation
+    can agree with the oracle more closely than the oracle agrees with itself under this noise."""
+    import oracle
+    a0 = oracle.alpha0(settings, W0)
+    ref = oracle.run(settings, W0, a0, nsteps, dt_fixed=dt_fixed, t_end=t_end)
+    worst_max, worst_l1 = 0.0, 0.0
+    for sd in seeds:
+        rng = np.random.default_rng(sd)
+        W2 = W0 * (1.0 + 1e-15 * rng.standard_normal(W0.shape))
+        r2 = oracle.run(settings, W2, oracle.alpha0(settings, W2), nsteps, dt_fixed=dt_fixed, t_end=t_end)
+        if r2[0] != ref[0] or r2[1].shape != ref[1].shape:
+            continue
+        worst_max = max(worst_max, comp_rel_err(r2[1], ref[1]))
+        worst_l1 = max(worst_l1, l1_rel(r2[1], ref[1]))
+    return ref, worst_max, worst_l1
