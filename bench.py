@@ -42,6 +42,10 @@ FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
 # 2*DFMA + DADD + DMUL of one launch divided by its 2*(n+1)*n Gauss points
 # (profiles/k_flux_gks_fp64_counts_quadrants128.md).  Valid for the kernel source it was measured on.
 FLUX_GKS_FLOPS_PER_GP = 1968.0
+# DRAM bytes (read + write) per launch of that kernel on this workload, mean of the x and y launches
+# of one ncu capture at 400 x 400 (profiles/k_flux_gks_traffic_quadrants400.md); None once the
+# kernel has changed since the capture.
+FLUX_GKS_TRAFFIC_BYTES = 65.5e6
 
 
 def parse():
@@ -177,7 +181,8 @@ def bench_ours(args, ws, rank, local):
     gps_per_launch = 2.0 * (s.nx + 1) * s.ny       # x- and y-sweeps have the same count on a square mesh
     roof = {"kernel": "k_flux<GKS> (Gauss-point flux)", "bound": "alu", "unit": "GFLOP/s",
             "peak": round(FP64_PEAK_GFLOPS, 1), "peak_source": "derived: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz",
-            "avg_launch_ms": avg_flux_ms, "launches_timed": fl["timed"], "traffic": None,
+            "avg_launch_ms": avg_flux_ms, "launches_timed": fl["timed"], "traffic": FLUX_GKS_TRAFFIC_BYTES,
+            "traffic_unit": "B per launch (ncu dram read+write)",
             "kernel_time_share": {k: round(v / max(sum(share.values()), 1e-30), 4) for k, v in share.items()},
             "dominant_kernel_class": dominant}
     if FLUX_GKS_FLOPS_PER_GP is not None:
