@@ -128,6 +128,22 @@ DFGKS_API dfgks_status dfgks_step(dfgks* h, int n, double dt, int flux, double t
 DFGKS_API dfgks_status dfgks_residual(dfgks* h, const double* W, const double* alpha, double dt, int flux,
                             double* L, double* dtL, double* dtLt, double* alpha_next);
 
+/* The stage operator of dfgks_residual for callers that cannot allocate device memory (code that
+ * runs while a CUDA graph is being built, hosts whose device memory belongs to their own pool
+ * allocator, latency-bound loops).  The paper has no counterpart; this is a deployment variant.
+ * Takes a configuration instead of a handle; inputs and outputs as in dfgks_residual (device
+ * memory, dense [4][ny][nx] / [ny][nx]; outputs may be NULL); work is ordered on `stream`
+ * (a cudaStream_t, or NULL for the legacy default stream).  No cudaMalloc or cudaFree is called:
+ * every intermediate lives in one file-scope 16 MiB device array that each GPU using the library
+ * holds until exit.  Meshes above 128 x 128 = 16384 cells are rejected with DFGKS_EINVAL.
+ * The first call on a device looks up that array's device address (cudaGetSymbolAddress) with the
+ * device current; make that first call before any stream capture.  All calls share the array and
+ * it keeps the last call's contents: calls that overlap on the GPU (different streams, concurrent
+ * graphs) race on it and must be serialised by the caller. */
+DFGKS_API dfgks_status dfgks_residual_noalloc(const dfgks_config* cfg, void* stream,
+                                              const double* W, const double* alpha, double dt, int flux,
+                                              double* L, double* dtL, double* dtLt, double* alpha_next);
+
 /* Vector-Jacobian product of dfgks_residual with respect to W, with alpha, dt and every branch
  * decision (DF switch, fallback, |.| and min/max kinks) held at the values of the forward pass:
  *   W_bar += (dL/dW)^T L_bar + (d dtL/dW)^T dtL_bar + (d dtLt/dW)^T dtLt_bar.

@@ -59,6 +59,7 @@ SIGNATURES = {
     "dfgks_set_timing": [_V, C.c_int],
     "dfgks_get_timing": [_V, _V, _V, _V, C.c_int],
     "dfgks_probe_fp64": [C.c_int, _D, _D],
+    "dfgks_residual_noalloc": [C.POINTER(Config), _V, _V, _V, C.c_double, C.c_int, _V, _V, _V, _V],
 }
 
 
