@@ -41,11 +41,11 @@ FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
 # FP64 flops the Gauss-point flux kernel executes per Gauss point (GKS): ncu instruction counts
 # 2*DFMA + DADD + DMUL of one launch divided by its 2*(n+1)*n Gauss points
 # (profiles/k_flux_gks_fp64_counts_quadrants128.md).  Valid for the kernel source it was measured on.
-FLUX_GKS_FLOPS_PER_GP = 1968.0
+FLUX_GKS_FLOPS_PER_GP = 1866.0
 # DRAM bytes (read + write) per launch of that kernel on this workload, mean of the x and y launches
 # of one ncu capture at 400 x 400 (profiles/k_flux_gks_traffic_quadrants400.md); None once the
 # kernel has changed since the capture.
-FLUX_GKS_TRAFFIC_BYTES = 65.5e6
+FLUX_GKS_TRAFFIC_BYTES = 65.1e6
 
 
 def parse():
@@ -55,6 +55,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--n", type=int, default=400, help="mesh side of the four-quadrant workload")
+    p.add_argument("--workload", default="quadrants", choices=["quadrants", "batch"],
+                   help="quadrants: the 400x400 GKS step (default); batch: the 64-problem uneven batch")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     return p.parse_args()
@@ -235,6 +237,71 @@ def bench_ours(args, ws, rank, local):
     }
 
 
+def bench_batch(args):
+    """The 64-problem uneven batch (sides 64..512, mixed GKS / L-F, own dt each): one launch per
+    phase over all problems replayed from a CUDA graph, against per-problem launches of the same
+    kernels one problem after another on one stream.  Both advance every problem K steps."""
+    import torch
+    from paper_2402_10914_gb300 import inputs as I
+    from paper_2402_10914_gb300.solver import BatchSolver, Solver
+    ws = I.batch()
+    cells = sum(w.settings.nx * w.settings.ny for w in ws)
+    units = 2.0 * cells * args.steps
+    flush = torch.empty(32 * 1024 * 1024, dtype=torch.float64, device="cuda")
+    b = BatchSolver([w.settings for w in ws])
+    for p, w in enumerate(ws):
+        b.set_ic(p, w.W0)
+    shapes, _ = b.autotune()
+    from paper_2402_10914_gb300 import _lib
+    b.step(args.warmup, use_graph=True)
+    before = [b.status(p)["step"] for p in range(len(ws))]
+    flush.fill_(1.0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rc = b.step(args.steps, use_graph=True)
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    done_batch = [b.status(p)["step"] - before[p] for p in range(len(ws))]
+    failed = [p for p in range(len(ws)) if b.status(p)["err"]]
+    b.close()
+    # a problem that loses positivity stops at its last good step in both paths; count the
+    # cell-stages actually completed
+    units = sum(2.0 * w.settings.nx * w.settings.ny * d for w, d in zip(ws, done_batch))
+    sols = [Solver(w.settings) for w in ws]
+    for s, w in zip(sols, ws):
+        s.set_ic(w.W0)
+        try:
+            s.step(args.warmup)
+        except _lib.DfgksError:
+            pass
+    flush.fill_(2.0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    done_seq = []
+    for s in sols:
+        try:
+            d, _ = s.step(args.steps)
+        except _lib.DfgksError:
+            d = -1
+        done_seq.append(d)
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t0
+    done_seq = [s.get_state()[3] - args.warmup if d < 0 else d for s, d in zip(sols, done_seq)]
+    units_seq = sum(2.0 * w.settings.nx * w.settings.ny * max(d, 0) for w, d in zip(ws, done_seq))
+    for s in sols:
+        s.close()
+    line = {"metric": "FP64 cell-stage updates/s (64-problem uneven batch, mixed GKS/L-F)", "value": units / t_batch,
+            "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t_batch / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "batch64_uneven_seed1000", "problems": len(ws), "cells": cells,
+                       "sides": sorted(set(w.settings.nx for w in ws)), "shapes": shapes, "status": rc,
+                       "problems_lost_positivity": failed, "l2": "one 256 MiB flush before each timed region"},
+            "per_problem_sequential": {"value": units_seq / t_seq, "ms_per_step": t_seq / args.steps * 1e3},
+            "speedup_vs_per_problem": (units / t_batch) / (units_seq / t_seq)}
+    print(json.dumps(line))
+
+
 def oracle_sample(n_threads=None, steps=1, n=400):
     """The CPU oracle as it stands on one full S2O4 step of the same workload."""
     import oracle
@@ -282,6 +349,10 @@ def main():
 
     import __graft_entry__
     __graft_entry__.build()
+    if args.workload == "batch":
+        if rank == 0:
+            bench_batch(args)
+        return
     r = bench_ours(args, ws, rank, local)
     if rank != 0:
         return

@@ -153,6 +153,36 @@ DFGKS_API dfgks_status dfgks_adjoint_residual(dfgks* h, const double* W, const d
                                     const double* L_bar, const double* dtL_bar, const double* dtLt_bar,
                                     double* W_bar);
 
+/* ---- Batched problems ----------------------------------------------------------------------
+ * Many independent problems (each its own mesh size, boundary conditions, flux solver and CFL dt)
+ * advanced together: every phase of a step is one launch over all problems, and the step's launch
+ * sequence can be captured once in a CUDA graph and replayed.  Not part of the paper (a throughput
+ * mode for many small problems on one GPU).  S2O4 only (time_scheme 0).  Each problem's state,
+ * alpha, dt, time and step counter are its own; a problem that loses positivity stops at its last
+ * good step while the others continue. */
+typedef struct dfgks_batch dfgks_batch;
+
+/* cfgs[np], flux[np] (dfgks_flux); stream NULL creates a private stream (graph capture needs a
+ * non-default stream).  Allocates every problem's buffers. */
+DFGKS_API dfgks_status dfgks_batch_create(const dfgks_config* cfgs, const int* flux, int np, void* stream,
+                                          dfgks_batch** out);
+DFGKS_API dfgks_status dfgks_batch_destroy(dfgks_batch* b);
+/* Initial state of problem p (host if on_device == 0); alpha^0 as in dfgks_set_ic; ENONPHYS on bad data. */
+DFGKS_API dfgks_status dfgks_batch_set_ic(dfgks_batch* b, int p, const double* W, int on_device);
+/* Advance every problem n steps; use_graph != 0 replays a captured CUDA graph of one step.
+ * Returns DFGKS_ENONPOS if any problem lost positivity (see dfgks_batch_status). */
+DFGKS_API dfgks_status dfgks_batch_step(dfgks_batch* b, int n, int use_graph);
+DFGKS_API dfgks_status dfgks_batch_get_state(dfgks_batch* b, int p, double* W, double* alpha, double* t, long* step,
+                                             int on_device);
+/* Step count, error flag (0 or DFGKS_ENONPOS) and normal DF-branch count of problem p. */
+DFGKS_API dfgks_status dfgks_batch_status(dfgks_batch* b, int p, long* step, int* err, unsigned long long* df_normal);
+/* Block shapes (bx, by), bx*by = 128, bx a multiple of 32, of the face-line, tangential and flux kernels. */
+DFGKS_API dfgks_status dfgks_batch_set_shapes(dfgks_batch* b, const int* shapes6);
+/* Pick those shapes by timing one batched step per candidate (32x4, 64x2, 128x1), kernel class by
+ * class; states are saved and restored around the trials.  shapes6 (may be NULL) receives the
+ * choice, best_ms (may be NULL) the last class's best step time. */
+DFGKS_API dfgks_status dfgks_batch_autotune(dfgks_batch* b, int* shapes6, double* best_ms);
+
 /* Per-face intermediates of one stage, for diagnostics and kernel-by-kernel comparison.
  * dir 0: x-faces, [ny][nx+1] (face index fastest); dir 1: y-faces, [nx][ny+1].
  * Per face 59 doubles: F[4], dtF[4] (global frame, Gauss-averaged), omega^t, alpha_{p,1},

@@ -60,6 +60,14 @@ SIGNATURES = {
     "dfgks_get_timing": [_V, _V, _V, _V, C.c_int],
     "dfgks_probe_fp64": [C.c_int, _D, _D],
     "dfgks_residual_noalloc": [C.POINTER(Config), _V, _V, _V, C.c_double, C.c_int, _V, _V, _V, _V],
+    "dfgks_batch_create": [_V, _V, C.c_int, _V, C.POINTER(_V)],
+    "dfgks_batch_destroy": [_V],
+    "dfgks_batch_set_ic": [_V, C.c_int, _V, C.c_int],
+    "dfgks_batch_step": [_V, C.c_int, C.c_int],
+    "dfgks_batch_get_state": [_V, C.c_int, _V, _V, _D, C.POINTER(C.c_long), C.c_int],
+    "dfgks_batch_status": [_V, C.c_int, C.POINTER(C.c_long), C.POINTER(C.c_int), C.POINTER(C.c_ulonglong)],
+    "dfgks_batch_set_shapes": [_V, _V],
+    "dfgks_batch_autotune": [_V, _V, _D],
 }
 
 

@@ -1,0 +1,597 @@
+// dfgks_batch.cu -- many independent problems of uneven mesh sizes advanced together.
+//
+// Every phase of a step (CFL dt, ghost fill, the three sweep kernels per direction and stage, the
+// stage update, bookkeeping) is one launch over all problems: each thread block looks its problem
+// up in a prefix table of per-problem block counts and runs the same per-thread body as the
+// single-problem kernels (dfgks_bodies.cuh), so small meshes fill the GPU together instead of
+// one after another.  Each problem keeps its own device-resident dt, time, halt flag and state
+// buffer parity, so one step is the same launch sequence for every step: it is captured once in
+// a CUDA graph and replayed.  The block shape of the sweep kernels is chosen by an autotuner.
+#include <cuda_runtime.h>
+#include <float.h>
+#include <string.h>
+#include <new>
+#include <vector>
+
+#include "../../include/dfgks.h"
+#include "dfgks_bodies.cuh"
+
+using namespace dfk;
+
+namespace {
+
+struct BatchProblem {
+    Mesh m;
+    SchemeConsts S;
+    int flux;
+    double* W[2];
+    double* A[2];
+    double* Ws;
+    double* acc;
+    SweepBuffers B;
+    DevState* st;
+};
+
+// Phases with a per-problem block grid.  For the sweep kernels the block shape (bx x by, 128
+// threads) is tunable; the grid of a problem follows from its mesh and that shape.
+enum Phase { PH_GX = 0, PH_GY, PH_CFL, PH_LINES0, PH_LINES1, PH_FACES0, PH_FACES1, PH_FLUX0, PH_FLUX1, PH_UPD,
+             PH_COUNT };
+
+struct Shape { int bx, by; };
+
+__host__ __device__ inline void phase_grid(int ph, const Mesh& m, Shape sh, int& gx, int& gy, int& gz) {
+    gz = 1;
+    switch (ph) {
+        case PH_GX: gx = (m.ny + 31) / 32; gy = 1; break;
+        case PH_GY: gx = (m.nx + 2 * G + 127) / 128; gy = 2 * G; break;
+        case PH_CFL: gx = (m.nx * m.ny + 255) / 256; gy = 1; break;
+        case PH_LINES0: gx = (m.nx + 1 + sh.bx - 1) / sh.bx; gy = (m.ny + 4 + sh.by - 1) / sh.by; break;
+        case PH_LINES1: gx = (m.nx + 4 + sh.bx - 1) / sh.bx; gy = (m.ny + 1 + sh.by - 1) / sh.by; break;
+        case PH_FACES0: case PH_FLUX0: gx = (m.nx + 1 + sh.bx - 1) / sh.bx; gy = (m.ny + sh.by - 1) / sh.by; gz = 2; break;
+        case PH_FACES1: case PH_FLUX1: gx = (m.nx + sh.bx - 1) / sh.bx; gy = (m.ny + 1 + sh.by - 1) / sh.by; gz = 2; break;
+        default: gx = (m.nx + 31) / 32; gy = (m.ny + 7) / 8; break;   // PH_UPD, 32 x 8
+    }
+}
+
+struct BlockMap {
+    const int* start;     // device: np + 1 prefix of block counts
+    int np;
+    Shape sh;
+};
+
+// problem of this block and the block's (bx, by, bz) inside that problem's grid
+__device__ __forceinline__ int locate(const BlockMap& bm, int ph, const BatchProblem* P, int& bx, int& by, int& bz) {
+    int lo = 0, hi = bm.np;                 // start[lo] <= blockIdx.x < start[hi]
+    const int b = blockIdx.x;
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (bm.start[mid] <= b) lo = mid; else hi = mid;
+    }
+    int gx, gy, gz;
+    phase_grid(ph, P[lo].m, bm.sh, gx, gy, gz);
+    int local = b - bm.start[lo];
+    bx = local % gx;
+    by = (local / gx) % gy;
+    bz = local / (gx * gy);
+    return lo;
+}
+
+__global__ void kb_cfl(const BatchProblem* P, BlockMap bm) {
+    int bx, by, bz;
+    const int p = locate(bm, PH_CFL, P, bx, by, bz);
+    const BatchProblem& q = P[p];
+    if (q.st->halt) return;
+    const int c = bx * 256 + threadIdx.x;
+    double v = c < q.m.nx * q.m.ny ? cfl_cell(q.m, q.W[q.st->par], q.S.gamma, c) : DBL_MAX;
+    v = block_min(v);
+    if (threadIdx.x == 0 && v > 0.0) atomicMin(&q.st->dtmin_bits, (unsigned long long)__double_as_longlong(v));
+}
+
+__global__ void kb_begin_step(const BatchProblem* P, const double* cfl, int np, double t_end) {
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    DevState* st = P[p].st;
+    const double dtmin = __longlong_as_double((long long)st->dtmin_bits);
+    st->dtmin_bits = (unsigned long long)__double_as_longlong(DBL_MAX);
+    if (st->halt) return;
+    if (t_end > 0.0 && st->t >= t_end) { st->halt = 1; return; }
+    double dt = cfl[p] * dtmin;
+    st->clipped = 0;
+    if (t_end > 0.0 && st->t + dt >= t_end - 1e-12 * fabs(t_end)) { dt = t_end - st->t; st->clipped = 1; }
+    st->dt = dt;
+}
+
+__global__ void kb_end_step(const BatchProblem* P, int np, double t_end) {
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    DevState* st = P[p].st;
+    if (st->halt) return;
+    st->t = st->clipped ? t_end : st->t + st->dt;
+    st->step += 1;
+    st->par ^= 1;
+}
+
+// stage 0 reads W^n (and fills alpha^n ghosts), stage 1 reads W*
+__global__ void kb_ghost_x(const BatchProblem* P, BlockMap bm, int stage) {
+    int bx, by, bz;
+    const int p = locate(bm, PH_GX, P, bx, by, bz);
+    const BatchProblem& q = P[p];
+    if (q.st->halt) return;
+    double* W = stage == 0 ? q.W[q.st->par] : q.Ws;
+    double* A = stage == 0 ? q.A[q.st->par] : nullptr;
+    ghost_x_body(q.m, W, A, threadIdx.x, bx * blockDim.y + threadIdx.y);
+}
+
+__global__ void kb_ghost_y(const BatchProblem* P, BlockMap bm, int stage) {
+    int bx, by, bz;
+    const int p = locate(bm, PH_GY, P, bx, by, bz);
+    const BatchProblem& q = P[p];
+    if (q.st->halt) return;
+    double* W = stage == 0 ? q.W[q.st->par] : q.Ws;
+    double* A = stage == 0 ? q.A[q.st->par] : nullptr;
+    ghost_y_body(q.m, W, A, bx * blockDim.x + threadIdx.x - G, by);
+}
+
+template <int DIR>
+__global__ void __launch_bounds__(128) kb_lines(const BatchProblem* P, BlockMap bm, int stage) {
+    int bx, by, bz;
+    const int p = locate(bm, DIR == 0 ? PH_LINES0 : PH_LINES1, P, bx, by, bz);
+    const BatchProblem& q = P[p];
+    if (q.st->halt) return;
+    const int par = q.st->par;
+    const double* W = stage == 0 ? q.W[par] : q.Ws;
+    int ndf = lines_body<DIR>(q.m, q.S, W, q.A[par], q.B.lines, q.B.line_stride, bx * bm.sh.bx + threadIdx.x,
+                              by * bm.sh.by + threadIdx.y);
+    warp_count_add(&q.st->df_normal, ndf);
+}
+
+template <int DIR>
+__global__ void __launch_bounds__(128) kb_faces(const BatchProblem* P, BlockMap bm, int stage) {
+    int bx, by, bz;
+    const int p = locate(bm, DIR == 0 ? PH_FACES0 : PH_FACES1, P, bx, by, bz);
+    const BatchProblem& q = P[p];
+    if (q.st->halt) return;
+    const int par = q.st->par;
+    const double* W = stage == 0 ? q.W[par] : q.Ws;
+    int nfb;
+    int ndf = faces_body<DIR>(q.m, q.S, W, q.A[par], q.B.lines, q.B.line_stride, q.B.gp, q.B.gp_stride,
+                              bx * bm.sh.bx + threadIdx.x, by * bm.sh.by + threadIdx.y, bz, nfb);
+    warp_count_add(&q.st->df_tangential, ndf);
+    warp_count_add(&q.st->fallbacks, nfb);
+}
+
+template <int DIR>
+__global__ void __launch_bounds__(128) kb_flux(const BatchProblem* P, BlockMap bm) {
+    int bx, by, bz;
+    const int p = locate(bm, DIR == 0 ? PH_FLUX0 : PH_FLUX1, P, bx, by, bz);
+    const BatchProblem& q = P[p];
+    if (q.st->halt) return;
+    const int ax = bx * bm.sh.bx + threadIdx.x, ay = by * bm.sh.by + threadIdx.y;
+    if (q.flux == 0)
+        flux_body<DIR, 0, false>(q.m, q.S, q.B.lines, q.B.line_stride, q.B.gp, q.B.gp_stride, q.B.flux[DIR],
+                                 q.B.flux_stride[DIR], q.st->dt, ax, ay, bz);
+    else
+        flux_body<DIR, 1, false>(q.m, q.S, q.B.lines, q.B.line_stride, q.B.gp, q.B.gp_stride, q.B.flux[DIR],
+                                 q.B.flux_stride[DIR], q.st->dt, ax, ay, bz);
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(256) kb_update(const BatchProblem* P, BlockMap bm) {
+    int bx, by, bz;
+    const int p = locate(bm, PH_UPD, P, bx, by, bz);
+    const BatchProblem& q = P[p];
+    if (q.st->halt) return;
+    const int par = q.st->par;
+    UpdateArgs a;
+    a.Wn = nullptr; a.L = nullptr; a.dtL = nullptr; a.dtLt = nullptr; a.alpha_dense = 0;
+    a.acc = q.acc;
+    if (MODE == UM_S2O4_1) { a.Win = q.W[par]; a.Wout = q.Ws; a.alpha_out = nullptr; }
+    else { a.Win = q.Ws; a.Wout = q.W[par ^ 1]; a.alpha_out = q.A[par ^ 1]; }
+    update_body<MODE>(q.m, q.S, a, q.B.flux[0], q.B.flux_stride[0], q.B.flux[1], q.B.flux_stride[1], q.st->dt, q.st,
+                      bx * 32 + threadIdx.x, by * 8 + threadIdx.y);
+}
+
+}  // namespace
+
+struct dfgks_batch {
+    int np;
+    cudaStream_t stream;
+    bool own_stream;
+    std::vector<BatchProblem> host;      // descriptors (device pointers inside)
+    BatchProblem* dev;                   // device copy
+    DevState* st;                        // np device states
+    DevState* st_host;                   // pinned mirror
+    double* cfl;                         // per-problem CFL numbers (device)
+    int* starts;                         // PH_COUNT x (np + 1) prefix tables (device)
+    std::vector<int> hstarts;
+    int total[PH_COUNT];
+    Shape shape[3];                      // lines, faces, flux
+    std::vector<void*> allocs;
+    unsigned long long bytes;
+    cudaGraphExec_t graph;
+    bool graph_ok;
+    double t_end;
+};
+
+static dfgks_status cst(cudaError_t e) {
+    return e == cudaSuccess ? DFGKS_OK : (e == cudaErrorMemoryAllocation ? DFGKS_ENOMEM : DFGKS_ECUDA);
+}
+#define BCK(call) do { cudaError_t e_ = (call); if (e_ != cudaSuccess) return cst(e_); } while (0)
+
+static long long rup(long long n, long long a) { return (n + a - 1) / a * a; }
+
+static Shape shape_of(const dfgks_batch* b, int ph) {
+    if (ph == PH_LINES0 || ph == PH_LINES1) return b->shape[0];
+    if (ph == PH_FACES0 || ph == PH_FACES1) return b->shape[1];
+    if (ph == PH_FLUX0 || ph == PH_FLUX1) return b->shape[2];
+    return Shape{32, 4};
+}
+
+static dfgks_status build_maps(dfgks_batch* b) {
+    b->hstarts.assign((size_t)PH_COUNT * (b->np + 1), 0);
+    for (int ph = 0; ph < PH_COUNT; ++ph) {
+        int acc = 0;
+        for (int p = 0; p < b->np; ++p) {
+            int gx, gy, gz;
+            phase_grid(ph, b->host[p].m, shape_of(b, ph), gx, gy, gz);
+            b->hstarts[(size_t)ph * (b->np + 1) + p] = acc;
+            acc += gx * gy * gz;
+        }
+        b->hstarts[(size_t)ph * (b->np + 1) + b->np] = acc;
+        b->total[ph] = acc;
+    }
+    BCK(cudaMemcpyAsync(b->starts, b->hstarts.data(), b->hstarts.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream));
+    BCK(cudaStreamSynchronize(b->stream));
+    return DFGKS_OK;
+}
+
+static BlockMap bmap(const dfgks_batch* b, int ph) {
+    BlockMap m;
+    m.start = b->starts + (size_t)ph * (b->np + 1);
+    m.np = b->np;
+    m.sh = shape_of(b, ph);
+    return m;
+}
+
+static void enqueue_batch_step(dfgks_batch* b) {
+    cudaStream_t s = b->stream;
+    const BatchProblem* P = b->dev;
+    const int np = b->np, tb = 128, nb = (np + tb - 1) / tb;
+    kb_cfl<<<b->total[PH_CFL], 256, 0, s>>>(P, bmap(b, PH_CFL));
+    kb_begin_step<<<nb, tb, 0, s>>>(P, b->cfl, np, b->t_end);
+    for (int stage = 0; stage < 2; ++stage) {
+        kb_ghost_x<<<b->total[PH_GX], dim3(2 * G, 32), 0, s>>>(P, bmap(b, PH_GX), stage);
+        kb_ghost_y<<<b->total[PH_GY], 128, 0, s>>>(P, bmap(b, PH_GY), stage);
+        for (int d = 0; d < 2; ++d) {
+            const int phl = d == 0 ? PH_LINES0 : PH_LINES1, phf = d == 0 ? PH_FACES0 : PH_FACES1;
+            const int phx = d == 0 ? PH_FLUX0 : PH_FLUX1;
+            dim3 bl(b->shape[0].bx, b->shape[0].by), bf(b->shape[1].bx, b->shape[1].by), bx(b->shape[2].bx, b->shape[2].by);
+            if (d == 0) {
+                kb_lines<0><<<b->total[phl], bl, 0, s>>>(P, bmap(b, phl), stage);
+                kb_faces<0><<<b->total[phf], bf, 0, s>>>(P, bmap(b, phf), stage);
+                kb_flux<0><<<b->total[phx], bx, 0, s>>>(P, bmap(b, phx));
+            } else {
+                kb_lines<1><<<b->total[phl], bl, 0, s>>>(P, bmap(b, phl), stage);
+                kb_faces<1><<<b->total[phf], bf, 0, s>>>(P, bmap(b, phf), stage);
+                kb_flux<1><<<b->total[phx], bx, 0, s>>>(P, bmap(b, phx));
+            }
+        }
+        if (stage == 0) kb_update<UM_S2O4_1><<<b->total[PH_UPD], dim3(32, 8), 0, s>>>(P, bmap(b, PH_UPD));
+        else kb_update<UM_S2O4_2><<<b->total[PH_UPD], dim3(32, 8), 0, s>>>(P, bmap(b, PH_UPD));
+    }
+    kb_end_step<<<nb, tb, 0, s>>>(P, np, b->t_end);
+}
+
+static void free_batch(dfgks_batch* b) {
+    if (b->graph_ok) cudaGraphExecDestroy(b->graph);
+    for (void* p : b->allocs) cudaFree(p);
+    if (b->st_host) cudaFreeHost(b->st_host);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+}
+
+template <class T>
+static cudaError_t balloc(dfgks_batch* b, T** p, size_t n) {
+    cudaError_t e = cudaMalloc((void**)p, n * sizeof(T));
+    if (e == cudaSuccess) { b->allocs.push_back((void*)*p); b->bytes += n * sizeof(T); }
+    return e;
+}
+
+static bool batch_config_ok(const dfgks_config* c) {
+    if (!c || c->nx < 1 || c->ny < 1 || c->nx > 8192 || c->ny > 8192) return false;
+    if (!(c->x1 > c->x0) || !(c->y1 > c->y0) || !(c->gamma > 1.0) || !(c->cfl > 0.0) || !(c->eps > 0.0)) return false;
+    if (!(c->dH > 0.0 && c->dH <= 1.0) || !(c->dL >= 0.0 && c->dL <= 1.0) || !(c->C1 >= 0.0) || !(c->C2 >= 0.0)) return false;
+    const int bcs[4] = {c->bc_xlo, c->bc_xhi, c->bc_ylo, c->bc_yhi};
+    for (int k = 0; k < 4; ++k) if (bcs[k] < 0 || bcs[k] > 2) return false;
+    if ((c->bc_xlo == 0) != (c->bc_xhi == 0) || (c->bc_ylo == 0) != (c->bc_yhi == 0)) return false;
+    if (c->bc_xlo == 0 && c->nx < G) return false;
+    if (c->bc_ylo == 0 && c->ny < G) return false;
+    return c->time_scheme == 0 && (c->tau_reading == 0 || c->tau_reading == 1);
+}
+
+extern "C" DFGKS_API dfgks_status dfgks_batch_create(const dfgks_config* cfgs, const int* flux, int np, void* stream,
+                                                     dfgks_batch** out) {
+    if (!out || !cfgs || !flux || np < 1 || np > 65536) return DFGKS_EINVAL;
+    *out = nullptr;
+    for (int p = 0; p < np; ++p)
+        if (!batch_config_ok(&cfgs[p]) || (flux[p] != 0 && flux[p] != 1)) return DFGKS_EINVAL;
+    dfgks_batch* b = new (std::nothrow) dfgks_batch();
+    if (!b) return DFGKS_ENOMEM;
+    b->np = np;
+    b->bytes = 0;
+    b->graph_ok = false;
+    b->t_end = 0.0;
+    b->st_host = nullptr;
+    b->dev = nullptr;
+    b->shape[0] = b->shape[1] = b->shape[2] = Shape{32, 4};
+    if (stream) { b->stream = (cudaStream_t)stream; b->own_stream = false; }
+    else if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) { delete b; return DFGKS_ECUDA; }
+    else b->own_stream = true;
+    cudaError_t e = balloc(b, &b->st, (size_t)np);
+    if (e == cudaSuccess) e = balloc(b, &b->dev, (size_t)np);
+    if (e == cudaSuccess) e = balloc(b, &b->cfl, (size_t)np);
+    if (e == cudaSuccess) e = balloc(b, &b->starts, (size_t)PH_COUNT * (np + 1));
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&b->st_host, (size_t)np * sizeof(DevState));
+    std::vector<double> cfl(np);
+    b->host.resize(np);
+    for (int p = 0; p < np && e == cudaSuccess; ++p) {
+        const dfgks_config* c = &cfgs[p];
+        BatchProblem& q = b->host[p];
+        memset(&q, 0, sizeof(q));
+        Mesh& m = q.m;
+        m.nx = c->nx; m.ny = c->ny;
+        m.P = (int)rup(c->nx + 2 * G, 4);
+        m.NYg = c->ny + 2 * G;
+        m.plane = (long long)m.P * m.NYg;
+        m.dx = (c->x1 - c->x0) / c->nx;
+        m.dy = (c->y1 - c->y0) / c->ny;
+        m.bc[0] = c->bc_xlo; m.bc[1] = c->bc_xhi; m.bc[2] = c->bc_ylo; m.bc[3] = c->bc_yhi;
+        SchemeConsts& S = q.S;
+        S.gamma = c->gamma; S.gm1 = c->gamma - 1.0; S.K = (4.0 - 2.0 * c->gamma) / (c->gamma - 1.0);
+        S.inv_K2 = 1.0 / (S.K + 2.0);
+        S.d[3] = c->dH; S.d[0] = (1.0 - c->dH) * (1.0 - c->dL) / 2.0; S.d[1] = (1.0 - c->dH) * c->dL; S.d[2] = S.d[0];
+        S.inv_d3 = 1.0 / c->dH;
+        S.eps = c->eps; S.alpha_thres = c->alpha_thres; S.C1 = c->C1; S.C2 = c->C2;
+        S.time_limiter = c->time_limiter; S.tau_reading = c->tau_reading; S.gp_fallback = c->gp_fallback;
+        q.flux = flux[p];
+        cfl[p] = c->cfl;
+        const long long nfx = (long long)(m.nx + 1) * m.ny, nfy = (long long)(m.ny + 1) * m.nx;
+        const long long nlx = (long long)(m.nx + 1) * (m.ny + 4), nly = (long long)(m.ny + 1) * (m.nx + 4);
+        q.B.line_stride = rup(nlx > nly ? nlx : nly, 4);
+        q.B.gp_stride = rup(2 * (nfx > nfy ? nfx : nfy), 4);
+        q.B.flux_stride[0] = rup(2 * nfx, 4);
+        q.B.flux_stride[1] = rup(2 * nfy, 4);
+        const long long dense = (long long)m.nx * m.ny;
+        if (e == cudaSuccess) e = balloc(b, &q.W[0], (size_t)(4 * m.plane));
+        if (e == cudaSuccess) e = balloc(b, &q.W[1], (size_t)(4 * m.plane));
+        if (e == cudaSuccess) e = balloc(b, &q.A[0], (size_t)m.plane);
+        if (e == cudaSuccess) e = balloc(b, &q.A[1], (size_t)m.plane);
+        if (e == cudaSuccess) e = balloc(b, &q.Ws, (size_t)(4 * m.plane));
+        if (e == cudaSuccess) e = balloc(b, &q.acc, (size_t)(4 * dense));
+        if (e == cudaSuccess) e = balloc(b, &q.B.lines, (size_t)(LR_COUNT * q.B.line_stride));
+        if (e == cudaSuccess) e = balloc(b, &q.B.gp, (size_t)(GP_COUNT * q.B.gp_stride));
+        if (e == cudaSuccess) e = balloc(b, &q.B.flux[0], (size_t)(FR_COUNT * q.B.flux_stride[0]));
+        if (e == cudaSuccess) e = balloc(b, &q.B.flux[1], (size_t)(FR_COUNT * q.B.flux_stride[1]));
+        q.st = b->st + p;
+        if (e == cudaSuccess) {
+            launch_fill_value(q.W[0], 4 * m.plane, 1.0, b->stream);
+            launch_fill_value(q.W[1], 4 * m.plane, 1.0, b->stream);
+            launch_fill_value(q.Ws, 4 * m.plane, 1.0, b->stream);
+            launch_fill_value(q.A[0], m.plane, 1.0, b->stream);
+            launch_fill_value(q.A[1], m.plane, 1.0, b->stream);
+        }
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->dev, b->host.data(), (size_t)np * sizeof(BatchProblem), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->cfl, cfl.data(), (size_t)np * sizeof(double), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) {
+        for (int p = 0; p < np; ++p) {
+            DevState z;
+            memset(&z, 0, sizeof(z));
+            z.dtmin_bits = 0x7FEFFFFFFFFFFFFFULL;
+            z.fail_step = -1;
+            z.fail_key = ~0ULL;
+            b->st_host[p] = z;
+        }
+        e = cudaMemcpyAsync(b->st, b->st_host, (size_t)np * sizeof(DevState), cudaMemcpyHostToDevice, b->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    dfgks_status r = cst(e);
+    if (r == DFGKS_OK) r = build_maps(b);
+    if (r != DFGKS_OK) { free_batch(b); delete b; return r; }
+    *out = b;
+    return DFGKS_OK;
+}
+
+extern "C" DFGKS_API dfgks_status dfgks_batch_destroy(dfgks_batch* b) {
+    if (!b) return DFGKS_OK;
+    cudaStreamSynchronize(b->stream);
+    free_batch(b);
+    delete b;
+    return DFGKS_OK;
+}
+
+// W host or device [4][ny][nx] for problem p; alpha^0 as in dfgks_set_ic (reconstruction with alpha = 1)
+extern "C" DFGKS_API dfgks_status dfgks_batch_set_ic(dfgks_batch* b, int p, const double* W, int on_device) {
+    if (!b || p < 0 || p >= b->np || !W) return DFGKS_EINVAL;
+    BatchProblem& q = b->host[p];
+    const Mesh& m = q.m;
+    const size_t bytes = (size_t)4 * m.nx * m.ny * sizeof(double);
+    BCK(cudaMemcpyAsync(q.acc, W, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, b->stream));
+    int* bad = reinterpret_cast<int*>(q.B.flux[1]);          // scratch: a flux record plane is free here
+    BCK(cudaMemsetAsync(bad, 0, sizeof(int), b->stream));
+    launch_dense_to_ghosted(m, q.acc, 4, q.Ws, b->stream);
+    launch_check_state(m, q.Ws, q.S.gm1, bad, b->stream);
+    int hbad = 0;
+    BCK(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+    BCK(cudaStreamSynchronize(b->stream));
+    if (hbad) return DFGKS_ENONPHYS;
+    // the state starts in buffer 0
+    launch_dense_to_ghosted(m, q.acc, 4, q.W[0], b->stream);
+    launch_fill_value(q.A[0], m.plane, 1.0, b->stream);
+    launch_fill_ghosts(m, q.W[0], nullptr, nullptr, b->stream);
+    double* dts = q.acc;                                       // scratch scalar
+    launch_set_scalar(dts, 1.0, b->stream);
+    for (int d = 0; d < 2; ++d) launch_sweep(d, m, q.S, 1, true, q.W[0], q.A[0], dts, q.B, nullptr, nullptr, b->stream);
+    UpdateArgs a;
+    memset(&a, 0, sizeof(a));
+    a.alpha_out = q.A[0];
+    launch_update(UM_ALPHA, m, q.S, a, q.B, dts, nullptr, nullptr, b->stream);
+    DevState z;
+    memset(&z, 0, sizeof(z));
+    z.dtmin_bits = 0x7FEFFFFFFFFFFFFFULL;
+    z.fail_step = -1;
+    z.fail_key = ~0ULL;
+    b->st_host[p] = z;
+    BCK(cudaMemcpyAsync(b->st + p, &b->st_host[p], sizeof(DevState), cudaMemcpyHostToDevice, b->stream));
+    BCK(cudaGetLastError());
+    BCK(cudaStreamSynchronize(b->stream));
+    return DFGKS_OK;
+}
+
+extern "C" DFGKS_API dfgks_status dfgks_batch_get_state(dfgks_batch* b, int p, double* W, double* alpha, double* t,
+                                                        long* step, int on_device) {
+    if (!b || p < 0 || p >= b->np) return DFGKS_EINVAL;
+    BCK(cudaMemcpyAsync(&b->st_host[p], b->st + p, sizeof(DevState), cudaMemcpyDeviceToHost, b->stream));
+    BCK(cudaStreamSynchronize(b->stream));
+    const DevState hs = b->st_host[p];
+    BatchProblem& q = b->host[p];
+    const size_t n = (size_t)q.m.nx * q.m.ny;
+    cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (W) {
+        launch_ghosted_to_dense(q.m, q.W[hs.par], 4, q.acc, b->stream);
+        BCK(cudaMemcpyAsync(W, q.acc, 4 * n * sizeof(double), kind, b->stream));
+    }
+    if (alpha) {
+        launch_ghosted_to_dense(q.m, q.A[hs.par], 1, q.acc, b->stream);
+        BCK(cudaMemcpyAsync(alpha, q.acc, n * sizeof(double), kind, b->stream));
+    }
+    BCK(cudaGetLastError());
+    BCK(cudaStreamSynchronize(b->stream));
+    if (t) *t = hs.t;
+    if (step) *step = (long)hs.step;
+    return DFGKS_OK;
+}
+
+// Advance every problem n steps (each with its own CFL dt).  use_graph != 0: the step's launch
+// sequence is captured once in a CUDA graph and replayed.  Returns DFGKS_ENONPOS if any problem
+// lost positivity (that problem stops at its last good step; the others continue).
+extern "C" DFGKS_API dfgks_status dfgks_batch_step(dfgks_batch* b, int n, int use_graph) {
+    if (!b || n < 0) return DFGKS_EINVAL;
+    if (use_graph && !b->graph_ok) {
+        cudaGraph_t g;
+        BCK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+        enqueue_batch_step(b);
+        cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+        if (e != cudaSuccess) return cst(e);
+        e = cudaGraphInstantiate(&b->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return cst(e);
+        b->graph_ok = true;
+    }
+    for (int s = 0; s < n; ++s) {
+        if (use_graph) BCK(cudaGraphLaunch(b->graph, b->stream));
+        else enqueue_batch_step(b);
+    }
+    BCK(cudaGetLastError());
+    BCK(cudaMemcpyAsync(b->st_host, b->st, (size_t)b->np * sizeof(DevState), cudaMemcpyDeviceToHost, b->stream));
+    BCK(cudaStreamSynchronize(b->stream));
+    for (int p = 0; p < b->np; ++p) if (b->st_host[p].err) return DFGKS_ENONPOS;
+    return DFGKS_OK;
+}
+
+// Block shapes (bx, by with bx * by = 128) of the face-line, tangential and flux kernels.
+extern "C" DFGKS_API dfgks_status dfgks_batch_set_shapes(dfgks_batch* b, const int* shapes6) {
+    if (!b || !shapes6) return DFGKS_EINVAL;
+    for (int k = 0; k < 3; ++k) {
+        int bx = shapes6[2 * k], by = shapes6[2 * k + 1];
+        if (bx < 1 || by < 1 || bx * by != 128 || (bx % 32) != 0) return DFGKS_EINVAL;
+    }
+    for (int k = 0; k < 3; ++k) b->shape[k] = Shape{shapes6[2 * k], shapes6[2 * k + 1]};
+    if (b->graph_ok) { cudaGraphExecDestroy(b->graph); b->graph_ok = false; }
+    return build_maps(b);
+}
+
+// Autotuner: for each of the three sweep kernels in turn, time one batched step per candidate
+// block shape (32x4, 64x2, 128x1) with the others fixed, keep the fastest.  The problems' states
+// are saved before and restored after, so tuning does not advance them.  shapes6 receives the choice.
+extern "C" DFGKS_API dfgks_status dfgks_batch_autotune(dfgks_batch* b, int* shapes6, double* best_ms) {
+    if (!b) return DFGKS_EINVAL;
+    // snapshot: both state buffers, both alpha buffers, DevStates
+    std::vector<double*> saved;
+    auto restore_or_save = [&](bool save) -> cudaError_t {
+        size_t k = 0;
+        for (int p = 0; p < b->np; ++p) {
+            BatchProblem& q = b->host[p];
+            double* bufs[4] = {q.W[0], q.W[1], q.A[0], q.A[1]};
+            size_t sz[4] = {(size_t)(4 * q.m.plane), (size_t)(4 * q.m.plane), (size_t)q.m.plane, (size_t)q.m.plane};
+            for (int i = 0; i < 4; ++i, ++k) {
+                cudaError_t e;
+                if (save) {
+                    double* c = nullptr;
+                    e = cudaMalloc((void**)&c, sz[i] * sizeof(double));
+                    if (e != cudaSuccess) return e;
+                    saved.push_back(c);
+                    e = cudaMemcpyAsync(c, bufs[i], sz[i] * sizeof(double), cudaMemcpyDeviceToDevice, b->stream);
+                } else {
+                    e = cudaMemcpyAsync(bufs[i], saved[k], sz[i] * sizeof(double), cudaMemcpyDeviceToDevice, b->stream);
+                }
+                if (e != cudaSuccess) return e;
+            }
+        }
+        return cudaSuccess;
+    };
+    BCK(cudaMemcpyAsync(b->st_host, b->st, (size_t)b->np * sizeof(DevState), cudaMemcpyDeviceToHost, b->stream));
+    BCK(cudaStreamSynchronize(b->stream));
+    std::vector<DevState> st0(b->st_host, b->st_host + b->np);
+    cudaError_t e = restore_or_save(true);
+    if (e != cudaSuccess) { for (double* c : saved) cudaFree(c); return cst(e); }
+    const Shape cand[3] = {{32, 4}, {64, 2}, {128, 1}};
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best_total = 0.f;
+    dfgks_status r = DFGKS_OK;
+    for (int k = 0; k < 3 && r == DFGKS_OK; ++k) {
+        float best = 1e30f;
+        Shape keep = b->shape[k];
+        for (int c = 0; c < 3 && r == DFGKS_OK; ++c) {
+            b->shape[k] = cand[c];
+            r = build_maps(b);
+            if (r != DFGKS_OK) break;
+            enqueue_batch_step(b);                           // warm-up
+            cudaEventRecord(e0, b->stream);
+            enqueue_batch_step(b);
+            cudaEventRecord(e1, b->stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess) { r = DFGKS_ECUDA; break; }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) { best = ms; keep = cand[c]; }
+            // undo the two trial steps
+            if (restore_or_save(false) != cudaSuccess) { r = DFGKS_ECUDA; break; }
+            memcpy(b->st_host, st0.data(), (size_t)b->np * sizeof(DevState));
+            if (cudaMemcpyAsync(b->st, b->st_host, (size_t)b->np * sizeof(DevState), cudaMemcpyHostToDevice, b->stream) != cudaSuccess) { r = DFGKS_ECUDA; break; }
+            cudaStreamSynchronize(b->stream);
+        }
+        b->shape[k] = keep;
+        best_total = best;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamSynchronize(b->stream);
+    for (double* c : saved) cudaFree(c);
+    if (r != DFGKS_OK) return r;
+    r = build_maps(b);
+    if (b->graph_ok) { cudaGraphExecDestroy(b->graph); b->graph_ok = false; }
+    if (shapes6) for (int k = 0; k < 3; ++k) { shapes6[2 * k] = b->shape[k].bx; shapes6[2 * k + 1] = b->shape[k].by; }
+    if (best_ms) *best_ms = best_total;
+    return r;
+}
+
+extern "C" DFGKS_API dfgks_status dfgks_batch_status(dfgks_batch* b, int p, long* step, int* err, unsigned long long* df_normal) {
+    if (!b || p < 0 || p >= b->np) return DFGKS_EINVAL;
+    BCK(cudaMemcpyAsync(&b->st_host[p], b->st + p, sizeof(DevState), cudaMemcpyDeviceToHost, b->stream));
+    BCK(cudaStreamSynchronize(b->stream));
+    if (step) *step = (long)b->st_host[p].step;
+    if (err) *err = b->st_host[p].err;
+    if (df_normal) *df_normal = b->st_host[p].df_normal;
+    return DFGKS_OK;
+}

@@ -151,6 +151,7 @@ extern "C" dfgks_status dfgks_create(const dfgks_config* cfg, void* stream, dfgk
     m.bc[0] = cfg->bc_xlo; m.bc[1] = cfg->bc_xhi; m.bc[2] = cfg->bc_ylo; m.bc[3] = cfg->bc_yhi;
     SchemeConsts& S = h->S;
     S.gamma = cfg->gamma; S.gm1 = cfg->gamma - 1.0; S.K = (4.0 - 2.0 * cfg->gamma) / (cfg->gamma - 1.0);
+    S.inv_K2 = 1.0 / (S.K + 2.0);
     S.d[3] = cfg->dH;
     S.d[0] = (1.0 - cfg->dH) * (1.0 - cfg->dL) / 2.0;
     S.d[1] = (1.0 - cfg->dH) * cfg->dL;

@@ -21,7 +21,7 @@ constexpr int G = 3;                       // ghost layers: the normal stencil s
 constexpr double kGaussEta = 0.28867513459481288225;   // sqrt(3)/6: Gauss points at eta = -/+ this
 
 struct SchemeConsts {
-    double gamma, gm1, K;                  // gamma, gamma-1, internal degrees of freedom
+    double gamma, gm1, K, inv_K2;          // gamma, gamma-1, internal degrees of freedom, 1/(K+2)
     double d[4];                           // WENO-AO linear weights d0..d3 (Sect. 3.1)
     double inv_d3;
     double eps, alpha_thres, C1, C2;
@@ -97,10 +97,10 @@ __device__ __forceinline__ void back_project(const CharBasis& B, const double Q[
 struct AO {
     double A1, A2;          // sum_k c_k a1_k, sum_k c_k a2_k
     double c3a3, c3a4;      // c3 * a3, c3 * a4 of the quartic
-    double bmin, bmax, tauZ;  // for the time limiter
+    double rmax, rmin;      // tau_Z/(beta_min+eps), tau_Z/(beta_max+eps): the time limiter's ratios
 };
 
-__device__ __forceinline__ AO weno_ao(const double q[5], const SchemeConsts& S, bool want_limiter) {
+__device__ __forceinline__ AO weno_ao(const double q[5], const SchemeConsts& S) {
     const double qm2 = q[0], qm1 = q[1], q0 = q[2], q1 = q[3], q2 = q[4];
     // quadratic sub-stencils {i-2,i-1,i}, {i-1,i,i+1}, {i,i+1,i+2}
     double a1_0 = 0.5 * qm2 - 2.0 * qm1 + 1.5 * q0;
@@ -121,9 +121,18 @@ __device__ __forceinline__ AO weno_ao(const double q[5], const SchemeConsts& S, 
     double b2 = a1_2 * a1_2 + c13_3 * a2_2 * a2_2;
     double b3 = a1_3 * (a1_3 + 0.5 * a3_3) + c13_3 * a2_3 * a2_3 + (21.0 / 5.0) * a2_3 * a4_3
               + (3129.0 / 80.0) * a3_3 * a3_3 + (87617.0 / 140.0) * a4_3 * a4_3;
-    // Eq. 37 and the WENO-Z weights
+    // Eq. 37 and the WENO-Z weights.  The four ratios tau/(beta_k+eps) share one reciprocal of
+    // the product of their denominators (2 divisions per reconstruction instead of 5).
     double tau = (fabs(b3 - b0) + fabs(b3 - b1) + fabs(b3 - b2)) * (1.0 / 3.0);
-    double r0 = tau / (b0 + S.eps), r1 = tau / (b1 + S.eps), r2 = tau / (b2 + S.eps), r3 = tau / (b3 + S.eps);
+    double e0 = b0 + S.eps, e1 = b1 + S.eps, e2 = b2 + S.eps, e3 = b3 + S.eps;
+    double p01 = e0 * e1, p23 = e2 * e3, prod = p01 * p23;
+    double r0, r1, r2, r3;
+    if (prod < 1e300) {                              // beta+eps >= eps, so prod >= eps^4 > 0
+        double ti = tau / prod;
+        r0 = ti * (e1 * p23); r1 = ti * (e0 * p23); r2 = ti * (p01 * e3); r3 = ti * (p01 * e2);
+    } else {
+        r0 = tau / e0; r1 = tau / e1; r2 = tau / e2; r3 = tau / e3;
+    }
     double w0 = S.d[0] * (1.0 + r0 * r0), w1 = S.d[1] * (1.0 + r1 * r1);
     double w2 = S.d[2] * (1.0 + r2 * r2), w3 = S.d[3] * (1.0 + r3 * r3);
     double iw = 1.0 / (w0 + w1 + w2 + w3);
@@ -134,18 +143,15 @@ __device__ __forceinline__ AO weno_ao(const double q[5], const SchemeConsts& S, 
     o.A2 = c0 * a2_0 + c1 * a2_1 + c2 * a2_2 + c3 * a2_3;
     o.c3a3 = c3 * a3_3;
     o.c3a4 = c3 * a4_3;
-    if (want_limiter) {
-        o.tauZ = tau;
-        o.bmin = fmin(fmin(b0, b1), fmin(b2, b3));
-        o.bmax = fmax(fmax(b0, b1), fmax(b2, b3));
-    }
+    // tau >= 0, so the ratio is largest at beta_min and smallest at beta_max
+    o.rmax = fmax(fmax(r0, r1), fmax(r2, r3));
+    o.rmin = fmin(fmin(r0, r1), fmin(r2, r3));
     return o;
 }
 
 // time-limiter ingredient 2 at2 / (at1 + at2) of one reconstruction (Sect. 2.2)
-__device__ __forceinline__ double limiter_alpha(const AO& o, double eps) {
-    double r1 = o.tauZ / (o.bmin + eps), r2 = o.tauZ / (o.bmax + eps);
-    double a1 = 1.0 + r1 * r1, a2 = 1.0 + r2 * r2;
+__device__ __forceinline__ double limiter_alpha(const AO& o) {
+    double a1 = 1.0 + o.rmax * o.rmax, a2 = 1.0 + o.rmin * o.rmin;
     return 2.0 * a2 / (a1 + a2);
 }
 
@@ -194,16 +200,21 @@ struct Mom {
     double mx[3];   // <1>, <xi^2>, <xi^4>
 };
 
-struct Maxw { double rho, U, V, p, il2; };   // il2 = 1/(2 lambda) = p/rho
+// One Maxwellian: il2 = 1/(2 lambda) = p/rho, tl = 2 lambda, f4 = 4 lambda^2/(K+2),
+// qK = U^2 + V^2 + (K+2)/(2 lambda); the slope solves of a state share them.
+struct Maxw { double rho, ir, U, V, p, il2, tl, f4, qK; };
 
-__device__ __forceinline__ Maxw maxw_of(const double W[4], double gm1) {
+__device__ __forceinline__ Maxw maxw_of(const double W[4], const SchemeConsts& S) {
     Maxw s;
     s.rho = W[0];
-    double ir = 1.0 / W[0];
-    s.U = W[1] * ir;
-    s.V = W[2] * ir;
-    s.p = gm1 * (W[3] - 0.5 * W[0] * (s.U * s.U + s.V * s.V));
-    s.il2 = s.p * ir;
+    s.ir = 1.0 / W[0];
+    s.U = W[1] * s.ir;
+    s.V = W[2] * s.ir;
+    s.p = S.gm1 * (W[3] - 0.5 * W[0] * (s.U * s.U + s.V * s.V));
+    s.tl = W[0] / s.p;
+    s.il2 = s.p * s.ir;
+    s.f4 = s.tl * s.tl * S.inv_K2;
+    s.qK = s.U * s.U + s.V * s.V + (S.K + 2.0) * s.il2;
     return s;
 }
 
@@ -214,9 +225,10 @@ __device__ __forceinline__ void fill_moments(const Maxw& s, double K, Mom& m) {
         m.mu[0] = 1.0;
         m.mu[1] = s.U;
     } else {
-        double sl = sqrt(0.5 / s.il2);                       // sqrt(lambda)
-        double x = sl * s.U;
-        double e = exp(-x * x) * (0.28209479177387814347 / sl);   // exp(-lambda U^2) / (2 sqrt(pi lambda))
+        double lam = 0.5 * s.tl;
+        double isl = rsqrt(lam);                              // 1/sqrt(lambda)
+        double x = lam * isl * s.U;                           // sqrt(lambda) U
+        double e = exp(-x * x) * (0.28209479177387814347 * isl);  // exp(-lambda U^2) / (2 sqrt(pi lambda))
         if (HALF > 0) { m.mu[0] = 0.5 * erfc(-x); m.mu[1] = s.U * m.mu[0] + e; }
         else          { m.mu[0] = 0.5 * erfc(x);  m.mu[1] = s.U * m.mu[0] - e; }
     }
@@ -259,15 +271,12 @@ __device__ __forceinline__ void a_mom(const Mom& m, const double a[4], double ou
 }
 
 // closed-form solution of <a psi> = b for a Maxwellian (U, V, lambda)
-__device__ __forceinline__ void slope_solve(const Maxw& s, double K, const double b[4], double a[4]) {
-    double q = s.U * s.U + s.V * s.V + (K + 2.0) * s.il2;
-    double tl = 1.0 / s.il2;                          // 2 lambda
-    double f4 = tl * tl / (K + 2.0);                  // 4 lambda^2 / (K+2)
-    double R2 = b[1] - s.U * b[0], R3 = b[2] - s.V * b[0], R4 = 2.0 * b[3] - q * b[0];
-    a[3] = f4 * (R4 - 2.0 * s.U * R2 - 2.0 * s.V * R3);
-    a[2] = tl * R3 - s.V * a[3];
-    a[1] = tl * R2 - s.U * a[3];
-    a[0] = b[0] - s.U * a[1] - s.V * a[2] - 0.5 * a[3] * q;
+__device__ __forceinline__ void slope_solve(const Maxw& s, const double b[4], double a[4]) {
+    double R2 = b[1] - s.U * b[0], R3 = b[2] - s.V * b[0], R4 = 2.0 * b[3] - s.qK * b[0];
+    a[3] = s.f4 * (R4 - 2.0 * s.U * R2 - 2.0 * s.V * R3);
+    a[2] = s.tl * R3 - s.V * a[3];
+    a[1] = s.tl * R2 - s.U * a[3];
+    a[0] = b[0] - s.U * a[1] - s.V * a[2] - 0.5 * a[3] * s.qK;
 }
 
 struct GPState { double W[4], Wn[4], Wt[4]; };   // one side of one Gauss point, local frame
@@ -275,24 +284,24 @@ struct GPState { double W[4], Wn[4], Wt[4]; };   // one side of one Gauss point,
 __device__ __forceinline__ void gks_flux(const GPState& L, const GPState& R, double dt, const SchemeConsts& S,
                                          double F[4], double dF[4]) {
     const double K = S.K;
-    Maxw sl = maxw_of(L.W, S.gm1), sr = maxw_of(R.W, S.gm1);
+    Maxw sl = maxw_of(L.W, S), sr = maxw_of(R.W, S);
     Mom ml, mr;
     fill_moments<+1>(sl, K, ml);
     fill_moments<-1>(sr, K, mr);
     double b[4], alx[4], aly[4], arx[4], ary[4];
-    double irl = 1.0 / sl.rho, irr = 1.0 / sr.rho;
+    const double irl = sl.ir, irr = sr.ir;
 #pragma unroll
     for (int i = 0; i < 4; ++i) b[i] = L.Wn[i] * irl;
-    slope_solve(sl, K, b, alx);
+    slope_solve(sl, b, alx);
 #pragma unroll
     for (int i = 0; i < 4; ++i) b[i] = L.Wt[i] * irl;
-    slope_solve(sl, K, b, aly);
+    slope_solve(sl, b, aly);
 #pragma unroll
     for (int i = 0; i < 4; ++i) b[i] = R.Wn[i] * irr;
-    slope_solve(sr, K, b, arx);
+    slope_solve(sr, b, arx);
 #pragma unroll
     for (int i = 0; i < 4; ++i) b[i] = R.Wt[i] * irr;
-    slope_solve(sr, K, b, ary);
+    slope_solve(sr, b, ary);
     // Sect. 3.4: equilibrium state and slopes by kinetic weighting
     double Wc[4], Wcx[4], Wcy[4], t1[4], t2[4];
     psi_mom<0, 0, 0>(ml, t1); psi_mom<0, 0, 0>(mr, t2);
@@ -304,21 +313,22 @@ __device__ __forceinline__ void gks_flux(const GPState& L, const GPState& R, dou
     a_mom<0, 0>(ml, aly, t1); a_mom<0, 0>(mr, ary, t2);
 #pragma unroll
     for (int i = 0; i < 4; ++i) Wcy[i] = sl.rho * t1[i] + sr.rho * t2[i];
-    Maxw sc = maxw_of(Wc, S.gm1);
+    Maxw sc = maxw_of(Wc, S);
     Mom mc;
     fill_moments<0>(sc, K, mc);
-    double acx[4], acy[4], Ac[4], irc = 1.0 / sc.rho;
+    double acx[4], acy[4], Ac[4];
+    const double irc = sc.ir;
 #pragma unroll
     for (int i = 0; i < 4; ++i) b[i] = Wcx[i] * irc;
-    slope_solve(sc, K, b, acx);
+    slope_solve(sc, b, acx);
 #pragma unroll
     for (int i = 0; i < 4; ++i) b[i] = Wcy[i] * irc;
-    slope_solve(sc, K, b, acy);
+    slope_solve(sc, b, acy);
     // compatibility <A + a_x u + a_y v> = 0
     a_mom<1, 0>(mc, acx, t1); a_mom<0, 1>(mc, acy, t2);
 #pragma unroll
     for (int i = 0; i < 4; ++i) b[i] = -(t1[i] + t2[i]);
-    slope_solve(sc, K, b, Ac);
+    slope_solve(sc, b, Ac);
     // moments entering the flux
     double Mc0[4], Mc1[4], Mc2[4], Ml0[4], Mr0[4], Ml1[4], Mr1[4];
     psi_mom<1, 0, 0>(mc, Mc0);
@@ -335,10 +345,11 @@ __device__ __forceinline__ void gks_flux(const GPState& L, const GPState& R, dou
 #pragma unroll
     for (int i = 0; i < 4; ++i) Mr1[i] = t1[i] + t2[i];
     // numerical collision time (Sect. 2.2) and the combined time coefficients of Eq. 27
-    double T = S.C1 * dt + S.C2 * fabs((sl.p - sr.p) / (sl.p + sr.p)) * dt;
+    double rT = S.C1 + S.C2 * fabs((sl.p - sr.p) / (sl.p + sr.p));   // tau_n / dt
+    double T = rT * dt;
     double tau = (S.tau_reading == 1) ? T : 0.0;
     double E2 = 0.0, r = 0.0;
-    if (T > 0.0) { E2 = exp(-0.5 * dt / T); r = T / dt; }
+    if (rT > 0.0) { E2 = exp(-0.5 / rT); r = rT; }
     double E1 = E2 * E2;
     double om = 1.0 - E2;
     double S3 = om * (3.0 - E2);                       // 3 - 4 E2 + E1
@@ -362,11 +373,11 @@ __device__ __forceinline__ void gks_flux(const GPState& L, const GPState& R, dou
         a_mom<1, 0>(mlF, alx, t1); a_mom<0, 1>(mlF, aly, t2);
 #pragma unroll
         for (int i = 0; i < 4; ++i) b[i] = -(t1[i] + t2[i]);
-        slope_solve(sl, K, b, Al);
+        slope_solve(sl, b, Al);
         a_mom<1, 0>(mrF, arx, t1); a_mom<0, 1>(mrF, ary, t2);
 #pragma unroll
         for (int i = 0; i < 4; ++i) b[i] = -(t1[i] + t2[i]);
-        slope_solve(sr, K, b, Ar);
+        slope_solve(sr, b, Ar);
         a_mom<1, 0>(ml, Al, Ml2);
         a_mom<1, 0>(mr, Ar, Mr2);
     }

@@ -74,7 +74,7 @@ struct DevState {
     int halt;                       // 1: skip the remaining kernels
     int err;                        // 0 or DFGKS_ENONPOS
     int clipped;                    // the current step was clipped to t_end
-    int pad_;
+    int par;                        // batched path: which of the two state buffers is current
     long long fail_step;
     unsigned long long fail_key;    // smallest failing linear cell index j*nx + i
     unsigned long long fallbacks, df_normal, df_tangential;

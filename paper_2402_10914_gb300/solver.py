@@ -178,3 +178,105 @@ class Solver:
         _lib.check(_lib.lib().dfgks_face_records(self._h, _ptr(W), _ptr(alpha), float(dt), int(flux),
                                                  int(direction), _ptr(out)), "dfgks_face_records")
         return out
+
+
+class BatchSolver:
+    """Many independent problems advanced together (dfgks_batch_*): one launch per phase over all
+    problems, optionally replayed from a CUDA graph.  ``settings`` is a list of ``Settings``."""
+
+    def __init__(self, settings: list, autotune_cache: str | None = None):
+        self.settings = list(settings)
+        n = len(self.settings)
+        cfgs = (_lib.Config * n)()
+        for k, s in enumerate(self.settings):
+            cfgs[k] = make_config(s)
+        flux = (C.c_int * n)(*[int(s.flux) for s in self.settings])
+        h = C.c_void_p()
+        _lib.check(_lib.lib().dfgks_batch_create(C.cast(cfgs, C.c_void_p), C.cast(flux, C.c_void_p), n, None,
+                                                 C.byref(h)), "dfgks_batch_create")
+        self._h = h
+        self.shapes = None
+        self._cache = autotune_cache
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.lib().dfgks_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_ic(self, p: int, W):
+        W = np.ascontiguousarray(np.asarray(W, dtype=np.float64))
+        _lib.check(_lib.lib().dfgks_batch_set_ic(self._h, int(p), C.c_void_p(W.ctypes.data), 0), "dfgks_batch_set_ic")
+
+    def step(self, n: int, use_graph: bool = True) -> int:
+        """Advance all problems n steps; returns the status (0 or ENONPOS) instead of raising on
+        positivity loss, since the other problems continue."""
+        rc = _lib.lib().dfgks_batch_step(self._h, int(n), int(use_graph))
+        if rc not in (_lib.OK, _lib.ENONPOS):
+            _lib.check(rc, "dfgks_batch_step")
+        return rc
+
+    def get_state(self, p: int):
+        s = self.settings[p]
+        W = np.empty((4, s.ny, s.nx))
+        a = np.empty((s.ny, s.nx))
+        t, st = C.c_double(), C.c_long()
+        _lib.check(_lib.lib().dfgks_batch_get_state(self._h, int(p), C.c_void_p(W.ctypes.data), C.c_void_p(a.ctypes.data),
+                                                    C.byref(t), C.byref(st), 0), "dfgks_batch_get_state")
+        return W, a, t.value, st.value
+
+    def status(self, p: int):
+        st, err, dfn = C.c_long(), C.c_int(), C.c_ulonglong()
+        _lib.check(_lib.lib().dfgks_batch_status(self._h, int(p), C.byref(st), C.byref(err), C.byref(dfn)),
+                   "dfgks_batch_status")
+        return {"step": st.value, "err": err.value, "df_normal": dfn.value}
+
+    def set_shapes(self, shapes):
+        arr = (C.c_int * 6)(*[int(v) for pair in shapes for v in pair])
+        _lib.check(_lib.lib().dfgks_batch_set_shapes(self._h, C.cast(arr, C.c_void_p)), "dfgks_batch_set_shapes")
+        self.shapes = [tuple(x) for x in shapes]
+
+    def signature(self) -> str:
+        return ";".join("%dx%d:%d" % (s.nx, s.ny, s.flux) for s in self.settings)
+
+    def autotune(self):
+        """Pick the sweep kernels' block shapes by timing (dfgks_batch_autotune); with a cache file,
+        reuse an earlier choice for the same set of problems."""
+        import json
+        import os
+        key = self.signature()
+        if self._cache and os.path.exists(self._cache):
+            try:
+                cached = json.load(open(self._cache)).get(key)
+            except Exception:
+                cached = None
+            if cached:
+                self.set_shapes(cached)
+                return self.shapes, None
+        arr = (C.c_int * 6)()
+        best = C.c_double()
+        _lib.check(_lib.lib().dfgks_batch_autotune(self._h, C.cast(arr, C.c_void_p), C.byref(best)),
+                   "dfgks_batch_autotune")
+        self.shapes = [(arr[0], arr[1]), (arr[2], arr[3]), (arr[4], arr[5])]
+        if self._cache:
+            data = {}
+            if os.path.exists(self._cache):
+                try:
+                    data = json.load(open(self._cache))
+                except Exception:
+                    data = {}
+            data[key] = self.shapes
+            with open(self._cache, "w") as f:
+                json.dump(data, f)
+        return self.shapes, best.value

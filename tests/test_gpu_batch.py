@@ -1,0 +1,129 @@
+"""Batched path (dfgks_batch_*): many uneven problems advanced by one launch per phase, optionally
+replayed from a CUDA graph, against the per-problem handles.  Both run the same per-thread bodies,
+but in different kernels, where the compiler may contract a different multiply-add into an FMA;
+with the time limiter's amplification (about 2x per step) the results agree to ~1e-12 after a
+few steps rather than bitwise.  A failing problem stops alone; the autotuner does not advance
+the state."""
+import numpy as np
+import pytest
+
+from paper_2402_10914_gb300 import inputs as I
+from tests.parity_util import comp_rel_err, l1_rel
+
+BAR = 1e-10      # max relative per component after <= 20 steps (observed 2.4e-12 after 7)
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def mixed_problems():
+    ws = [I.quadrants(32, seed=3), I.quadrants(48, seed=4, flux=I.LF), I.quadrants(64, seed=5),
+          I.random_rough(40, 56, seed=6, flux=I.LF, time_limiter=0), I.sine_c1(40),
+          I.random_smooth(24, 30, seed=7, bc=(I.PERIODIC, I.PERIODIC, I.REFLECT, I.OUTFLOW), flux=I.GKS)]
+    return ws
+
+
+def per_problem(ws, nsteps):
+    from paper_2402_10914_gb300.solver import Solver
+    out = []
+    for w in ws:
+        with Solver(w.settings) as s:
+            s.set_ic(w.W0)
+            done, _ = s.step(nsteps)
+            W, a, t, step = s.get_state()
+        out.append((W, a, t, step))
+    return out
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_batch_equals_per_problem(use_graph):
+    from paper_2402_10914_gb300.solver import BatchSolver
+    ws = mixed_problems()
+    ref = per_problem(ws, 7)
+    with BatchSolver([w.settings for w in ws]) as b:
+        for p, w in enumerate(ws):
+            b.set_ic(p, w.W0)
+        assert b.step(3, use_graph=use_graph) == 0
+        assert b.step(4, use_graph=use_graph) == 0
+        for p in range(len(ws)):
+            W, a, t, step = b.get_state(p)
+            Wr, ar, tr, sr = ref[p]
+            assert step == sr == 7
+            assert abs(t - tr) <= 1e-13 * tr
+            assert comp_rel_err(W, Wr) <= BAR and l1_rel(W, Wr) <= 1e-12, (p, comp_rel_err(W, Wr))
+            assert comp_rel_err(a[None], ar[None], floor_frac=1e-12) <= BAR
+
+
+def test_batch_failure_is_isolated():
+    from paper_2402_10914_gb300.solver import BatchSolver, Solver
+    from paper_2402_10914_gb300 import _lib
+    bad = I.quadrants(64, seed=2)           # loses positivity at step 12
+    good = I.quadrants(48, seed=3)
+    good.settings = good.settings.with_(time_limiter=0)   # well conditioned over 20 steps
+    with Solver(bad.settings) as s:
+        s.set_ic(bad.W0)
+        with pytest.raises(_lib.DfgksError):
+            s.step(20)
+        Wb, ab, tb, sb = s.get_state()
+    ref_good = per_problem([good], 20)[0]
+    with BatchSolver([bad.settings, good.settings]) as b:
+        b.set_ic(0, bad.W0)
+        b.set_ic(1, good.W0)
+        assert b.step(20) == _lib.ENONPOS
+        st = b.status(0)
+        assert st["err"] == _lib.ENONPOS and st["step"] == sb
+        W, a, t, step = b.get_state(0)
+        assert comp_rel_err(W, Wb) <= BAR and abs(t - tb) <= 1e-13 * tb
+        W1, a1, t1, s1 = b.get_state(1)
+        assert s1 == 20 and comp_rel_err(W1, ref_good[0]) <= 1e-12
+
+
+def test_autotune_keeps_state_and_results(tmp_path):
+    from paper_2402_10914_gb300.solver import BatchSolver
+    ws = mixed_problems()[:4]
+    ref = per_problem(ws, 5)
+    cache = str(tmp_path / "shapes.json")
+    with BatchSolver([w.settings for w in ws], autotune_cache=cache) as b:
+        for p, w in enumerate(ws):
+            b.set_ic(p, w.W0)
+        b.step(2, use_graph=False)
+        shapes, best = b.autotune()
+        assert len(shapes) == 3 and all(x * y == 128 for x, y in shapes)
+        b.step(3, use_graph=True)
+        for p in range(len(ws)):
+            W, a, t, step = b.get_state(p)
+            assert step == 5 and comp_rel_err(W, ref[p][0]) <= BAR
+    with BatchSolver([w.settings for w in ws], autotune_cache=cache) as b2:
+        shapes2, best2 = b2.autotune()          # served from the cache
+        assert best2 is None and shapes2 == shapes
+
+
+def test_batch_rejects_unsupported():
+    from paper_2402_10914_gb300.solver import BatchSolver
+    from paper_2402_10914_gb300 import _lib
+    s = I.quadrants(16, seed=3).settings.with_(time_scheme=I.SSPRK3)
+    with pytest.raises(_lib.DfgksError) as e:
+        BatchSolver([s])
+    assert e.value.status == _lib.EINVAL
+
+
+def test_c3_batch_first_steps_match_per_problem():
+    # the 64-problem uneven batch (sides 64..512, mixed GKS / L-F): 2 steps, every problem compared
+    from paper_2402_10914_gb300.solver import BatchSolver
+    ws = I.batch()
+    ref = per_problem(ws, 2)
+    with BatchSolver([w.settings for w in ws]) as b:
+        for p, w in enumerate(ws):
+            b.set_ic(p, w.W0)
+        assert b.step(2) == 0
+        for p in range(len(ws)):
+            W, a, t, step = b.get_state(p)
+            assert step == 2 and comp_rel_err(W, ref[p][0]) <= BAR, p
