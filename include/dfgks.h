@@ -145,13 +145,27 @@ DFGKS_API dfgks_status dfgks_residual_noalloc(const dfgks_config* cfg, void* str
                                               double* L, double* dtL, double* dtLt, double* alpha_next);
 
 /* Vector-Jacobian product of dfgks_residual with respect to W, with alpha, dt and every branch
- * decision (DF switch, fallback, |.| and min/max kinks) held at the values of the forward pass:
+ * decision (DF switch, Gauss-point fallback, the sign of |.|, the arguments chosen by min/max)
+ * held at the values of the forward pass:
  *   W_bar += (dL/dW)^T L_bar + (d dtL/dW)^T dtL_bar + (d dtLt/dW)^T dtLt_bar.
- * All pointers device; L_bar / dtL_bar / dtLt_bar may be NULL (treated as zero).  Not part of the
- * paper (a hand-written reverse sweep of the same operator).  Asynchronous on the stream. */
+ * All pointers device, dense [4][ny][nx]; L_bar / dtL_bar / dtLt_bar may be NULL (zero).  Not part
+ * of the paper: a hand-written reverse sweep of the operator of Eq. 2 (ghost fill, normal and
+ * tangential reconstruction, GKS / L-F flux, time-limiter weight).  Asynchronous on the stream;
+ * uses the handle's scratch (allocated on first use). */
 DFGKS_API dfgks_status dfgks_adjoint_residual(dfgks* h, const double* W, const double* alpha, double dt, int flux,
-                                    const double* L_bar, const double* dtL_bar, const double* dtLt_bar,
-                                    double* W_bar);
+                                              const double* L_bar, const double* dtL_bar, const double* dtLt_bar,
+                                              double* W_bar);
+
+/* Gradient through n S2O4 steps (Eq. 24 with the time limiter) started from W0 (device, dense):
+ * W0_bar = (dW^n/dW0)^T WT_bar, with the step sizes dts[n] (host; e.g. those dfgks_step recorded),
+ * alpha^0 computed from W0 as in dfgks_set_ic and the alpha sequence and branch decisions of the
+ * forward trajectory held fixed.  Checkpointed recompute: the forward pass keeps W and alpha every
+ * ckpt_every steps; each segment is recomputed from its checkpoint before its steps are reversed.
+ * Allocates its checkpoint and segment buffers for the call.  On return the handle holds the
+ * forward solution W^n, its alpha, time and step count.  S2O4 only (DFGKS_ENOTSUP otherwise);
+ * DFGKS_ENONPOS if the forward trajectory loses positivity.  Synchronises the stream. */
+DFGKS_API dfgks_status dfgks_adjoint_steps(dfgks* h, const double* W0, int n, const double* dts, int flux,
+                                           int ckpt_every, const double* WT_bar, double* W0_bar);
 
 /* ---- Batched problems ----------------------------------------------------------------------
  * Many independent problems (each its own mesh size, boundary conditions, flux solver and CFL dt)

@@ -65,7 +65,7 @@ def lib():
                          "oracle_char_basis", "oracle_jacobians", "oracle_moments_u", "oracle_slope_solve",
                          "oracle_avg_psi", "oracle_gks_point", "oracle_lf_point", "oracle_df_alpha_point",
                          "oracle_time_integrals", "oracle_fill_ghosts", "oracle_cfl_dt", "oracle_residual",
-                         "oracle_face_records", "oracle_alpha0", "oracle_run"):
+                         "oracle_face_records", "oracle_alpha0", "oracle_run", "oracle_residual_vjp"):
                 getattr(L, name).restype = C.c_int
             L.oracle_moments_u.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int, C.c_double, _D]
             L.oracle_gks_point.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double, C.c_int] + [_D] * 8
@@ -80,6 +80,7 @@ def lib():
             L.oracle_slope_solve.argtypes = [_D, C.c_double, _D, _D]
             L.oracle_avg_psi.argtypes = [_D, C.c_double, _D, C.c_int, C.c_int, _D]
             L.oracle_residual.argtypes = [C.POINTER(Cfg), _D, _D, C.c_double, _D, _D, _D, _D, C.POINTER(Stats)]
+            L.oracle_residual_vjp.argtypes = [C.POINTER(Cfg), _D, _D, C.c_double, _D, _D, _D, _D]
             L.oracle_face_records.argtypes = [C.POINTER(Cfg), _D, _D, C.c_double, C.c_int, _D, _D]
             L.oracle_alpha0.argtypes = [C.POINTER(Cfg), _D, _D]
             L.oracle_run.argtypes = [C.POINTER(Cfg), _D, _D, _D, C.c_int, C.c_double, C.c_double, _D,
@@ -275,3 +276,41 @@ def run(s, W, alpha, nsteps, t=0.0, dt_fixed=0.0, t_end=0.0):
     rc = lib().oracle_run(C.byref(c), _p(Wc), _p(ac), _p(tt), int(nsteps), float(dt_fixed or 0.0),
                           float(t_end or 0.0), _p(dts), C.byref(done), C.byref(st))
     return rc, Wc.reshape(4, s.ny, s.nx), ac.reshape(s.ny, s.nx), tt[0], dts[:done.value], st
+
+
+def residual_vjp(s, W, alpha, dt, L_bar=None, dtL_bar=None, dtLt_bar=None):
+    """(dL/dW)^T L_bar + (d dtL/dW)^T dtL_bar + (d dtLt/dW)^T dtLt_bar by reverse-mode
+    differentiation of the oracle's stage operator (alpha, dt and branch decisions fixed)."""
+    c = make_cfg(s)
+    N = s.nx * s.ny
+    out = np.zeros(4 * N)
+    bars = [None if b is None else _arr(b, 4 * N) for b in (L_bar, dtL_bar, dtLt_bar)]
+    rc = lib().oracle_residual_vjp(C.byref(c), _p(_arr(W, 4 * N)), _p(_arr(alpha, N)), float(dt),
+                                   _p(bars[0]), _p(bars[1]), _p(bars[2]), _p(out))
+    assert rc == 0
+    return out.reshape(4, s.ny, s.nx)
+
+
+def run_vjp(s, W0, dts, WT_bar):
+    """The oracle's own reverse sweep through len(dts) S2O4 steps (Eq. 24 with the time limiter):
+    each stage's adjoint is residual_vjp, combined by the step's linear structure; alpha^0 from W0,
+    the alpha sequence of the forward trajectory held fixed.  Returns (W^n, dJ/dW0)."""
+    N = (4, s.ny, s.nx)
+    W = np.asarray(W0, dtype=np.float64).reshape(N).copy()
+    a = alpha0(s, W)
+    hist = []
+    for dt in dts:
+        L, dL, _, _, _ = residual(s, W, a, dt)
+        Ws = W + 0.5 * dt * L + 0.125 * dt * dt * dL
+        hist.append((W.copy(), a.copy(), Ws, dt))
+        rc, W, a, _, _, _ = run(s, W, a, 1, dt_fixed=dt)
+        assert rc == 0
+    Wb = np.asarray(WT_bar, dtype=np.float64).reshape(N).copy()
+    for Wn, an, Ws, dt in reversed(hist):
+        dt2 = dt * dt
+        Wsb = residual_vjp(s, Ws, an, dt, dtLt_bar=dt2 / 3.0 * Wb)
+        Lb = dt * Wb + 0.5 * dt * Wsb
+        dLb = 0.5 * dt2 * Wb + 0.125 * dt2 * Wsb
+        dLtb = -dt2 / 3.0 * Wb
+        Wb = Wb + Wsb + residual_vjp(s, Wn, an, dt, Lb, dLb, dLtb)
+    return W, Wb

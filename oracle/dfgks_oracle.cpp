@@ -80,6 +80,67 @@ typedef struct {
 } oracle_stats;
 }
 
+// ------------------------------------------------------------------------------------------
+// Reverse-mode scalar for the oracle's own adjoint: every operation on `ad::Var` appends a node
+// (up to two parents and the local partial derivatives) to a tape; a reverse sweep over the tape
+// accumulates adjoints.  Branches are taken on values, so the forward pass fixes every decision.
+// ------------------------------------------------------------------------------------------
+namespace ad {
+struct Tape {
+    std::vector<int> pa, pb;
+    std::vector<double> da, db;
+    int push(int a, double ga, int b, double gb) {
+        pa.push_back(a); da.push_back(ga); pb.push_back(b); db.push_back(gb);
+        return (int)pa.size() - 1;
+    }
+    void clear() { pa.clear(); pb.clear(); da.clear(); db.clear(); }
+};
+static Tape* g_tape = nullptr;
+
+struct Var {
+    double v;
+    int id;                        // -1: a constant
+    Var() : v(0.0), id(-1) {}
+    Var(double x) : v(x), id(-1) {}
+    static Var leaf(double x) { Var r(x); r.id = g_tape->push(-1, 0.0, -1, 0.0); return r; }
+};
+inline Var mk(double v, int a, double ga, int b, double gb) {
+    Var r(v);
+    if (a >= 0 || b >= 0) r.id = g_tape->push(a, ga, b, gb);
+    return r;
+}
+inline Var operator+(const Var& x, const Var& y) { return mk(x.v + y.v, x.id, 1.0, y.id, 1.0); }
+inline Var operator-(const Var& x, const Var& y) { return mk(x.v - y.v, x.id, 1.0, y.id, -1.0); }
+inline Var operator*(const Var& x, const Var& y) { return mk(x.v * y.v, x.id, y.v, y.id, x.v); }
+inline Var operator/(const Var& x, const Var& y) { double q = x.v / y.v; return mk(q, x.id, 1.0 / y.v, y.id, -q / y.v); }
+inline Var operator-(const Var& x) { return mk(-x.v, x.id, -1.0, -1, 0.0); }
+inline Var operator+(const Var& x, double c) { return mk(x.v + c, x.id, 1.0, -1, 0.0); }
+inline Var operator+(double c, const Var& x) { return mk(c + x.v, x.id, 1.0, -1, 0.0); }
+inline Var operator-(const Var& x, double c) { return mk(x.v - c, x.id, 1.0, -1, 0.0); }
+inline Var operator-(double c, const Var& x) { return mk(c - x.v, x.id, -1.0, -1, 0.0); }
+inline Var operator*(const Var& x, double c) { return mk(x.v * c, x.id, c, -1, 0.0); }
+inline Var operator*(double c, const Var& x) { return mk(c * x.v, x.id, c, -1, 0.0); }
+inline Var operator/(const Var& x, double c) { return mk(x.v / c, x.id, 1.0 / c, -1, 0.0); }
+inline Var operator/(double c, const Var& x) { double q = c / x.v; return mk(q, x.id, -q / x.v, -1, 0.0); }
+inline bool operator<(const Var& x, const Var& y) { return x.v < y.v; }
+inline bool operator>(const Var& x, const Var& y) { return x.v > y.v; }
+inline bool operator<(const Var& x, double c) { return x.v < c; }
+inline bool operator>(const Var& x, double c) { return x.v > c; }
+inline bool operator<=(const Var& x, double c) { return x.v <= c; }
+inline bool operator>=(const Var& x, double c) { return x.v >= c; }
+inline Var fabs(const Var& x) { return x.v >= 0.0 ? mk(x.v, x.id, 1.0, -1, 0.0) : mk(-x.v, x.id, -1.0, -1, 0.0); }
+inline Var sqrt(const Var& x) { double r = std::sqrt(x.v); return mk(r, x.id, 0.5 / r, -1, 0.0); }
+inline Var exp(const Var& x) { double r = std::exp(x.v); return mk(r, x.id, r, -1, 0.0); }
+inline Var erfc(const Var& x) {
+    return mk(std::erfc(x.v), x.id, -2.0 / std::sqrt(M_PI) * std::exp(-x.v * x.v), -1, 0.0);
+}
+}  // namespace ad
+
+namespace orc {
+template <class R> struct Parallel { static const bool ok = true; };
+template <> struct Parallel<ad::Var> { static const bool ok = false; };
+}
+
 namespace orc {
 
 static const int G = 3;                 // ghost layers: the normal stencil reaches i-3 .. i+2
@@ -865,7 +926,7 @@ static void stage_operator(const Ctx& C, const Field<R>& F, double dt, bool want
         const int nf = d.nn + 1, nl = d.nt + 4;
         std::vector<LineRec<R>> lines((size_t)nf * nl);
         long dfn = 0;
-        #pragma omp parallel for schedule(static) reduction(+:dfn)
+        #pragma omp parallel for schedule(static) reduction(+:dfn) if(Parallel<R>::ok)
         for (int tl = 0; tl < nl; ++tl)
             for (int f = 0; f < nf; ++f) {
                 lines[(size_t)tl * nf + f] = normal_line(C, F, d, f, tl - 2);
@@ -875,7 +936,7 @@ static void stage_operator(const Ctx& C, const Field<R>& F, double dt, bool want
         faces[dir].resize((size_t)nf * d.nt);
         if (keep_faces) out.sides[dir].resize((size_t)nf * d.nt * 2);
         long fb = 0, dft = 0;
-        #pragma omp parallel for schedule(static) reduction(+:fb,dft)
+        #pragma omp parallel for schedule(static) reduction(+:fb,dft) if(Parallel<R>::ok)
         for (int t = 0; t < d.nt; ++t)
             for (int f = 0; f < nf; ++f) {
                 Counters c;
@@ -891,7 +952,7 @@ static void stage_operator(const Ctx& C, const Field<R>& F, double dt, bool want
     }
     for (int k = 0; k < 4; ++k) { out.L[k].assign((size_t)nx * ny, R(0.0)); out.dtL[k].assign((size_t)nx * ny, R(0.0)); out.dtLt[k].assign((size_t)nx * ny, R(0.0)); }
     out.alpha_next.assign((size_t)nx * ny, R(1.0));
-    #pragma omp parallel for schedule(static)
+    #pragma omp parallel for schedule(static) if(Parallel<R>::ok)
     for (int j = 0; j < ny; ++j)
         for (int i = 0; i < nx; ++i) {
             const FaceRec<R>& Wf = faces[0][(size_t)j * (nx + 1) + i];
@@ -1164,6 +1225,50 @@ int oracle_face_records(const oracle_cfg* cfg, const double* W, const double* al
             p[16] = lr[n].tl_alpha;
         }
     }
+    return 0;
+}
+
+// Vector-Jacobian product of the stage operator by reverse-mode differentiation of the same code:
+// W_bar = (dL/dW)^T L_bar + (d dtL/dW)^T dtL_bar + (d dtLt/dW)^T dtLt_bar, with alpha, dt and every
+// branch decision fixed by the forward pass (any of the three bars may be NULL).
+int oracle_residual_vjp(const oracle_cfg* cfg, const double* W, const double* alpha, double dt,
+                        const double* L_bar, const double* dtL_bar, const double* dtLt_bar, double* W_bar) {
+    Ctx C;
+    if (!make_ctx(cfg, C)) return 1;
+    ad::Tape tape;
+    ad::g_tape = &tape;
+    const int nx = cfg->nx, ny = cfg->ny;
+    const size_t N = (size_t)nx * ny;
+    Field<ad::Var> F;
+    F.init(nx, ny);
+    std::vector<int> leaf((size_t)4 * N);
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            for (int k = 0; k < 4; ++k) {
+                ad::Var x = ad::Var::leaf(W[k * N + (size_t)j * nx + i]);
+                F.w[k][F.id(i, j)] = x;
+                leaf[k * N + (size_t)j * nx + i] = x.id;
+            }
+            F.alpha[F.id(i, j)] = alpha[(size_t)j * nx + i];
+        }
+    fill_ghosts(C, F, true);
+    StageOut<ad::Var> o;
+    stage_operator(C, F, dt, true, o);
+    std::vector<double> adj(tape.pa.size(), 0.0);
+    for (int k = 0; k < 4; ++k)
+        for (size_t c = 0; c < N; ++c) {
+            if (L_bar && o.L[k][c].id >= 0) adj[o.L[k][c].id] += L_bar[k * N + c];
+            if (dtL_bar && o.dtL[k][c].id >= 0) adj[o.dtL[k][c].id] += dtL_bar[k * N + c];
+            if (dtLt_bar && o.dtLt[k][c].id >= 0) adj[o.dtLt[k][c].id] += dtLt_bar[k * N + c];
+        }
+    for (long n = (long)tape.pa.size() - 1; n >= 0; --n) {
+        const double g = adj[n];
+        if (g == 0.0) continue;
+        if (tape.pa[n] >= 0) adj[tape.pa[n]] += tape.da[n] * g;
+        if (tape.pb[n] >= 0) adj[tape.pb[n]] += tape.db[n] * g;
+    }
+    for (size_t q = 0; q < 4 * N; ++q) W_bar[q] = adj[leaf[q]];
+    ad::g_tape = nullptr;
     return 0;
 }
 

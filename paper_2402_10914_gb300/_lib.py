@@ -68,6 +68,7 @@ SIGNATURES = {
     "dfgks_batch_status": [_V, C.c_int, C.POINTER(C.c_long), C.POINTER(C.c_int), C.POINTER(C.c_ulonglong)],
     "dfgks_batch_set_shapes": [_V, _V],
     "dfgks_batch_autotune": [_V, _V, _D],
+    "dfgks_adjoint_steps": [_V, _V, C.c_int, _D, C.c_int, C.c_int, _V, _V],
 }
 
 

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdfgks.so")
-SOURCES = ["dfgks_kernels.cu", "dfgks_capi.cu", "dfgks_probe.cu", "dfgks_noalloc.cu", "dfgks_batch.cu"]
+SOURCES = ["dfgks_kernels.cu", "dfgks_capi.cu", "dfgks_probe.cu", "dfgks_noalloc.cu", "dfgks_batch.cu", "dfgks_adjoint.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -1,0 +1,387 @@
+// dfgks_adjoint.cu -- reverse (vector-Jacobian product) of the single-stage operator.
+//
+// With the forward records of one direction in place (face lines, Gauss-point states, fluxes),
+// three kernels walk that direction's sweep backwards:
+//   ka_flux  : one thread per Gauss point.  Face adjoints from the cells' L, dL/dt and limited
+//              dL/dt adjoints (Eq. 2 with A_m = 1/2), then the GKS / L-F flux adjoint into the
+//              Gauss-point record adjoints, and the time-limiter weight's adjoint.
+//   ka_faces : one thread per face side.  Recomputes the tangential reconstruction and scatters
+//              (atomically) into the adjoints of the five face lines and of the face basis; a
+//              Gauss point that fell back to the cell average sends its adjoint to that cell.
+//   ka_lines : one thread per face line.  Recomputes the normal reconstruction and the limiter
+//              weight and scatters into the ghosted cell adjoints.
+// A final pass folds ghost-cell adjoints back into the interior cells they were copied from.
+// alpha, dt and every branch decision are those of the forward pass.
+#include "dfgks_adjoint.cuh"
+#include "dfgks_bodies.cuh"
+
+namespace dfk {
+
+__device__ __forceinline__ void aadd(double* p, double v) { if (v != 0.0) atomicAdd(p, v); }
+
+template <int DIR>
+__device__ __forceinline__ void to_global_vec(double W[4]) { to_global<DIR>(W); }
+
+template <int DIR, int FLUX>
+__global__ void __launch_bounds__(128) ka_flux(Mesh m, SchemeConsts S, AdjointArgs a, const double* __restrict__ lines,
+                                               long long ls, const double* __restrict__ gp, long long gs,
+                                               const double* __restrict__ fr, long long fs, const double* dtp,
+                                               double* __restrict__ lb, double* __restrict__ gb) {
+    Geo<DIR> g(m);
+    int ax = blockIdx.x * blockDim.x + threadIdx.x, ay = blockIdx.y * blockDim.y + threadIdx.y;
+    const int mm = blockIdx.z;
+    int f = DIR == 0 ? ax : ay;
+    int t = DIR == 0 ? ay : ax;
+    if (f > g.nn || t >= g.nt) return;
+    const long long fid = g.face(f, t), nf = g.nfaces();
+    const long long dplane = (long long)m.nx * m.ny;
+    // adjoints of the two cells' residuals (cells outside the mesh have none)
+    double dL[4] = {0, 0, 0, 0}, ddL[4] = {0, 0, 0, 0}, ddLt[4] = {0, 0, 0, 0};
+    for (int side = 0; side < 2; ++side) {
+        const int n = f - 1 + side;
+        if (n < 0 || n >= g.nn) continue;
+        const long long c = DIR == 0 ? (long long)t * m.nx + n : (long long)n * m.nx + t;
+        const double sg = side == 0 ? -1.0 : 1.0;    // F enters L of the left cell with -1/dn
+        for (int k = 0; k < 4; ++k) {
+            if (a.Lb) dL[k] += sg * a.Lb[k * dplane + c];
+            if (a.dtLb) ddL[k] += sg * a.dtLb[k * dplane + c];
+            if (a.dtLtb) ddLt[k] += sg * a.dtLtb[k * dplane + c];
+        }
+    }
+    const double idn = 1.0 / g.dn;
+    const double om = fr[FR_OMEGA * fs + fid];
+    double Fb[4], dFb[4];
+    for (int k = 0; k < 4; ++k) {
+        Fb[k] = 0.5 * dL[k] * idn;                              // Gauss weight 1/2
+        dFb[k] = 0.5 * (ddL[k] + om * ddLt[k]) * idn;
+    }
+    if (mm == 0 && S.time_limiter) {
+        double wb = 0.0;
+        for (int k = 0; k < 4; ++k) {
+            double dFface = 0.5 * fr[(FR_DF + k) * fs + fid] + 0.5 * fr[(FR_DF + k) * fs + nf + fid];
+            wb += dFface * ddLt[k] * idn;
+        }
+        lb[LR_TL * ls + g.line(f, t)] = wb;
+    }
+    to_local<DIR>(Fb);                                          // F = T^{-1} F~, T orthogonal
+    to_local<DIR>(dFb);
+    const long long eL = fid, eR = nf + fid;
+    GPState L, R;
+    for (int k = 0; k < 4; ++k) {
+        L.W[k] = gp[(mm * 12 + k) * gs + eL];
+        L.Wn[k] = gp[(mm * 12 + 4 + k) * gs + eL];
+        L.Wt[k] = gp[(mm * 12 + 8 + k) * gs + eL];
+        R.W[k] = gp[(mm * 12 + k) * gs + eR];
+        R.Wn[k] = gp[(mm * 12 + 4 + k) * gs + eR];
+        R.Wt[k] = gp[(mm * 12 + 8 + k) * gs + eR];
+    }
+    GPStateBar Lbar, Rbar;
+    for (int k = 0; k < 4; ++k) { Lbar.W[k] = Lbar.Wn[k] = Lbar.Wt[k] = Rbar.W[k] = Rbar.Wn[k] = Rbar.Wt[k] = 0.0; }
+    if (FLUX == 0) gks_flux_vjp(L, R, *dtp, S, Fb, dFb, Lbar, Rbar);
+    else lf_flux_vjp(L, R, S, Fb, dFb, Lbar, Rbar);
+    for (int k = 0; k < 4; ++k) {
+        gb[(mm * 12 + k) * gs + eL] = Lbar.W[k];
+        gb[(mm * 12 + 4 + k) * gs + eL] = Lbar.Wn[k];
+        gb[(mm * 12 + 8 + k) * gs + eL] = Lbar.Wt[k];
+        gb[(mm * 12 + k) * gs + eR] = Rbar.W[k];
+        gb[(mm * 12 + 4 + k) * gs + eR] = Rbar.Wn[k];
+        gb[(mm * 12 + 8 + k) * gs + eR] = Rbar.Wt[k];
+    }
+}
+
+template <int DIR>
+__global__ void __launch_bounds__(128) ka_faces(Mesh m, SchemeConsts S, const double* __restrict__ W,
+                                                const double* __restrict__ alpha, const double* __restrict__ lines,
+                                                long long ls, const double* __restrict__ gb, long long gs,
+                                                double* __restrict__ lb, double* __restrict__ Wb) {
+    Geo<DIR> g(m);
+    int ax = blockIdx.x * blockDim.x + threadIdx.x, ay = blockIdx.y * blockDim.y + threadIdx.y;
+    const int side = blockIdx.z;
+    int f = DIR == 0 ? ax : ay;
+    int t = DIR == 0 ? ay : ax;
+    if (f > g.nn || t >= g.nt) return;
+    const long long l0 = g.line(f, t);
+    CharBasis B;
+    B.u = lines[LR_U * ls + l0]; B.v = lines[LR_V * ls + l0]; B.c = lines[LR_C * ls + l0];
+    B.ic = lines[LR_IC * ls + l0]; B.H = lines[LR_H * ls + l0]; B.b1 = lines[LR_B1 * ls + l0];
+    B.b2 = lines[LR_B2 * ls + l0]; B.q2 = lines[LR_Q2 * ls + l0];
+    const int wbase = side == 0 ? LR_WL : LR_WR;
+    const int nbase = side == 0 ? LR_WLN : LR_WRN;
+    double Wl[5][4], Q[5][4];
+    for (int b = 0; b < 5; ++b) {
+        long long lbb = g.line(f, t + Geo<DIR>::sigma * (b - 2));
+        for (int k = 0; k < 4; ++k) Wl[b][k] = lines[(wbase + k) * ls + lbb];
+        project(B, Wl[b], Q[b]);
+    }
+    const int ncell = f - 1 + side;
+    double al[3];
+    for (int b = 0; b < 3; ++b) al[b] = alpha[g.cell(m, ncell, t + Geo<DIR>::sigma * (b - 1))];
+    const bool df = fmax(fmax(al[0], al[1]), al[2]) < S.alpha_thres;
+    double qv[2][4], qt[2][4];
+    const double idt = 1.0 / g.dtan;
+    for (int k = 0; k < 4; ++k) {
+        double sq[5] = {Q[0][k], Q[1][k], Q[2][k], Q[3][k], Q[4][k]};
+        double v[2], s[2];
+        if (df) df_at_gauss(sq, al[1], v, s);
+        else { AO o = weno_ao(sq, S); ao_at_gauss(o, sq[2], v, s); }
+        qv[0][k] = v[0]; qv[1][k] = v[1];
+        qt[0][k] = s[0] * idt; qt[1][k] = s[1] * idt;
+    }
+    const long long e = (long long)side * g.nfaces() + g.face(f, t);
+    BasisBar Bb;
+    basis_bar_zero(Bb);
+    double qvb[2][4], slb[2][4];
+    for (int mm = 0; mm < 2; ++mm) {
+        for (int k = 0; k < 4; ++k) { qvb[mm][k] = 0.0; slb[mm][k] = 0.0; }
+        double Wg[4];
+        back_project(B, qv[mm], Wg);
+        double wb[4], wnb[4], wtb[4];
+        for (int k = 0; k < 4; ++k) {
+            wb[k] = gb[(mm * 12 + k) * gs + e];
+            wnb[k] = gb[(mm * 12 + 4 + k) * gs + e];
+            wtb[k] = gb[(mm * 12 + 8 + k) * gs + e];
+        }
+        if (S.gp_fallback && !physical_state(Wg, S.gm1)) {
+            // the Gauss point used the (rotated) cell average with zero slopes
+            to_global<DIR>(wb);
+            const long long c = g.cell(m, ncell, t);
+            for (int k = 0; k < 4; ++k) aadd(&Wb[k * m.plane + c], wb[k]);
+            continue;
+        }
+        back_project_vjp(B, qv[mm], wb, qvb[mm], Bb);
+        double qtb[4] = {0, 0, 0, 0};
+        back_project_vjp(B, qt[mm], wtb, qtb, Bb);
+        for (int k = 0; k < 4; ++k) {
+            slb[mm][k] = qtb[k] * idt;
+            aadd(&lb[(nbase + k) * ls + l0], wnb[k]);            // normal slope copied from the line
+        }
+    }
+    double Qb[5][4];
+    for (int b = 0; b < 5; ++b) for (int k = 0; k < 4; ++k) Qb[b][k] = 0.0;
+    for (int k = 0; k < 4; ++k) {
+        double sq[5] = {Q[0][k], Q[1][k], Q[2][k], Q[3][k], Q[4][k]};
+        double vb[2] = {qvb[0][k], qvb[1][k]}, sb[2] = {slb[0][k], slb[1][k]};
+        double qb[5] = {0, 0, 0, 0, 0};
+        if (df) df_at_gauss_vjp(al[1], vb, sb, qb);
+        else {
+            AOBar ob;
+            ao_bar_zero(ob);
+            ao_at_gauss_vjp(vb, sb, qb[2], ob);
+            weno_ao_vjp(sq, S, ob, qb);
+        }
+        for (int b = 0; b < 5; ++b) Qb[b][k] = qb[b];
+    }
+    for (int b = 0; b < 5; ++b) {
+        double wl[4] = {0, 0, 0, 0};
+        project_vjp(B, Wl[b], Qb[b], wl, Bb);
+        long long lbb = g.line(f, t + Geo<DIR>::sigma * (b - 2));
+        for (int k = 0; k < 4; ++k) aadd(&lb[(wbase + k) * ls + lbb], wl[k]);
+    }
+    aadd(&lb[LR_U * ls + l0], Bb.u); aadd(&lb[LR_V * ls + l0], Bb.v); aadd(&lb[LR_C * ls + l0], Bb.c);
+    aadd(&lb[LR_IC * ls + l0], Bb.ic); aadd(&lb[LR_H * ls + l0], Bb.H); aadd(&lb[LR_B1 * ls + l0], Bb.b1);
+    aadd(&lb[LR_B2 * ls + l0], Bb.b2); aadd(&lb[LR_Q2 * ls + l0], Bb.q2);
+}
+
+template <int DIR>
+__global__ void __launch_bounds__(128) ka_lines(Mesh m, SchemeConsts S, const double* __restrict__ W,
+                                                const double* __restrict__ alpha, const double* __restrict__ lb,
+                                                long long ls, double* __restrict__ Wb) {
+    Geo<DIR> g(m);
+    int ax = blockIdx.x * blockDim.x + threadIdx.x, ay = blockIdx.y * blockDim.y + threadIdx.y;
+    int f = DIR == 0 ? ax : ay;
+    int tt = DIR == 0 ? ay : ax;
+    if (f > g.nn || tt >= g.nt + 4) return;
+    const int t = tt - 2;
+    const long long li = g.line(f, t);
+    double Wc[6][4], al[6];
+    for (int s = 0; s < 6; ++s) {
+        long long c = g.cell(m, f - 3 + s, t);
+        for (int k = 0; k < 4; ++k) Wc[s][k] = W[k * m.plane + c];
+        to_local<DIR>(Wc[s]);
+        al[s] = alpha[c];
+    }
+    CharBasis B = make_basis(Wc[2], Wc[3], S);
+    double Q[6][4];
+    for (int s = 0; s < 6; ++s) project(B, Wc[s], Q[s]);
+    const bool dfL = fmax(fmax(al[1], al[2]), al[3]) < S.alpha_thres;
+    const bool dfR = fmax(fmax(al[2], al[3]), al[4]) < S.alpha_thres;
+    const double idn = 1.0 / g.dn;
+    // forward values, and the evaluation that sets the limiter weight: the first strict minimum
+    // over components per side (starting from 1), the right side on a tie between the sides
+    double qL[4], qLn[4], qR[4], qRn[4];
+    double tlL = 1.0, tlR = 1.0;
+    int kL = -1, kR = -1;
+    for (int k = 0; k < 4; ++k) {
+        double sL[5] = {Q[0][k], Q[1][k], Q[2][k], Q[3][k], Q[4][k]};
+        double sR[5] = {Q[5][k], Q[4][k], Q[3][k], Q[2][k], Q[1][k]};
+        double v, sl;
+        if (!dfL || S.time_limiter) {
+            AO o = weno_ao(sL, S);
+            if (S.time_limiter) { double la = limiter_alpha(o); if (la < tlL) { tlL = la; kL = k; } }
+            if (!dfL) ao_at_right_edge(o, sL[2], v, sl);
+        }
+        if (dfL) df_at_right_edge(sL, al[2], v, sl);
+        qL[k] = v; qLn[k] = sl * idn;
+        if (!dfR || S.time_limiter) {
+            AO o = weno_ao(sR, S);
+            if (S.time_limiter) { double la = limiter_alpha(o); if (la < tlR) { tlR = la; kR = k; } }
+            if (!dfR) ao_at_right_edge(o, sR[2], v, sl);
+        }
+        if (dfR) df_at_right_edge(sR, al[3], v, sl);
+        qR[k] = v; qRn[k] = -sl * idn;
+    }
+    const double tlb = S.time_limiter ? lb[LR_TL * ls + li] : 0.0;
+    const bool limL = tlL < tlR;            // the side whose weight is the face's
+    BasisBar Bb;
+    Bb.u = lb[LR_U * ls + li]; Bb.v = lb[LR_V * ls + li]; Bb.c = lb[LR_C * ls + li]; Bb.ic = lb[LR_IC * ls + li];
+    Bb.H = lb[LR_H * ls + li]; Bb.b1 = lb[LR_B1 * ls + li]; Bb.b2 = lb[LR_B2 * ls + li]; Bb.q2 = lb[LR_Q2 * ls + li];
+    double WLb[4], WLnb[4], WRb[4], WRnb[4];
+    for (int k = 0; k < 4; ++k) {
+        WLb[k] = lb[(LR_WL + k) * ls + li]; WLnb[k] = lb[(LR_WLN + k) * ls + li];
+        WRb[k] = lb[(LR_WR + k) * ls + li]; WRnb[k] = lb[(LR_WRN + k) * ls + li];
+    }
+    double qLb[4] = {0, 0, 0, 0}, qLnb[4] = {0, 0, 0, 0}, qRb[4] = {0, 0, 0, 0}, qRnb[4] = {0, 0, 0, 0};
+    back_project_vjp(B, qL, WLb, qLb, Bb);
+    back_project_vjp(B, qLn, WLnb, qLnb, Bb);
+    back_project_vjp(B, qR, WRb, qRb, Bb);
+    back_project_vjp(B, qRn, WRnb, qRnb, Bb);
+    double Qb[6][4];
+    for (int s = 0; s < 6; ++s) for (int k = 0; k < 4; ++k) Qb[s][k] = 0.0;
+    for (int k = 0; k < 4; ++k) {
+        double sL[5] = {Q[0][k], Q[1][k], Q[2][k], Q[3][k], Q[4][k]};
+        double sR[5] = {Q[5][k], Q[4][k], Q[3][k], Q[2][k], Q[1][k]};
+        double qbL[5] = {0, 0, 0, 0, 0}, qbR[5] = {0, 0, 0, 0, 0};
+        // left side: value at xi = +1/2, slope / dn
+        {
+            AOBar ob;
+            ao_bar_zero(ob);
+            bool need = false;
+            if (dfL) df_at_right_edge_vjp(al[2], qLb[k], qLnb[k] * idn, qbL);
+            else { ao_at_right_edge_vjp(qLb[k], qLnb[k] * idn, qbL[2], ob); need = true; }
+            if (S.time_limiter && limL && k == kL && tlb != 0.0) {
+                AO o = weno_ao(sL, S);
+                limiter_alpha_vjp(o, tlb, ob);
+                need = true;
+            }
+            if (need) weno_ao_vjp(sL, S, ob, qbL);
+        }
+        // right side: mirrored stencil, slope sign reversed
+        {
+            AOBar ob;
+            ao_bar_zero(ob);
+            bool need = false;
+            if (dfR) df_at_right_edge_vjp(al[3], qRb[k], -qRnb[k] * idn, qbR);
+            else { ao_at_right_edge_vjp(qRb[k], -qRnb[k] * idn, qbR[2], ob); need = true; }
+            if (S.time_limiter && !limL && k == kR && tlb != 0.0) {
+                AO o = weno_ao(sR, S);
+                limiter_alpha_vjp(o, tlb, ob);
+                need = true;
+            }
+            if (need) weno_ao_vjp(sR, S, ob, qbR);
+        }
+        for (int i = 0; i < 5; ++i) { Qb[i][k] += qbL[i]; Qb[5 - i][k] += qbR[i]; }
+    }
+    double Wcb[6][4];
+    for (int s = 0; s < 6; ++s) {
+        for (int k = 0; k < 4; ++k) Wcb[s][k] = 0.0;
+        project_vjp(B, Wc[s], Qb[s], Wcb[s], Bb);
+    }
+    make_basis_vjp(Wc[2], Wc[3], S, Bb, Wcb[2], Wcb[3]);
+    for (int s = 0; s < 6; ++s) {
+        to_global<DIR>(Wcb[s]);                                // the rotation is orthogonal
+        long long c = g.cell(m, f - 3 + s, t);
+        for (int k = 0; k < 4; ++k) aadd(&Wb[k * m.plane + c], Wcb[s][k]);
+    }
+}
+
+// Reverse of the ghost fill: the y pass (all columns) first, then the x pass (interior rows).
+__global__ void ka_fold_y(Mesh m, double* Wb) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x - G;
+    if (i >= m.nx + G) return;
+    for (int gr = 2 * G - 1; gr >= 0; --gr) {
+        int j = gr < G ? gr - G : m.ny + gr - G;
+        bool mir;
+        int s = ghost_src(j, m.ny, m.bc[2], m.bc[3], mir);
+        long long d = gid(m, i, j), o = gid(m, i, s);
+        for (int k = 0; k < 4; ++k) {
+            double v = Wb[k * m.plane + d];
+            Wb[k * m.plane + d] = 0.0;
+            Wb[k * m.plane + o] += (mir && k == 2) ? -v : v;
+        }
+    }
+}
+
+__global__ void ka_fold_x(Mesh m, double* Wb) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= m.ny) return;
+    for (int gc = 2 * G - 1; gc >= 0; --gc) {
+        int i = gc < G ? gc - G : m.nx + gc - G;
+        bool mir;
+        int s = ghost_src(i, m.nx, m.bc[0], m.bc[1], mir);
+        long long d = gid(m, i, j), o = gid(m, s, j);
+        for (int k = 0; k < 4; ++k) {
+            double v = Wb[k * m.plane + d];
+            Wb[k * m.plane + d] = 0.0;
+            Wb[k * m.plane + o] += (mir && k == 1) ? -v : v;
+        }
+    }
+}
+
+__global__ void ka_accumulate_dense(Mesh m, const double* __restrict__ Wbg, double* __restrict__ out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= m.nx || j >= m.ny) return;
+    const long long dp = (long long)m.nx * m.ny;
+    for (int k = 0; k < 4; ++k) out[k * dp + (long long)j * m.nx + i] += Wbg[k * m.plane + gid(m, i, j)];
+}
+
+template <int DIR>
+static void adjoint_dir(const Mesh& m, const SchemeConsts& S, int flux, const AdjointArgs& a, const double* W,
+                        const double* alpha, const double* dtp, const SweepBuffers& B, double* lb, double* gbuf,
+                        double* Wb, cudaStream_t s, KernelTimer* T) {
+    const int nn = DIR == 0 ? m.nx : m.ny, nt = DIR == 0 ? m.ny : m.nx;
+    dim3 blk(32, 4);
+    int fx = DIR == 0 ? nn + 1 : nt, fy = DIR == 0 ? nt : nn + 1;
+    dim3 gf((fx + 31) / 32, (fy + 3) / 4, 2);
+    int lx = DIR == 0 ? nn + 1 : nt + 4, ly = DIR == 0 ? nt + 4 : nn + 1;
+    dim3 gl((lx + 31) / 32, (ly + 3) / 4);
+    cudaMemsetAsync(lb, 0, sizeof(double) * LR_COUNT * B.line_stride, s);
+    if (T) T->begin(KK_FLUX);
+    if (flux == 0)
+        ka_flux<DIR, 0><<<gf, blk, 0, s>>>(m, S, a, B.lines, B.line_stride, B.gp, B.gp_stride, B.flux[DIR],
+                                           B.flux_stride[DIR], dtp, lb, gbuf);
+    else
+        ka_flux<DIR, 1><<<gf, blk, 0, s>>>(m, S, a, B.lines, B.line_stride, B.gp, B.gp_stride, B.flux[DIR],
+                                           B.flux_stride[DIR], dtp, lb, gbuf);
+    if (T) { T->end(KK_FLUX, 1); T->begin(KK_FACES); }
+    ka_faces<DIR><<<gf, blk, 0, s>>>(m, S, W, alpha, B.lines, B.line_stride, gbuf, B.gp_stride, lb, Wb);
+    if (T) { T->end(KK_FACES, 1); T->begin(KK_LINES); }
+    ka_lines<DIR><<<gl, blk, 0, s>>>(m, S, W, alpha, lb, B.line_stride, Wb);
+    if (T) T->end(KK_LINES, 1);
+}
+
+void launch_adjoint_dir(int dir, const Mesh& m, const SchemeConsts& S, int flux, const AdjointArgs& a,
+                        const double* W, const double* alpha, const double* dtp, const SweepBuffers& B,
+                        double* lb, double* gbuf, double* Wb, cudaStream_t s, KernelTimer* T) {
+    if (dir == 0) adjoint_dir<0>(m, S, flux, a, W, alpha, dtp, B, lb, gbuf, Wb, s, T);
+    else adjoint_dir<1>(m, S, flux, a, W, alpha, dtp, B, lb, gbuf, Wb, s, T);
+}
+
+void launch_adjoint_finish(const Mesh& m, double* Wbg, double* Wb_dense, cudaStream_t s) {
+    ka_fold_y<<<(m.nx + 2 * G + 127) / 128, 128, 0, s>>>(m, Wbg);
+    ka_fold_x<<<(m.ny + 127) / 128, 128, 0, s>>>(m, Wbg);
+    dim3 blk(32, 8), grd((m.nx + 31) / 32, (m.ny + 7) / 8);
+    ka_accumulate_dense<<<grd, blk, 0, s>>>(m, Wbg, Wb_dense);
+}
+
+// y <- a x + b y on dense arrays (step-adjoint combinations)
+__global__ void ka_axpby(long long n, double a, const double* __restrict__ x, double b, double* __restrict__ y) {
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
+        y[q] = a * x[q] + b * y[q];
+}
+void launch_axpby(long long n, double a, const double* x, double b, double* y, cudaStream_t s) {
+    long long blocks = (n + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    ka_axpby<<<(unsigned)blocks, 256, 0, s>>>(n, a, x, b, y);
+}
+
+}  // namespace dfk

@@ -1,0 +1,737 @@
+// dfgks_adjoint.cuh -- hand-written reverse (vector-Jacobian) products of the building blocks in
+// dfgks_device.cuh.  Each *_vjp routine recomputes what it needs of its forward counterpart and
+// accumulates (+=) adjoints into its inputs.  Branch decisions (DF switch, fallback, the sign of
+// |.|, the arguments selected by min/max) are those of the forward values; at an exact tie the
+// derivative of the first argument is taken, and |x| has slope +1 at x = 0.
+#pragma once
+#include "dfgks_device.cuh"
+
+namespace dfk {
+
+// ------------------------------------------------------------------------------------------
+// Characteristic basis
+// ------------------------------------------------------------------------------------------
+struct BasisBar { double u, v, c, ic, H, b1, b2, q2; };
+
+DFK_HD void basis_bar_zero(BasisBar& b) { b.u = b.v = b.c = b.ic = b.H = b.b1 = b.b2 = b.q2 = 0.0; }
+
+// adjoint of make_basis: accumulates into Wlb, Wrb (the two cell states)
+DFK_HD void make_basis_vjp(const double Wl[4], const double Wr[4], const SchemeConsts& S, const BasisBar& Bb,
+                           double Wlb[4], double Wrb[4]) {
+    double r = 0.5 * (Wl[0] + Wr[0]), m = 0.5 * (Wl[1] + Wr[1]);
+    double n = 0.5 * (Wl[2] + Wr[2]), E = 0.5 * (Wl[3] + Wr[3]);
+    double ir = 1.0 / r, u = m * ir, v = n * ir, q2 = 0.5 * (u * u + v * v);
+    double p = S.gm1 * (E - r * q2);
+    double c = sqrt(S.gamma * p * ir), ic = 1.0 / c, H = (E + p) * ir, b1 = S.gm1 * ic * ic;
+    double b1b = Bb.b1 + Bb.b2 * q2;
+    double q2b = Bb.q2 + Bb.b2 * b1;
+    double icb = Bb.ic + b1b * S.gm1 * 2.0 * ic;
+    double cb = Bb.c - icb * ic * ic;
+    double Eb = Bb.H * ir, pb = Bb.H * ir, irb = Bb.H * (E + p);
+    double sb = cb * 0.5 / c;
+    pb += sb * S.gamma * ir;
+    irb += sb * S.gamma * p;
+    Eb += pb * S.gm1;
+    double rb = -pb * S.gm1 * q2;
+    q2b += -pb * S.gm1 * r;
+    double ub = Bb.u + q2b * u, vb = Bb.v + q2b * v;
+    double mb = ub * ir, nb = vb * ir;
+    irb += ub * m + vb * n;
+    rb += -irb * ir * ir;
+    const double g[4] = {rb, mb, nb, Eb};
+    for (int k = 0; k < 4; ++k) { Wlb[k] += 0.5 * g[k]; Wrb[k] += 0.5 * g[k]; }
+}
+
+// adjoint of project (Q = L W): Wb += L^T Qb, basis adjoint accumulated
+DFK_HD void project_vjp(const CharBasis& B, const double W[4], const double Qb[4], double Wb[4], BasisBar& Bb) {
+    double kb = 0.5 * Qb[0] - Qb[1] + 0.5 * Qb[3];
+    double mmb = 0.5 * Qb[0] - 0.5 * Qb[3];
+    Wb[0] += Qb[1] - B.v * Qb[2];
+    Bb.v += -Qb[2] * W[0];
+    Wb[2] += Qb[2];
+    // mm = (u W0 - W1) ic
+    Bb.u += mmb * B.ic * W[0];
+    Wb[0] += mmb * B.ic * B.u;
+    Wb[1] += -mmb * B.ic;
+    Bb.ic += mmb * (B.u * W[0] - W[1]);
+    // k = b2 W0 - t
+    Bb.b2 += kb * W[0];
+    Wb[0] += kb * B.b2;
+    double tb = -kb;
+    // t = b1 (u W1 + v W2 - W3)
+    Bb.b1 += tb * (B.u * W[1] + B.v * W[2] - W[3]);
+    Bb.u += tb * B.b1 * W[1];
+    Wb[1] += tb * B.b1 * B.u;
+    Bb.v += tb * B.b1 * W[2];
+    Wb[2] += tb * B.b1 * B.v;
+    Wb[3] += -tb * B.b1;
+}
+
+// adjoint of back_project (W = R Q): Qb += R^T Wb, basis adjoint accumulated
+DFK_HD void back_project_vjp(const CharBasis& B, const double Q[4], const double Wb[4], double Qb[4], BasisBar& Bb) {
+    double s = Q[0] + Q[3], d = Q[3] - Q[0];
+    double W0 = s + Q[1];
+    double sb = 0.0, db = 0.0;
+    // W3 = H s + u c d + q2 Q1 + v Q2
+    Bb.H += Wb[3] * s;
+    sb += Wb[3] * B.H;
+    Bb.u += Wb[3] * B.c * d;
+    Bb.c += Wb[3] * B.u * d;
+    db += Wb[3] * B.u * B.c;
+    Bb.q2 += Wb[3] * Q[1];
+    Qb[1] += Wb[3] * B.q2;
+    Bb.v += Wb[3] * Q[2];
+    Qb[2] += Wb[3] * B.v;
+    // W2 = v W0 + Q2
+    Bb.v += Wb[2] * W0;
+    Qb[2] += Wb[2];
+    // W1 = u W0 + c d
+    Bb.u += Wb[1] * W0;
+    Bb.c += Wb[1] * d;
+    db += Wb[1] * B.c;
+    // W0 = s + Q1, with the uses in W1 and W2
+    double W0b = Wb[0] + Wb[2] * B.v + Wb[1] * B.u;
+    sb += W0b;
+    Qb[1] += W0b;
+    Qb[0] += sb - db;
+    Qb[3] += sb + db;
+}
+
+// ------------------------------------------------------------------------------------------
+// WENO-AO(5,3) and the DF quadratic
+// ------------------------------------------------------------------------------------------
+struct AOBar { double A1, A2, c3a3, c3a4, rmax, rmin; };
+
+DFK_HD void ao_bar_zero(AOBar& b) { b.A1 = b.A2 = b.c3a3 = b.c3a4 = b.rmax = b.rmin = 0.0; }
+
+DFK_HD void weno_ao_vjp(const double q[5], const SchemeConsts& S, const AOBar& ob, double qb[5]) {
+    const double qm2 = q[0], qm1 = q[1], q0 = q[2], q1 = q[3], q2 = q[4];
+    double a1[4], a2[4];
+    a1[0] = 0.5 * qm2 - 2.0 * qm1 + 1.5 * q0;
+    a2[0] = 0.5 * (qm2 - 2.0 * qm1 + q0);
+    a1[1] = 0.5 * (q1 - qm1);
+    a2[1] = 0.5 * (qm1 - 2.0 * q0 + q1);
+    a1[2] = -1.5 * q0 + 2.0 * q1 - 0.5 * q2;
+    a2[2] = 0.5 * (q0 - 2.0 * q1 + q2);
+    a1[3] = (5.0 * (qm2 - q2) - 34.0 * (qm1 - q1)) * (1.0 / 48.0);
+    a2[3] = (-(qm2 + q2) + 12.0 * (qm1 + q1) - 22.0 * q0) * (1.0 / 16.0);
+    double a3 = (-(qm2 - q2) + 2.0 * (qm1 - q1)) * (1.0 / 12.0);
+    double a4 = ((qm2 + q2) - 4.0 * (qm1 + q1) + 6.0 * q0) * (1.0 / 24.0);
+    const double c13_3 = 13.0 / 3.0;
+    double b[4];
+    for (int k = 0; k < 3; ++k) b[k] = a1[k] * a1[k] + c13_3 * a2[k] * a2[k];
+    b[3] = a1[3] * (a1[3] + 0.5 * a3) + c13_3 * a2[3] * a2[3] + (21.0 / 5.0) * a2[3] * a4
+         + (3129.0 / 80.0) * a3 * a3 + (87617.0 / 140.0) * a4 * a4;
+    double tau = (fabs(b[3] - b[0]) + fabs(b[3] - b[1]) + fabs(b[3] - b[2])) * (1.0 / 3.0);
+    double e[4], r[4], w[4], wsum = 0.0;
+    for (int k = 0; k < 4; ++k) { e[k] = b[k] + S.eps; r[k] = tau / e[k]; w[k] = S.d[k] * (1.0 + r[k] * r[k]); wsum += w[k]; }
+    double iw = 1.0 / wsum;
+    double c3 = w[3] * iw * S.inv_d3;
+    double c[4];
+    for (int k = 0; k < 3; ++k) c[k] = w[k] * iw - c3 * S.d[k];
+    c[3] = c3;
+    // reverse
+    double a1b[4], a2b[4], cb[4];
+    for (int k = 0; k < 4; ++k) { a1b[k] = ob.A1 * c[k]; a2b[k] = ob.A2 * c[k]; cb[k] = ob.A1 * a1[k] + ob.A2 * a2[k]; }
+    cb[3] += ob.c3a3 * a3 + ob.c3a4 * a4;
+    double a3b = ob.c3a3 * c3, a4b = ob.c3a4 * c3;
+    double wb[4] = {0, 0, 0, 0}, iwb = 0.0;
+    for (int k = 0; k < 3; ++k) { wb[k] += cb[k] * iw; iwb += cb[k] * w[k]; cb[3] += -cb[k] * S.d[k]; }
+    wb[3] += cb[3] * iw * S.inv_d3;
+    iwb += cb[3] * w[3] * S.inv_d3;
+    double sumb = -iwb * iw * iw;
+    double rb[4];
+    for (int k = 0; k < 4; ++k) { wb[k] += sumb; rb[k] = wb[k] * S.d[k] * 2.0 * r[k]; }
+    // rmax / rmin: the first index attaining them
+    int kmax = 0, kmin = 0;
+    for (int k = 1; k < 4; ++k) { if (r[k] > r[kmax]) kmax = k; if (r[k] < r[kmin]) kmin = k; }
+    rb[kmax] += ob.rmax;
+    rb[kmin] += ob.rmin;
+    double taub = 0.0, bb[4];
+    for (int k = 0; k < 4; ++k) { taub += rb[k] / e[k]; bb[k] = -rb[k] * r[k] / e[k]; }
+    for (int k = 0; k < 3; ++k) {
+        double sg = (b[3] - b[k]) >= 0.0 ? 1.0 : -1.0;
+        bb[3] += taub * (1.0 / 3.0) * sg;
+        bb[k] -= taub * (1.0 / 3.0) * sg;
+    }
+    for (int k = 0; k < 3; ++k) { a1b[k] += bb[k] * 2.0 * a1[k]; a2b[k] += bb[k] * 2.0 * c13_3 * a2[k]; }
+    a1b[3] += bb[3] * (2.0 * a1[3] + 0.5 * a3);
+    a3b += bb[3] * (0.5 * a1[3] + 2.0 * (3129.0 / 80.0) * a3);
+    a2b[3] += bb[3] * (2.0 * c13_3 * a2[3] + (21.0 / 5.0) * a4);
+    a4b += bb[3] * ((21.0 / 5.0) * a2[3] + 2.0 * (87617.0 / 140.0) * a4);
+    // coefficients -> stencil values
+    qb[0] += 0.5 * a1b[0] + 0.5 * a2b[0] + (5.0 / 48.0) * a1b[3] - (1.0 / 16.0) * a2b[3] - (1.0 / 12.0) * a3b + (1.0 / 24.0) * a4b;
+    qb[1] += -2.0 * a1b[0] - a2b[0] - 0.5 * a1b[1] + 0.5 * a2b[1] - (34.0 / 48.0) * a1b[3] + (12.0 / 16.0) * a2b[3]
+           + (2.0 / 12.0) * a3b - (4.0 / 24.0) * a4b;
+    qb[2] += 1.5 * a1b[0] + 0.5 * a2b[0] - a2b[1] - 1.5 * a1b[2] + 0.5 * a2b[2] - (22.0 / 16.0) * a2b[3] + (6.0 / 24.0) * a4b;
+    qb[3] += 0.5 * a1b[1] + 0.5 * a2b[1] + 2.0 * a1b[2] - a2b[2] + (34.0 / 48.0) * a1b[3] + (12.0 / 16.0) * a2b[3]
+           - (2.0 / 12.0) * a3b - (4.0 / 24.0) * a4b;
+    qb[4] += -0.5 * a1b[2] + 0.5 * a2b[2] - (5.0 / 48.0) * a1b[3] - (1.0 / 16.0) * a2b[3] + (1.0 / 12.0) * a3b + (1.0 / 24.0) * a4b;
+}
+
+DFK_HD void limiter_alpha_vjp(const AO& o, double outb, AOBar& ob) {
+    double a1 = 1.0 + o.rmax * o.rmax, a2 = 1.0 + o.rmin * o.rmin, D = a1 + a2;
+    ob.rmax += outb * (-2.0 * a2 / (D * D)) * 2.0 * o.rmax;
+    ob.rmin += outb * (2.0 * a1 / (D * D)) * 2.0 * o.rmin;
+}
+
+DFK_HD void ao_at_right_edge_vjp(double valb, double slopeb, double& q0b, AOBar& ob) {
+    q0b += valb;
+    ob.A1 += 0.5 * valb + slopeb;
+    ob.A2 += (1.0 / 6.0) * valb + slopeb;
+    ob.c3a3 += 0.125 * valb + 0.75 * slopeb;
+    ob.c3a4 += 0.05 * valb + 0.5 * slopeb;
+}
+
+DFK_HD void ao_at_gauss_vjp(const double valb[2], const double slopeb[2], double& q0b, AOBar& ob) {
+    const double g = kGaussEta;
+    double Eb = valb[0] + valb[1], Ob = valb[1] - valb[0], Esb = slopeb[0] + slopeb[1], Osb = slopeb[1] - slopeb[0];
+    q0b += Eb;
+    ob.c3a4 += -(1.0 / 180.0) * Eb + g * (1.0 / 3.0) * Osb;
+    ob.A1 += g * Ob + Esb;
+    ob.c3a3 += g * (1.0 / 12.0) * Ob + 0.25 * Esb;
+    ob.A2 += 2.0 * g * Osb;
+}
+
+// a1 = (q3 - q1)/2, a2 = (q1 - 2 q2 + q3)/2 of the DF quadratic
+DFK_HD void df_coeffs_vjp(double a1b, double a2b, double qb[5]) {
+    qb[3] += 0.5 * a1b + 0.5 * a2b;
+    qb[1] += -0.5 * a1b + 0.5 * a2b;
+    qb[2] += -a2b;
+}
+
+DFK_HD void df_at_right_edge_vjp(double alpha, double valb, double slopeb, double qb[5]) {
+    qb[2] += valb;
+    df_coeffs_vjp(alpha * (0.5 * valb + slopeb), alpha * ((1.0 / 6.0) * valb + slopeb), qb);
+}
+
+DFK_HD void df_at_gauss_vjp(double alpha, const double valb[2], const double slopeb[2], double qb[5]) {
+    const double g = kGaussEta;
+    qb[2] += valb[0] + valb[1];
+    double Ob = valb[1] - valb[0], Esb = slopeb[0] + slopeb[1], Osb = slopeb[1] - slopeb[0];
+    df_coeffs_vjp(alpha * g * Ob + alpha * Esb, 2.0 * alpha * g * Osb, qb);
+}
+
+// ------------------------------------------------------------------------------------------
+// GKS flux
+// ------------------------------------------------------------------------------------------
+struct MaxwBar { double rho, ir, U, V, p, tl, il2, f4, qK; };
+struct MomBar { double mu[7], mv[6], mx[3]; };
+
+DFK_HD void zero(MaxwBar& b) { b.rho = b.ir = b.U = b.V = b.p = b.tl = b.il2 = b.f4 = b.qK = 0.0; }
+DFK_HD void zero(MomBar& b) {
+    for (int i = 0; i < 7; ++i) b.mu[i] = 0.0;
+    for (int i = 0; i < 6; ++i) b.mv[i] = 0.0;
+    for (int i = 0; i < 3; ++i) b.mx[i] = 0.0;
+}
+
+DFK_HD void maxw_of_vjp(const double W[4], const SchemeConsts& S, const Maxw& s, const MaxwBar& sb, double Wb[4]) {
+    double tlb = sb.tl + sb.f4 * 2.0 * s.tl * S.inv_K2;
+    double Ub = sb.U + sb.qK * 2.0 * s.U, Vb = sb.V + sb.qK * 2.0 * s.V;
+    double il2b = sb.il2 + sb.qK * (S.K + 2.0);
+    double pb = sb.p + il2b * s.ir;
+    double irb = sb.ir + il2b * s.p;
+    Wb[0] += tlb / s.p;
+    pb += -tlb * s.tl / s.p;
+    Wb[3] += pb * S.gm1;
+    Wb[0] += -pb * S.gm1 * 0.5 * (s.U * s.U + s.V * s.V);
+    Ub += -pb * S.gm1 * W[0] * s.U;
+    Vb += -pb * S.gm1 * W[0] * s.V;
+    Wb[1] += Ub * s.ir;
+    Wb[2] += Vb * s.ir;
+    irb += Ub * W[1] + Vb * W[2];
+    Wb[0] += -irb * s.ir * s.ir + sb.rho;
+}
+
+// adjoint of fill_moments; accumulates into the state's U, V, il2 and tl adjoints
+template <int HALF>
+DFK_HD void fill_moments_vjp(const Maxw& s, double K, const Mom& m, MomBar& mb, MaxwBar& sb) {
+    sb.il2 += mb.mx[1] * K + mb.mx[2] * K * (K + 2.0) * 2.0 * s.il2;
+    for (int n = 5; n >= 2; --n) {
+        double g = mb.mv[n];
+        sb.V += g * m.mv[n - 1];
+        mb.mv[n - 1] += g * s.V;
+        sb.il2 += g * (double)(n - 1) * m.mv[n - 2];
+        mb.mv[n - 2] += g * (double)(n - 1) * s.il2;
+    }
+    sb.V += mb.mv[1];
+    for (int n = 6; n >= 2; --n) {
+        double g = mb.mu[n];
+        sb.U += g * m.mu[n - 1];
+        mb.mu[n - 1] += g * s.U;
+        sb.il2 += g * (double)(n - 1) * m.mu[n - 2];
+        mb.mu[n - 2] += g * (double)(n - 1) * s.il2;
+    }
+    if (HALF == 0) {
+        sb.U += mb.mu[1];
+    } else {
+        double lam = 0.5 * s.tl;
+        double isl = rsqrt(lam);
+        double x = lam * isl * s.U;
+        double ex = exp(-x * x);
+        double e = ex * (0.28209479177387814347 * isl);
+        // mu1 = U mu0 +/- e
+        sb.U += mb.mu[1] * m.mu[0];
+        double mu0b = mb.mu[0] + mb.mu[1] * s.U;
+        double eb = HALF > 0 ? mb.mu[1] : -mb.mu[1];
+        // mu0 = erfc(-/+ x)/2: d/dx = +/- exp(-x^2)/sqrt(pi)
+        double xb = mu0b * (HALF > 0 ? 1.0 : -1.0) * ex * 0.56418958354775628695;
+        xb += eb * e * (-2.0 * x);
+        double islb = eb * ex * 0.28209479177387814347;
+        double lamb = xb * isl * s.U;
+        islb += xb * lam * s.U;
+        sb.U += xb * lam * isl;
+        lamb += -0.5 * islb * isl * isl * isl;
+        sb.tl += 0.5 * lamb;
+    }
+}
+
+template <int k, int l, int c>
+DFK_HD void M_vjp(const Mom& m, double g, MomBar& mb) {
+    mb.mu[k] += g * m.mv[l] * m.mx[c];
+    mb.mv[l] += g * m.mu[k] * m.mx[c];
+    mb.mx[c] += g * m.mu[k] * m.mv[l];
+}
+
+template <int k, int l, int c>
+DFK_HD void psi_mom_vjp(const Mom& m, const double ob[4], MomBar& mb) {
+    M_vjp<k, l, c>(m, ob[0], mb);
+    M_vjp<k + 1, l, c>(m, ob[1], mb);
+    M_vjp<k, l + 1, c>(m, ob[2], mb);
+    M_vjp<k + 2, l, c>(m, 0.5 * ob[3], mb);
+    M_vjp<k, l + 2, c>(m, 0.5 * ob[3], mb);
+    M_vjp<k, l, c + 1>(m, 0.5 * ob[3], mb);
+}
+
+template <int k, int l>
+DFK_HD void a_mom_vjp(const Mom& m, const double a[4], const double ob[4], MomBar& mb, double ab[4]) {
+    double t0[4], t1[4], t2[4], t3[4], t4[4], t5[4];
+    psi_mom<k, l, 0>(m, t0);
+    psi_mom<k + 1, l, 0>(m, t1);
+    psi_mom<k, l + 1, 0>(m, t2);
+    psi_mom<k + 2, l, 0>(m, t3);
+    psi_mom<k, l + 2, 0>(m, t4);
+    psi_mom<k, l, 1>(m, t5);
+    double h = 0.5 * a[3];
+    double tb[4];
+    for (int i = 0; i < 4; ++i) {
+        ab[0] += ob[i] * t0[i];
+        ab[1] += ob[i] * t1[i];
+        ab[2] += ob[i] * t2[i];
+        ab[3] += 0.5 * ob[i] * (t3[i] + t4[i] + t5[i]);
+    }
+    for (int i = 0; i < 4; ++i) tb[i] = ob[i] * a[0];
+    psi_mom_vjp<k, l, 0>(m, tb, mb);
+    for (int i = 0; i < 4; ++i) tb[i] = ob[i] * a[1];
+    psi_mom_vjp<k + 1, l, 0>(m, tb, mb);
+    for (int i = 0; i < 4; ++i) tb[i] = ob[i] * a[2];
+    psi_mom_vjp<k, l + 1, 0>(m, tb, mb);
+    for (int i = 0; i < 4; ++i) tb[i] = ob[i] * h;
+    psi_mom_vjp<k + 2, l, 0>(m, tb, mb);
+    psi_mom_vjp<k, l + 2, 0>(m, tb, mb);
+    psi_mom_vjp<k, l, 1>(m, tb, mb);
+}
+
+// adjoint of slope_solve: bb += S^T ab, state adjoints accumulated
+DFK_HD void slope_solve_vjp(const Maxw& s, const double b[4], const double abin[4], double bb[4], MaxwBar& sb) {
+    double R2 = b[1] - s.U * b[0], R3 = b[2] - s.V * b[0], R4 = 2.0 * b[3] - s.qK * b[0];
+    double X = R4 - 2.0 * s.U * R2 - 2.0 * s.V * R3;
+    double a3 = s.f4 * X;
+    double a2 = s.tl * R3 - s.V * a3;
+    double a1 = s.tl * R2 - s.U * a3;
+    double ab0 = abin[0], ab1 = abin[1], ab2 = abin[2], ab3 = abin[3];
+    // a0 = b0 - U a1 - V a2 - a3 qK / 2
+    bb[0] += ab0;
+    sb.U += -ab0 * a1;
+    ab1 += -ab0 * s.U;
+    sb.V += -ab0 * a2;
+    ab2 += -ab0 * s.V;
+    ab3 += -ab0 * 0.5 * s.qK;
+    sb.qK += -ab0 * 0.5 * a3;
+    // a1 = tl R2 - U a3
+    sb.tl += ab1 * R2;
+    double R2b = ab1 * s.tl;
+    sb.U += -ab1 * a3;
+    ab3 += -ab1 * s.U;
+    // a2 = tl R3 - V a3
+    sb.tl += ab2 * R3;
+    double R3b = ab2 * s.tl;
+    sb.V += -ab2 * a3;
+    ab3 += -ab2 * s.V;
+    // a3 = f4 X
+    sb.f4 += ab3 * X;
+    double Xb = ab3 * s.f4;
+    double R4b = Xb;
+    sb.U += -Xb * 2.0 * R2;
+    R2b += -Xb * 2.0 * s.U;
+    sb.V += -Xb * 2.0 * R3;
+    R3b += -Xb * 2.0 * s.V;
+    bb[3] += 2.0 * R4b;
+    sb.qK += -R4b * b[0];
+    bb[0] += -R4b * s.qK;
+    bb[2] += R3b;
+    sb.V += -R3b * b[0];
+    bb[0] += -R3b * s.V;
+    bb[1] += R2b;
+    sb.U += -R2b * b[0];
+    bb[0] += -R2b * s.U;
+}
+
+// value and derivative with respect to tau_n/dt of the combined time coefficients of Eq. 27
+struct Dual { double v, d; };
+DFK_HD Dual dmul(Dual a, Dual b) { return Dual{a.v * b.v, a.d * b.v + a.v * b.d}; }
+DFK_HD Dual dadd(Dual a, Dual b) { return Dual{a.v + b.v, a.d + b.d}; }
+DFK_HD Dual dsub(Dual a, Dual b) { return Dual{a.v - b.v, a.d - b.d}; }
+DFK_HD Dual dscale(double c, Dual a) { return Dual{c * a.v, c * a.d}; }
+
+struct TimeCoeffs { Dual gcF, gcD, acF, acD, AcF, AcD, glrF, glrD, alrF, alrD, AlrF, AlrD; };
+
+DFK_HD TimeCoeffs time_coeffs(double rT, double dt, int tau_reading) {
+    Dual r = {rT, 1.0};
+    Dual T = dscale(dt, r);
+    Dual tau = tau_reading == 1 ? T : Dual{0.0, 0.0};
+    Dual E2 = {0.0, 0.0}, rr = {0.0, 0.0};
+    if (rT > 0.0) { double e = exp(-0.5 / rT); E2 = Dual{e, e * 0.5 / (rT * rT)}; rr = r; }
+    Dual E1 = dmul(E2, E2);
+    Dual om = dsub(Dual{1.0, 0.0}, E2);
+    Dual S3 = dmul(om, dsub(Dual{3.0, 0.0}, E2));
+    double idt = 1.0 / dt;
+    TimeCoeffs c;
+    c.glrF = dmul(rr, S3);
+    c.glrD = dscale(-4.0 * idt, dmul(rr, dmul(om, om)));
+    c.gcF = dsub(Dual{1.0, 0.0}, c.glrF);
+    c.gcD = dscale(-1.0, c.glrD);
+    Dual TT = dadd(dmul(T, T), dmul(T, tau));
+    c.acF = dsub(dadd(dsub(dscale(idt, dmul(TT, S3)), dscale(2.0, dmul(T, E2))), dmul(T, E1)), tau);
+    c.acD = dscale(4.0 * idt * idt, dadd(dscale(-1.0, dmul(TT, dmul(om, om))), dscale(dt, dmul(T, dmul(E2, om)))));
+    c.AcF = dadd(dscale(-1.0, tau), dmul(tau, dmul(rr, S3)));
+    c.AcD = dsub(Dual{1.0, 0.0}, dscale(4.0 * idt * idt, dmul(dmul(T, tau), dmul(om, om))));
+    c.alrF = dsub(dscale(-1.0, c.acF), tau);
+    c.alrD = dscale(-1.0, c.acD);
+    c.AlrF = dscale(-idt, dmul(dmul(T, tau), S3));
+    c.AlrD = dscale(4.0 * idt * idt, dmul(dmul(T, tau), dmul(om, om)));
+    return c;
+}
+
+struct GPStateBar { double W[4], Wn[4], Wt[4]; };
+
+// adjoint of gks_flux: given Fb, dFb (local frame) accumulates into Lb, Rb
+DFK_HD void gks_flux_vjp(const GPState& L, const GPState& R, double dt, const SchemeConsts& S,
+                         const double Fb[4], const double dFb[4], GPStateBar& Lb, GPStateBar& Rb) {
+    const double K = S.K;
+    // ---- forward recompute
+    Maxw sl = maxw_of(L.W, S), sr = maxw_of(R.W, S);
+    Mom ml, mr;
+    fill_moments<+1>(sl, K, ml);
+    fill_moments<-1>(sr, K, mr);
+    double bLx[4], bLy[4], bRx[4], bRy[4], alx[4], aly[4], arx[4], ary[4];
+    for (int i = 0; i < 4; ++i) { bLx[i] = L.Wn[i] * sl.ir; bLy[i] = L.Wt[i] * sl.ir; bRx[i] = R.Wn[i] * sr.ir; bRy[i] = R.Wt[i] * sr.ir; }
+    slope_solve(sl, bLx, alx);
+    slope_solve(sl, bLy, aly);
+    slope_solve(sr, bRx, arx);
+    slope_solve(sr, bRy, ary);
+    double Wc[4], Wcx[4], Wcy[4], t1[4], t2[4];
+    double pl0[4], pr0[4], lx0[4], rx0[4], ly0[4], ry0[4];
+    psi_mom<0, 0, 0>(ml, pl0); psi_mom<0, 0, 0>(mr, pr0);
+    a_mom<0, 0>(ml, alx, lx0); a_mom<0, 0>(mr, arx, rx0);
+    a_mom<0, 0>(ml, aly, ly0); a_mom<0, 0>(mr, ary, ry0);
+    for (int i = 0; i < 4; ++i) {
+        Wc[i] = sl.rho * pl0[i] + sr.rho * pr0[i];
+        Wcx[i] = sl.rho * lx0[i] + sr.rho * rx0[i];
+        Wcy[i] = sl.rho * ly0[i] + sr.rho * ry0[i];
+    }
+    Maxw sc = maxw_of(Wc, S);
+    Mom mc;
+    fill_moments<0>(sc, K, mc);
+    double bcx[4], bcy[4], bct[4], acx[4], acy[4], Ac[4];
+    for (int i = 0; i < 4; ++i) { bcx[i] = Wcx[i] * sc.ir; bcy[i] = Wcy[i] * sc.ir; }
+    slope_solve(sc, bcx, acx);
+    slope_solve(sc, bcy, acy);
+    a_mom<1, 0>(mc, acx, t1); a_mom<0, 1>(mc, acy, t2);
+    for (int i = 0; i < 4; ++i) bct[i] = -(t1[i] + t2[i]);
+    slope_solve(sc, bct, Ac);
+    double Mc0[4], Mc1[4], Mc2[4], Ml0[4], Mr0[4], Ml1[4], Mr1[4];
+    psi_mom<1, 0, 0>(mc, Mc0);
+    a_mom<2, 0>(mc, acx, t1); a_mom<1, 1>(mc, acy, t2);
+    for (int i = 0; i < 4; ++i) Mc1[i] = t1[i] + t2[i];
+    a_mom<1, 0>(mc, Ac, Mc2);
+    psi_mom<1, 0, 0>(ml, Ml0);
+    psi_mom<1, 0, 0>(mr, Mr0);
+    a_mom<2, 0>(ml, alx, t1); a_mom<1, 1>(ml, aly, t2);
+    for (int i = 0; i < 4; ++i) Ml1[i] = t1[i] + t2[i];
+    a_mom<2, 0>(mr, arx, t1); a_mom<1, 1>(mr, ary, t2);
+    for (int i = 0; i < 4; ++i) Mr1[i] = t1[i] + t2[i];
+    double q = (sl.p - sr.p) / (sl.p + sr.p);
+    double rT = S.C1 + S.C2 * fabs(q);
+    TimeCoeffs tc = time_coeffs(rT, dt, S.tau_reading);
+    double Ml2[4] = {0, 0, 0, 0}, Mr2[4] = {0, 0, 0, 0}, Al[4] = {0, 0, 0, 0}, Ar[4] = {0, 0, 0, 0};
+    double bAl[4] = {0, 0, 0, 0}, bAr[4] = {0, 0, 0, 0};
+    Mom mlF, mrF;
+    if (S.tau_reading == 1) {
+        fill_moments<0>(sl, K, mlF);
+        fill_moments<0>(sr, K, mrF);
+        a_mom<1, 0>(mlF, alx, t1); a_mom<0, 1>(mlF, aly, t2);
+        for (int i = 0; i < 4; ++i) bAl[i] = -(t1[i] + t2[i]);
+        slope_solve(sl, bAl, Al);
+        a_mom<1, 0>(mrF, arx, t1); a_mom<0, 1>(mrF, ary, t2);
+        for (int i = 0; i < 4; ++i) bAr[i] = -(t1[i] + t2[i]);
+        slope_solve(sr, bAr, Ar);
+        a_mom<1, 0>(ml, Al, Ml2);
+        a_mom<1, 0>(mr, Ar, Mr2);
+    }
+    // ---- reverse of the final combination
+    MaxwBar slb, srb, scb;
+    zero(slb); zero(srb); zero(scb);
+    MomBar mlb, mrb, mcb;
+    zero(mlb); zero(mrb); zero(mcb);
+    double Mc0b[4], Mc1b[4], Mc2b[4], Ml0b[4], Mr0b[4], Ml1b[4], Mr1b[4], Ml2b[4], Mr2b[4];
+    double rTb = 0.0;
+    for (int i = 0; i < 4; ++i) {
+        double c0 = sc.rho * Mc0[i], c1 = sc.rho * Mc1[i], c2 = sc.rho * Mc2[i];
+        double g0 = sl.rho * Ml0[i] + sr.rho * Mr0[i];
+        double g1 = sl.rho * Ml1[i] + sr.rho * Mr1[i];
+        double g2 = sl.rho * Ml2[i] + sr.rho * Mr2[i];
+        double c0b = Fb[i] * tc.gcF.v + dFb[i] * tc.gcD.v;
+        double c1b = Fb[i] * tc.acF.v + dFb[i] * tc.acD.v;
+        double c2b = Fb[i] * tc.AcF.v + dFb[i] * tc.AcD.v;
+        double g0b = Fb[i] * tc.glrF.v + dFb[i] * tc.glrD.v;
+        double g1b = Fb[i] * tc.alrF.v + dFb[i] * tc.alrD.v;
+        double g2b = Fb[i] * tc.AlrF.v + dFb[i] * tc.AlrD.v;
+        rTb += Fb[i] * (tc.gcF.d * c0 + tc.acF.d * c1 + tc.AcF.d * c2 + tc.glrF.d * g0 + tc.alrF.d * g1 + tc.AlrF.d * g2)
+             + dFb[i] * (tc.gcD.d * c0 + tc.acD.d * c1 + tc.AcD.d * c2 + tc.glrD.d * g0 + tc.alrD.d * g1 + tc.AlrD.d * g2);
+        scb.rho += c0b * Mc0[i] + c1b * Mc1[i] + c2b * Mc2[i];
+        Mc0b[i] = c0b * sc.rho; Mc1b[i] = c1b * sc.rho; Mc2b[i] = c2b * sc.rho;
+        slb.rho += g0b * Ml0[i] + g1b * Ml1[i] + g2b * Ml2[i];
+        srb.rho += g0b * Mr0[i] + g1b * Mr1[i] + g2b * Mr2[i];
+        Ml0b[i] = g0b * sl.rho; Ml1b[i] = g1b * sl.rho; Ml2b[i] = g2b * sl.rho;
+        Mr0b[i] = g0b * sr.rho; Mr1b[i] = g1b * sr.rho; Mr2b[i] = g2b * sr.rho;
+    }
+    // tau_n / dt = C1 + C2 |(pl - pr)/(pl + pr)|
+    {
+        double sg = q >= 0.0 ? 1.0 : -1.0;
+        double den = (sl.p + sr.p) * (sl.p + sr.p);
+        slb.p += rTb * S.C2 * sg * 2.0 * sr.p / den;
+        srb.p += rTb * S.C2 * sg * (-2.0) * sl.p / den;
+    }
+    double alxb[4] = {0, 0, 0, 0}, alyb[4] = {0, 0, 0, 0}, arxb[4] = {0, 0, 0, 0}, aryb[4] = {0, 0, 0, 0};
+    double acxb[4] = {0, 0, 0, 0}, acyb[4] = {0, 0, 0, 0}, Acb[4] = {0, 0, 0, 0};
+    if (S.tau_reading == 1) {
+        double Alb[4] = {0, 0, 0, 0}, Arb[4] = {0, 0, 0, 0}, bAlb[4] = {0, 0, 0, 0}, bArb[4] = {0, 0, 0, 0};
+        MomBar mlFb, mrFb;
+        zero(mlFb); zero(mrFb);
+        a_mom_vjp<1, 0>(ml, Al, Ml2b, mlb, Alb);
+        a_mom_vjp<1, 0>(mr, Ar, Mr2b, mrb, Arb);
+        slope_solve_vjp(sl, bAl, Alb, bAlb, slb);
+        slope_solve_vjp(sr, bAr, Arb, bArb, srb);
+        double nb[4];
+        for (int i = 0; i < 4; ++i) nb[i] = -bAlb[i];
+        a_mom_vjp<1, 0>(mlF, alx, nb, mlFb, alxb);
+        a_mom_vjp<0, 1>(mlF, aly, nb, mlFb, alyb);
+        for (int i = 0; i < 4; ++i) nb[i] = -bArb[i];
+        a_mom_vjp<1, 0>(mrF, arx, nb, mrFb, arxb);
+        a_mom_vjp<0, 1>(mrF, ary, nb, mrFb, aryb);
+        fill_moments_vjp<0>(sl, K, mlF, mlFb, slb);
+        fill_moments_vjp<0>(sr, K, mrF, mrFb, srb);
+    }
+    // flux moments
+    psi_mom_vjp<1, 0, 0>(mc, Mc0b, mcb);
+    a_mom_vjp<2, 0>(mc, acx, Mc1b, mcb, acxb);
+    a_mom_vjp<1, 1>(mc, acy, Mc1b, mcb, acyb);
+    a_mom_vjp<1, 0>(mc, Ac, Mc2b, mcb, Acb);
+    psi_mom_vjp<1, 0, 0>(ml, Ml0b, mlb);
+    psi_mom_vjp<1, 0, 0>(mr, Mr0b, mrb);
+    a_mom_vjp<2, 0>(ml, alx, Ml1b, mlb, alxb);
+    a_mom_vjp<1, 1>(ml, aly, Ml1b, mlb, alyb);
+    a_mom_vjp<2, 0>(mr, arx, Mr1b, mrb, arxb);
+    a_mom_vjp<1, 1>(mr, ary, Mr1b, mrb, aryb);
+    // A^c from the compatibility condition
+    double bctb[4] = {0, 0, 0, 0};
+    slope_solve_vjp(sc, bct, Acb, bctb, scb);
+    double nb[4];
+    for (int i = 0; i < 4; ++i) nb[i] = -bctb[i];
+    a_mom_vjp<1, 0>(mc, acx, nb, mcb, acxb);
+    a_mom_vjp<0, 1>(mc, acy, nb, mcb, acyb);
+    // equilibrium slopes
+    double bcxb[4] = {0, 0, 0, 0}, bcyb[4] = {0, 0, 0, 0};
+    slope_solve_vjp(sc, bcx, acxb, bcxb, scb);
+    slope_solve_vjp(sc, bcy, acyb, bcyb, scb);
+    double Wcb[4] = {0, 0, 0, 0}, Wcxb[4], Wcyb[4];
+    for (int i = 0; i < 4; ++i) {
+        Wcxb[i] = bcxb[i] * sc.ir;
+        Wcyb[i] = bcyb[i] * sc.ir;
+        scb.ir += bcxb[i] * Wcx[i] + bcyb[i] * Wcy[i];
+    }
+    fill_moments_vjp<0>(sc, K, mc, mcb, scb);
+    maxw_of_vjp(Wc, S, sc, scb, Wcb);
+    // kinetic weighting of the equilibrium state and its slopes
+    double plb[4], prb[4];
+    for (int i = 0; i < 4; ++i) {
+        slb.rho += Wcb[i] * pl0[i] + Wcxb[i] * lx0[i] + Wcyb[i] * ly0[i];
+        srb.rho += Wcb[i] * pr0[i] + Wcxb[i] * rx0[i] + Wcyb[i] * ry0[i];
+        plb[i] = Wcb[i] * sl.rho;
+        prb[i] = Wcb[i] * sr.rho;
+    }
+    psi_mom_vjp<0, 0, 0>(ml, plb, mlb);
+    psi_mom_vjp<0, 0, 0>(mr, prb, mrb);
+    double tb[4];
+    for (int i = 0; i < 4; ++i) tb[i] = Wcxb[i] * sl.rho;
+    a_mom_vjp<0, 0>(ml, alx, tb, mlb, alxb);
+    for (int i = 0; i < 4; ++i) tb[i] = Wcxb[i] * sr.rho;
+    a_mom_vjp<0, 0>(mr, arx, tb, mrb, arxb);
+    for (int i = 0; i < 4; ++i) tb[i] = Wcyb[i] * sl.rho;
+    a_mom_vjp<0, 0>(ml, aly, tb, mlb, alyb);
+    for (int i = 0; i < 4; ++i) tb[i] = Wcyb[i] * sr.rho;
+    a_mom_vjp<0, 0>(mr, ary, tb, mrb, aryb);
+    // side slope coefficients
+    double bb[4];
+    for (int i = 0; i < 4; ++i) bb[i] = 0.0;
+    slope_solve_vjp(sl, bLx, alxb, bb, slb);
+    for (int i = 0; i < 4; ++i) { Lb.Wn[i] += bb[i] * sl.ir; slb.ir += bb[i] * L.Wn[i]; bb[i] = 0.0; }
+    slope_solve_vjp(sl, bLy, alyb, bb, slb);
+    for (int i = 0; i < 4; ++i) { Lb.Wt[i] += bb[i] * sl.ir; slb.ir += bb[i] * L.Wt[i]; bb[i] = 0.0; }
+    slope_solve_vjp(sr, bRx, arxb, bb, srb);
+    for (int i = 0; i < 4; ++i) { Rb.Wn[i] += bb[i] * sr.ir; srb.ir += bb[i] * R.Wn[i]; bb[i] = 0.0; }
+    slope_solve_vjp(sr, bRy, aryb, bb, srb);
+    for (int i = 0; i < 4; ++i) { Rb.Wt[i] += bb[i] * sr.ir; srb.ir += bb[i] * R.Wt[i]; }
+    fill_moments_vjp<+1>(sl, K, ml, mlb, slb);
+    fill_moments_vjp<-1>(sr, K, mr, mrb, srb);
+    maxw_of_vjp(L.W, S, sl, slb, Lb.W);
+    maxw_of_vjp(R.W, S, sr, srb, Rb.W);
+}
+
+// ------------------------------------------------------------------------------------------
+// Lax-Friedrichs flux
+// ------------------------------------------------------------------------------------------
+struct EulerBar { double u, v, p, c, H, q; };
+
+DFK_HD void euler_pt_vjp(const double W[4], const SchemeConsts& S, const EulerPt& e, EulerBar eb, double Wb[4]) {
+    double ir = 1.0 / W[0];
+    double irb = 0.0;
+    Wb[3] += eb.H * ir;
+    eb.p += eb.H * ir;
+    irb += eb.H * (W[3] + e.p);
+    double sb = eb.c * 0.5 / e.c;
+    eb.p += sb * S.gamma * ir;
+    irb += sb * S.gamma * e.p;
+    Wb[3] += eb.p * S.gm1;
+    Wb[0] += -eb.p * S.gm1 * e.q;
+    eb.q += -eb.p * S.gm1 * W[0];
+    eb.u += eb.q * e.u;
+    eb.v += eb.q * e.v;
+    Wb[1] += eb.u * ir;
+    Wb[2] += eb.v * ir;
+    irb += eb.u * W[1] + eb.v * W[2];
+    Wb[0] += -irb * ir * ir;
+}
+
+DFK_HD void jac_dp_vjp(const EulerPt& e, double gm1, const double X[4], double dpb, EulerBar& eb, double Xb[4]) {
+    Xb[3] += dpb * gm1;
+    eb.u += -dpb * gm1 * X[1];
+    Xb[1] += -dpb * gm1 * e.u;
+    eb.v += -dpb * gm1 * X[2];
+    Xb[2] += -dpb * gm1 * e.v;
+    eb.q += dpb * gm1 * X[0];
+    Xb[0] += dpb * gm1 * e.q;
+}
+
+DFK_HD void jac_x_vjp(const EulerPt& e, double gm1, const double X[4], const double Yb[4], EulerBar& eb, double Xb[4]) {
+    double dp = gm1 * (X[3] - e.u * X[1] - e.v * X[2] + e.q * X[0]);
+    double dpb = 0.0;
+    Xb[1] += Yb[0];
+    eb.u += Yb[1] * (2.0 * X[1] - 2.0 * e.u * X[0]);
+    Xb[1] += Yb[1] * 2.0 * e.u;
+    Xb[0] += -Yb[1] * e.u * e.u;
+    dpb += Yb[1];
+    eb.v += Yb[2] * (X[1] - e.u * X[0]);
+    Xb[1] += Yb[2] * e.v;
+    eb.u += Yb[2] * (X[2] - e.v * X[0]);
+    Xb[2] += Yb[2] * e.u;
+    Xb[0] += -Yb[2] * e.u * e.v;
+    eb.u += Yb[3] * ((X[3] + dp) - e.H * X[0]);
+    Xb[3] += Yb[3] * e.u;
+    dpb += Yb[3] * e.u;
+    eb.H += Yb[3] * (X[1] - e.u * X[0]);
+    Xb[1] += Yb[3] * e.H;
+    Xb[0] += -Yb[3] * e.H * e.u;
+    jac_dp_vjp(e, gm1, X, dpb, eb, Xb);
+}
+
+DFK_HD void jac_y_vjp(const EulerPt& e, double gm1, const double X[4], const double Yb[4], EulerBar& eb, double Xb[4]) {
+    double dp = gm1 * (X[3] - e.u * X[1] - e.v * X[2] + e.q * X[0]);
+    double dpb = 0.0;
+    Xb[2] += Yb[0];
+    eb.v += Yb[1] * (X[1] - e.u * X[0]);
+    Xb[1] += Yb[1] * e.v;
+    eb.u += Yb[1] * (X[2] - e.v * X[0]);
+    Xb[2] += Yb[1] * e.u;
+    Xb[0] += -Yb[1] * e.u * e.v;
+    eb.v += Yb[2] * (2.0 * X[2] - 2.0 * e.v * X[0]);
+    Xb[2] += Yb[2] * 2.0 * e.v;
+    Xb[0] += -Yb[2] * e.v * e.v;
+    dpb += Yb[2];
+    eb.v += Yb[3] * ((X[3] + dp) - e.H * X[0]);
+    Xb[3] += Yb[3] * e.v;
+    dpb += Yb[3] * e.v;
+    eb.H += Yb[3] * (X[2] - e.v * X[0]);
+    Xb[2] += Yb[3] * e.H;
+    Xb[0] += -Yb[3] * e.H * e.v;
+    jac_dp_vjp(e, gm1, X, dpb, eb, Xb);
+}
+
+DFK_HD void lf_flux_vjp(const GPState& L, const GPState& R, const SchemeConsts& S, const double Fb[4],
+                        const double dFb[4], GPStateBar& Lb, GPStateBar& Rb) {
+    EulerPt el = euler_pt(L.W, S), er = euler_pt(R.W, S);
+    double sL = fabs(el.u) + el.c, sR = fabs(er.u) + er.c;
+    bool left = !(sL < sR);                       // fmax / std::max keep the first argument on a tie
+    double s = left ? sL : sR;
+    double t1[4], t2[4], WtL[4], WtR[4];
+    jac_x(el, S.gm1, L.Wn, t1); jac_y(el, S.gm1, L.Wt, t2);
+    for (int i = 0; i < 4; ++i) WtL[i] = -(t1[i] + t2[i]);
+    jac_x(er, S.gm1, R.Wn, t1); jac_y(er, S.gm1, R.Wt, t2);
+    for (int i = 0; i < 4; ++i) WtR[i] = -(t1[i] + t2[i]);
+    EulerBar elb = {0, 0, 0, 0, 0, 0}, erb = {0, 0, 0, 0, 0, 0};
+    double sb = 0.0, WtLb[4] = {0, 0, 0, 0}, WtRb[4] = {0, 0, 0, 0}, AXb[4];
+    for (int i = 0; i < 4; ++i) {
+        sb += -0.5 * Fb[i] * (R.W[i] - L.W[i]) - 0.5 * dFb[i] * (WtR[i] - WtL[i]);
+        Rb.W[i] += -0.5 * s * Fb[i];
+        Lb.W[i] += 0.5 * s * Fb[i];
+        WtRb[i] += -0.5 * s * dFb[i];
+        WtLb[i] += 0.5 * s * dFb[i];
+        AXb[i] = 0.5 * dFb[i];
+    }
+    // A(W_side) W_t,side
+    jac_x_vjp(el, S.gm1, WtL, AXb, elb, WtLb);
+    jac_x_vjp(er, S.gm1, WtR, AXb, erb, WtRb);
+    // W_t = -(A W_n + B W_t)
+    double nb[4];
+    for (int i = 0; i < 4; ++i) nb[i] = -WtLb[i];
+    jac_x_vjp(el, S.gm1, L.Wn, nb, elb, Lb.Wn);
+    jac_y_vjp(el, S.gm1, L.Wt, nb, elb, Lb.Wt);
+    for (int i = 0; i < 4; ++i) nb[i] = -WtRb[i];
+    jac_x_vjp(er, S.gm1, R.Wn, nb, erb, Rb.Wn);
+    jac_y_vjp(er, S.gm1, R.Wt, nb, erb, Rb.Wt);
+    // the two Euler fluxes, F = (m, m u + p, m v, u (E + p))
+    const GPState* sides[2] = {&L, &R};
+    EulerPt* es[2] = {&el, &er};
+    EulerBar* ebs[2] = {&elb, &erb};
+    GPStateBar* bs[2] = {&Lb, &Rb};
+    for (int k = 0; k < 2; ++k) {
+        const double* W = sides[k]->W;
+        const EulerPt& e = *es[k];
+        EulerBar& eb = *ebs[k];
+        double* Wb = bs[k]->W;
+        double g0 = 0.5 * Fb[0], g1 = 0.5 * Fb[1], g2 = 0.5 * Fb[2], g3 = 0.5 * Fb[3];
+        Wb[1] += g0 + g1 * e.u + g2 * e.v;
+        eb.u += g1 * W[1] + g3 * (W[3] + e.p);
+        eb.p += g1 + g3 * e.u;
+        eb.v += g2 * W[1];
+        Wb[3] += g3 * e.u;
+    }
+    // wave speed s = max(|u_l| + c_l, |u_r| + c_r)
+    if (left) { elb.u += sb * (el.u >= 0.0 ? 1.0 : -1.0); elb.c += sb; }
+    else { erb.u += sb * (er.u >= 0.0 ? 1.0 : -1.0); erb.c += sb; }
+    euler_pt_vjp(L.W, S, el, elb, Lb.W);
+    euler_pt_vjp(R.W, S, er, erb, Rb.W);
+}
+
+}  // namespace dfk

@@ -6,6 +6,7 @@
 #include <stdlib.h>
 #include <string.h>
 #include <new>
+#include <vector>
 
 #include "../../include/dfgks.h"
 #include "dfgks_internal.h"
@@ -36,6 +37,9 @@ struct dfgks {
     long long fail_step;
     int fail_i, fail_j;
     KernelTimer* timer;    // per-kernel-class event timing and launch counts
+    double* adj_lines;     // reverse sweep: face-line record adjoints
+    double* adj_gp;        // reverse sweep: Gauss-point record adjoints
+    double* adj_Wg;        // reverse sweep: ghosted cell adjoints
 };
 
 static dfgks_status cuda_status(cudaError_t e) {
@@ -92,7 +96,7 @@ static bool config_ok(const dfgks_config* c) {
 
 static void free_all(dfgks* h) {
     double* ptrs[] = {h->W[0], h->W[1], h->A[0], h->A[1], h->Ws, h->As, h->acc, h->B.lines, h->B.gp,
-                      h->B.flux[0], h->B.flux[1], h->dt_scratch, h->dts};
+                      h->B.flux[0], h->B.flux[1], h->dt_scratch, h->dts, h->adj_lines, h->adj_gp, h->adj_Wg};
     for (double* p : ptrs) if (p) cudaFree(p);
     if (h->st) cudaFree(h->st);
     if (h->flag) cudaFree(h->flag);
@@ -294,7 +298,7 @@ extern "C" dfgks_status dfgks_get_state(dfgks* h, double* W, double* alpha, doub
 }
 
 // one step of Algorithm 1 on buffers (in -> out); every kernel returns at once once st->halt is set
-static void enqueue_step(dfgks* h, int s, double dt, int flux, double t_end, int cur0) {
+static void enqueue_step(dfgks* h, int s, double dt, int flux, double t_end, int cur0, double* Wstar_store = nullptr) {
     const Mesh& m = h->mesh;
     const SchemeConsts& S = h->S;
     cudaStream_t st = h->stream;
@@ -314,6 +318,7 @@ static void enqueue_step(dfgks* h, int s, double dt, int flux, double t_end, int
         for (int d = 0; d < 2; ++d) launch_sweep(d, m, S, flux, false, in, ain, dtp, h->B, h->st, halt, st, T);
         a.Win = in; a.Wout = h->Ws; a.acc = h->acc;
         launch_update(UM_S2O4_1, m, S, a, h->B, dtp, h->st, halt, st, T);
+        if (Wstar_store) launch_ghosted_to_dense(m, h->Ws, 4, Wstar_store, st);
         launch_fill_ghosts(m, h->Ws, nullptr, halt, st, T);
         for (int d = 0; d < 2; ++d) launch_sweep(d, m, S, flux, false, h->Ws, ain, dtp, h->B, h->st, halt, st, T);
         a.Win = h->Ws; a.Wout = out; a.alpha_out = aout;
@@ -412,12 +417,137 @@ extern "C" dfgks_status dfgks_face_records(dfgks* h, const double* W, const doub
     return DFGKS_OK;
 }
 
+static dfgks_status ensure_adjoint_buffers(dfgks* h) {
+    if (h->adj_lines) return DFGKS_OK;
+    CK(dalloc(h, &h->adj_lines, (long long)LR_COUNT * h->B.line_stride));
+    CK(dalloc(h, &h->adj_gp, (long long)GP_COUNT * h->B.gp_stride));
+    CK(dalloc(h, &h->adj_Wg, 4 * h->mesh.plane));
+    return DFGKS_OK;
+}
+
+// reverse sweep of the stage operator at (W, alpha, dt); W_bar (dense, device) += J^T (L_bar, ...)
+static dfgks_status adjoint_stage(dfgks* h, const double* W, const double* alpha, double dt, int flux,
+                                  const double* L_bar, const double* dtL_bar, const double* dtLt_bar, double* W_bar) {
+    dfgks_status r = ensure_adjoint_buffers(h);
+    if (r) return r;
+    launch_dense_to_ghosted(h->mesh, W, 4, h->Ws, h->stream);
+    launch_dense_to_ghosted(h->mesh, alpha, 1, h->As, h->stream);
+    launch_fill_ghosts(h->mesh, h->Ws, h->As, nullptr, h->stream);
+    launch_set_scalar(h->dt_scratch, dt, h->stream);
+    CK(cudaMemsetAsync(h->adj_Wg, 0, sizeof(double) * 4 * h->mesh.plane, h->stream));
+    AdjointArgs a = {L_bar, dtL_bar, dtLt_bar};
+    for (int d = 0; d < 2; ++d) {
+        // the records of this direction, then its reverse sweep
+        launch_sweep(d, h->mesh, h->S, flux, false, h->Ws, h->As, h->dt_scratch, h->B, nullptr, nullptr, h->stream);
+        launch_adjoint_dir(d, h->mesh, h->S, flux, a, h->Ws, h->As, h->dt_scratch, h->B, h->adj_lines, h->adj_gp,
+                           h->adj_Wg, h->stream, h->timer->on ? h->timer : nullptr);
+    }
+    launch_adjoint_finish(h->mesh, h->adj_Wg, W_bar, h->stream);
+    CK_LAUNCH();
+    return DFGKS_OK;
+}
+
 extern "C" dfgks_status dfgks_adjoint_residual(dfgks* h, const double* W, const double* alpha, double dt, int flux,
                                                const double* L_bar, const double* dtL_bar, const double* dtLt_bar,
                                                double* W_bar) {
-    (void)W; (void)alpha; (void)dt; (void)flux; (void)L_bar; (void)dtL_bar; (void)dtLt_bar; (void)W_bar;
-    if (!h) return DFGKS_EINVAL;
-    return DFGKS_ENOTSUP;
+    if (!h || !W || !alpha || !W_bar || !(dt > 0.0) || (flux != 0 && flux != 1)) return DFGKS_EINVAL;
+    return adjoint_stage(h, W, alpha, dt, flux, L_bar, dtL_bar, dtLt_bar, W_bar);
+}
+
+extern "C" dfgks_status dfgks_adjoint_steps(dfgks* h, const double* W0, int n, const double* dts, int flux, int ckpt_every,
+                                            const double* WT_bar, double* W0_bar) {
+    if (!h || !W0 || !dts || !WT_bar || !W0_bar || n < 1 || ckpt_every < 1 || (flux != 0 && flux != 1))
+        return DFGKS_EINVAL;
+    if (h->cfg.time_scheme != DFGKS_TIME_S2O4) return DFGKS_ENOTSUP;
+    for (int s = 0; s < n; ++s) if (!(dts[s] > 0.0)) return DFGKS_EINVAL;
+    const Mesh& m = h->mesh;
+    const long long N = (long long)m.nx * m.ny, N4 = 4 * N;
+    const int k = ckpt_every, nseg = (n + k - 1) / k;
+    std::vector<double*> bufs;
+    auto get = [&](long long cnt) -> double* {
+        double* p = nullptr;
+        if (cudaMalloc((void**)&p, (size_t)cnt * sizeof(double)) != cudaSuccess) return nullptr;
+        bufs.push_back(p);
+        return p;
+    };
+    double* ckW = get(nseg * N4);
+    double* ckA = get(nseg * N);
+    double* segW = get(k * N4);
+    double* segA = get(k * N);
+    double* segWs = get(k * N4);
+    double* Wb = get(N4);
+    double* Wsb = get(N4);
+    double* bL = get(N4);
+    double* bdL = get(N4);
+    double* bdLt = get(N4);
+    double* WTs = get(N4);
+    double* ATs = get(N);
+    dfgks_status r = DFGKS_OK;
+    for (double* p : bufs) if (!p) r = DFGKS_ENOMEM;
+    if (bufs.size() != 12) r = DFGKS_ENOMEM;
+    auto cleanup = [&]() { cudaStreamSynchronize(h->stream); for (double* p : bufs) cudaFree(p); };
+    if (r) { cleanup(); return r; }
+    // forward pass from W0 with the recorded steps, keeping a checkpoint every k steps
+    r = load_state(h, W0, nullptr, 0.0, 0, 1);
+    if (r) { cleanup(); return r; }
+    CK(cudaMemsetAsync(&h->st->halt, 0, sizeof(int), h->stream));
+    auto one_step = [&](double dt, double* Wstar) {
+        enqueue_step(h, 0, dt, flux, 0.0, h->cur, Wstar);
+        h->cur ^= 1;
+    };
+    for (int s = 0; s < n; ++s) {
+        if (s % k == 0) {
+            launch_ghosted_to_dense(m, h->W[h->cur], 4, ckW + (s / k) * N4, h->stream);
+            launch_ghosted_to_dense(m, h->A[h->cur], 1, ckA + (s / k) * N, h->stream);
+        }
+        one_step(dts[s], nullptr);
+    }
+    CK(cudaMemcpyAsync(h->st_host, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (h->st_host->err) { cleanup(); return DFGKS_ENONPOS; }
+    const DevState stT = *h->st_host;
+    launch_ghosted_to_dense(m, h->W[h->cur], 4, WTs, h->stream);
+    launch_ghosted_to_dense(m, h->A[h->cur], 1, ATs, h->stream);
+    CK(cudaMemcpyAsync(Wb, WT_bar, (size_t)N4 * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    for (int seg = nseg - 1; seg >= 0 && r == DFGKS_OK; --seg) {
+        const int s0 = seg * k, s1 = (s0 + k < n) ? s0 + k : n;
+        // recompute the segment from its checkpoint, keeping W^s, alpha^s and W* of every step
+        launch_dense_to_ghosted(m, ckW + seg * N4, 4, h->W[h->cur], h->stream);
+        launch_dense_to_ghosted(m, ckA + seg * N, 1, h->A[h->cur], h->stream);
+        for (int s = s0; s < s1; ++s) {
+            launch_ghosted_to_dense(m, h->W[h->cur], 4, segW + (s - s0) * N4, h->stream);
+            launch_ghosted_to_dense(m, h->A[h->cur], 1, segA + (s - s0) * N, h->stream);
+            one_step(dts[s], segWs + (s - s0) * N4);
+        }
+        // reverse through the segment: Eq. 24 with the time limiter,
+        //   W* = W + dt/2 L + dt^2/8 dL,  W' = W + dt L + dt^2/2 dL - dt^2/3 dLt + dt^2/3 dLt(W*)
+        for (int s = s1 - 1; s >= s0 && r == DFGKS_OK; --s) {
+            const double dt = dts[s], dt2 = dt * dt;
+            const double* Wn = segW + (s - s0) * N4;
+            const double* An = segA + (s - s0) * N;
+            const double* Wst = segWs + (s - s0) * N4;
+            CK(cudaMemsetAsync(Wsb, 0, (size_t)N4 * sizeof(double), h->stream));
+            launch_axpby(N4, dt2 / 3.0, Wb, 0.0, bdLt, h->stream);
+            r = adjoint_stage(h, Wst, An, dt, flux, nullptr, nullptr, bdLt, Wsb);
+            if (r) break;
+            launch_axpby(N4, dt, Wb, 0.0, bL, h->stream);
+            launch_axpby(N4, 0.5 * dt, Wsb, 1.0, bL, h->stream);
+            launch_axpby(N4, 0.5 * dt2, Wb, 0.0, bdL, h->stream);
+            launch_axpby(N4, 0.125 * dt2, Wsb, 1.0, bdL, h->stream);
+            launch_axpby(N4, -dt2 / 3.0, Wb, 0.0, bdLt, h->stream);
+            launch_axpby(N4, 1.0, Wsb, 1.0, Wb, h->stream);
+            r = adjoint_stage(h, Wn, An, dt, flux, bL, bdL, bdLt, Wb);
+        }
+    }
+    if (r == DFGKS_OK) CK(cudaMemcpyAsync(W0_bar, Wb, (size_t)N4 * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    // leave the handle at the forward solution W^n (state, alpha, time and step count)
+    launch_dense_to_ghosted(m, WTs, 4, h->W[h->cur], h->stream);
+    launch_dense_to_ghosted(m, ATs, 1, h->A[h->cur], h->stream);
+    *h->st_host = stT;
+    CK(cudaMemcpyAsync(h->st, h->st_host, sizeof(DevState), cudaMemcpyHostToDevice, h->stream));
+    cleanup();
+    CK_LAUNCH();
+    return r;
 }
 
 extern "C" dfgks_status dfgks_get_counters(dfgks* h, dfgks_counters* out) {

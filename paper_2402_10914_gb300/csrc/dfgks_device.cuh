@@ -15,6 +15,9 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+// every arithmetic routine also compiles for the host, so its derivatives can be checked there
+#define DFK_HD __host__ __device__ __forceinline__
+
 namespace dfk {
 
 constexpr int G = 3;                       // ghost layers: the normal stencil spans i-3 .. i+2
@@ -31,18 +34,18 @@ struct SchemeConsts {
 // ------------------------------------------------------------------------------------------
 // Euler state helpers
 // ------------------------------------------------------------------------------------------
-__device__ __forceinline__ double pressure_of(const double W[4], double gm1) {
+DFK_HD double pressure_of(const double W[4], double gm1) {
     return gm1 * (W[3] - 0.5 * (W[1] * W[1] + W[2] * W[2]) / W[0]);
 }
 
 // rotate a global-frame state into the local frame of a y-face (theta = pi/2): (rho, rhoV, -rhoU, rhoE)
 template <int DIR>
-__device__ __forceinline__ void to_local(double W[4]) {
+DFK_HD void to_local(double W[4]) {
     if (DIR == 1) { double m = W[1]; W[1] = W[2]; W[2] = -m; }
 }
 // local-frame flux back to the global frame, F = T^{-1} F~
 template <int DIR>
-__device__ __forceinline__ void to_global(double F[4]) {
+DFK_HD void to_global(double F[4]) {
     if (DIR == 1) { double a = F[1]; F[1] = -F[2]; F[2] = a; }
 }
 
@@ -51,7 +54,7 @@ __device__ __forceinline__ void to_global(double F[4]) {
 // ------------------------------------------------------------------------------------------
 struct CharBasis { double u, v, c, ic, H, b1, b2, q2; };
 
-__device__ __forceinline__ CharBasis make_basis(const double Wl[4], const double Wr[4], const SchemeConsts& S) {
+DFK_HD CharBasis make_basis(const double Wl[4], const double Wr[4], const SchemeConsts& S) {
     CharBasis B;
     double r = 0.5 * (Wl[0] + Wr[0]), m = 0.5 * (Wl[1] + Wr[1]);
     double n = 0.5 * (Wl[2] + Wr[2]), E = 0.5 * (Wl[3] + Wr[3]);
@@ -69,7 +72,7 @@ __device__ __forceinline__ CharBasis make_basis(const double Wl[4], const double
 }
 
 // Q = L W; components ordered by eigenvalue u-c, u (entropy), u (shear), u+c
-__device__ __forceinline__ void project(const CharBasis& B, const double W[4], double Q[4]) {
+DFK_HD void project(const CharBasis& B, const double W[4], double Q[4]) {
     double t = B.b1 * (B.u * W[1] + B.v * W[2] - W[3]);
     double k = B.b2 * W[0] - t;
     double m = (B.u * W[0] - W[1]) * B.ic;
@@ -80,7 +83,7 @@ __device__ __forceinline__ void project(const CharBasis& B, const double W[4], d
 }
 
 // W = R Q
-__device__ __forceinline__ void back_project(const CharBasis& B, const double Q[4], double W[4]) {
+DFK_HD void back_project(const CharBasis& B, const double Q[4], double W[4]) {
     double s = Q[0] + Q[3], d = Q[3] - Q[0];
     W[0] = s + Q[1];
     W[1] = B.u * W[0] + B.c * d;
@@ -100,7 +103,7 @@ struct AO {
     double rmax, rmin;      // tau_Z/(beta_min+eps), tau_Z/(beta_max+eps): the time limiter's ratios
 };
 
-__device__ __forceinline__ AO weno_ao(const double q[5], const SchemeConsts& S) {
+DFK_HD AO weno_ao(const double q[5], const SchemeConsts& S) {
     const double qm2 = q[0], qm1 = q[1], q0 = q[2], q1 = q[3], q2 = q[4];
     // quadratic sub-stencils {i-2,i-1,i}, {i-1,i,i+1}, {i,i+1,i+2}
     double a1_0 = 0.5 * qm2 - 2.0 * qm1 + 1.5 * q0;
@@ -150,19 +153,19 @@ __device__ __forceinline__ AO weno_ao(const double q[5], const SchemeConsts& S) 
 }
 
 // time-limiter ingredient 2 at2 / (at1 + at2) of one reconstruction (Sect. 2.2)
-__device__ __forceinline__ double limiter_alpha(const AO& o) {
+DFK_HD double limiter_alpha(const AO& o) {
     double a1 = 1.0 + o.rmax * o.rmax, a2 = 1.0 + o.rmin * o.rmin;
     return 2.0 * a2 / (a1 + a2);
 }
 
 // value and d/dxi of the AO polynomial at the right cell edge xi = +1/2
-__device__ __forceinline__ void ao_at_right_edge(const AO& o, double q0, double& val, double& slope) {
+DFK_HD void ao_at_right_edge(const AO& o, double q0, double& val, double& slope) {
     val = q0 + 0.5 * o.A1 + (1.0 / 6.0) * o.A2 + 0.125 * o.c3a3 + 0.05 * o.c3a4;
     slope = o.A1 + o.A2 + 0.75 * o.c3a3 + 0.5 * o.c3a4;
 }
 
 // zero-mean DF quadratic of Sect. 3.3, p_DF = Q_0 + alpha (p1 - Q_0), at xi = +1/2
-__device__ __forceinline__ void df_at_right_edge(const double q[5], double alpha, double& val, double& slope) {
+DFK_HD void df_at_right_edge(const double q[5], double alpha, double& val, double& slope) {
     double a1 = 0.5 * (q[3] - q[1]);
     double a2 = 0.5 * (q[1] - 2.0 * q[2] + q[3]);
     val = q[2] + alpha * (0.5 * a1 + (1.0 / 6.0) * a2);
@@ -170,7 +173,7 @@ __device__ __forceinline__ void df_at_right_edge(const double q[5], double alpha
 }
 
 // values and d/deta at the two Gauss points eta = -g (m=1), +g (m=2), g = sqrt(3)/6
-__device__ __forceinline__ void ao_at_gauss(const AO& o, double q0, double val[2], double slope[2]) {
+DFK_HD void ao_at_gauss(const AO& o, double q0, double val[2], double slope[2]) {
     const double g = kGaussEta;
     double E = q0 - (1.0 / 180.0) * o.c3a4;                 // even part: xi^2 = 1/12, xi^4 = 1/144
     double O = g * (o.A1 + (1.0 / 12.0) * o.c3a3);          // odd part
@@ -180,7 +183,7 @@ __device__ __forceinline__ void ao_at_gauss(const AO& o, double q0, double val[2
     slope[0] = Es - Os; slope[1] = Es + Os;
 }
 
-__device__ __forceinline__ void df_at_gauss(const double q[5], double alpha, double val[2], double slope[2]) {
+DFK_HD void df_at_gauss(const double q[5], double alpha, double val[2], double slope[2]) {
     const double g = kGaussEta;
     double a1 = 0.5 * (q[3] - q[1]);
     double a2 = 0.5 * (q[1] - 2.0 * q[2] + q[3]);
@@ -204,7 +207,7 @@ struct Mom {
 // qK = U^2 + V^2 + (K+2)/(2 lambda); the slope solves of a state share them.
 struct Maxw { double rho, ir, U, V, p, il2, tl, f4, qK; };
 
-__device__ __forceinline__ Maxw maxw_of(const double W[4], const SchemeConsts& S) {
+DFK_HD Maxw maxw_of(const double W[4], const SchemeConsts& S) {
     Maxw s;
     s.rho = W[0];
     s.ir = 1.0 / W[0];
@@ -220,7 +223,7 @@ __device__ __forceinline__ Maxw maxw_of(const double W[4], const SchemeConsts& S
 
 // half: 0 full, +1 u>0, -1 u<0
 template <int HALF>
-__device__ __forceinline__ void fill_moments(const Maxw& s, double K, Mom& m) {
+DFK_HD void fill_moments(const Maxw& s, double K, Mom& m) {
     if (HALF == 0) {
         m.mu[0] = 1.0;
         m.mu[1] = s.U;
@@ -244,11 +247,11 @@ __device__ __forceinline__ void fill_moments(const Maxw& s, double K, Mom& m) {
 }
 
 template <int k, int l, int c>
-__device__ __forceinline__ double M(const Mom& m) { return m.mu[k] * m.mv[l] * m.mx[c]; }
+DFK_HD double M(const Mom& m) { return m.mu[k] * m.mv[l] * m.mx[c]; }
 
 // <u^k v^l xi^{2c} psi>, psi = (1, u, v, (u^2+v^2+xi^2)/2)
 template <int k, int l, int c>
-__device__ __forceinline__ void psi_mom(const Mom& m, double out[4]) {
+DFK_HD void psi_mom(const Mom& m, double out[4]) {
     out[0] = M<k, l, c>(m);
     out[1] = M<k + 1, l, c>(m);
     out[2] = M<k, l + 1, c>(m);
@@ -257,7 +260,7 @@ __device__ __forceinline__ void psi_mom(const Mom& m, double out[4]) {
 
 // <u^k v^l a psi> with a = a0 + a1 u + a2 v + a3 (u^2+v^2+xi^2)/2
 template <int k, int l>
-__device__ __forceinline__ void a_mom(const Mom& m, const double a[4], double out[4]) {
+DFK_HD void a_mom(const Mom& m, const double a[4], double out[4]) {
     double t0[4], t1[4], t2[4], t3[4], t4[4], t5[4];
     psi_mom<k, l, 0>(m, t0);
     psi_mom<k + 1, l, 0>(m, t1);
@@ -271,7 +274,7 @@ __device__ __forceinline__ void a_mom(const Mom& m, const double a[4], double ou
 }
 
 // closed-form solution of <a psi> = b for a Maxwellian (U, V, lambda)
-__device__ __forceinline__ void slope_solve(const Maxw& s, const double b[4], double a[4]) {
+DFK_HD void slope_solve(const Maxw& s, const double b[4], double a[4]) {
     double R2 = b[1] - s.U * b[0], R3 = b[2] - s.V * b[0], R4 = 2.0 * b[3] - s.qK * b[0];
     a[3] = s.f4 * (R4 - 2.0 * s.U * R2 - 2.0 * s.V * R3);
     a[2] = s.tl * R3 - s.V * a[3];
@@ -281,7 +284,7 @@ __device__ __forceinline__ void slope_solve(const Maxw& s, const double b[4], do
 
 struct GPState { double W[4], Wn[4], Wt[4]; };   // one side of one Gauss point, local frame
 
-__device__ __forceinline__ void gks_flux(const GPState& L, const GPState& R, double dt, const SchemeConsts& S,
+DFK_HD void gks_flux(const GPState& L, const GPState& R, double dt, const SchemeConsts& S,
                                          double F[4], double dF[4]) {
     const double K = S.K;
     Maxw sl = maxw_of(L.W, S), sr = maxw_of(R.W, S);
@@ -398,7 +401,7 @@ __device__ __forceinline__ void gks_flux(const GPState& L, const GPState& R, dou
 // ------------------------------------------------------------------------------------------
 struct EulerPt { double u, v, p, c, H, q; };
 
-__device__ __forceinline__ EulerPt euler_pt(const double W[4], const SchemeConsts& S) {
+DFK_HD EulerPt euler_pt(const double W[4], const SchemeConsts& S) {
     EulerPt e;
     double ir = 1.0 / W[0];
     e.u = W[1] * ir;
@@ -411,14 +414,14 @@ __device__ __forceinline__ EulerPt euler_pt(const double W[4], const SchemeConst
 }
 
 // A X (x-flux Jacobian) and B X (y-flux Jacobian) at a state
-__device__ __forceinline__ void jac_x(const EulerPt& e, double gm1, const double X[4], double Y[4]) {
+DFK_HD void jac_x(const EulerPt& e, double gm1, const double X[4], double Y[4]) {
     double dp = gm1 * (X[3] - e.u * X[1] - e.v * X[2] + e.q * X[0]);
     Y[0] = X[1];
     Y[1] = 2.0 * e.u * X[1] - e.u * e.u * X[0] + dp;
     Y[2] = e.v * X[1] + e.u * X[2] - e.u * e.v * X[0];
     Y[3] = e.u * (X[3] + dp) + e.H * (X[1] - e.u * X[0]);
 }
-__device__ __forceinline__ void jac_y(const EulerPt& e, double gm1, const double X[4], double Y[4]) {
+DFK_HD void jac_y(const EulerPt& e, double gm1, const double X[4], double Y[4]) {
     double dp = gm1 * (X[3] - e.u * X[1] - e.v * X[2] + e.q * X[0]);
     Y[0] = X[2];
     Y[1] = e.v * X[1] + e.u * X[2] - e.u * e.v * X[0];
@@ -426,7 +429,7 @@ __device__ __forceinline__ void jac_y(const EulerPt& e, double gm1, const double
     Y[3] = e.v * (X[3] + dp) + e.H * (X[2] - e.v * X[0]);
 }
 
-__device__ __forceinline__ void lf_flux(const GPState& L, const GPState& R, const SchemeConsts& S,
+DFK_HD void lf_flux(const GPState& L, const GPState& R, const SchemeConsts& S,
                                         double F[4], double dF[4]) {
     EulerPt el = euler_pt(L.W, S), er = euler_pt(R.W, S);
     double FL[4] = {L.W[1], L.W[1] * el.u + el.p, L.W[1] * el.v, el.u * (L.W[3] + el.p)};
@@ -449,7 +452,7 @@ __device__ __forceinline__ void lf_flux(const GPState& L, const GPState& R, cons
 }
 
 // DF factor of one Gauss point (Sect. 3.2), local-frame states
-__device__ __forceinline__ double df_alpha(const double WL[4], const double WR[4], const SchemeConsts& S) {
+DFK_HD double df_alpha(const double WL[4], const double WR[4], const SchemeConsts& S) {
     EulerPt l = euler_pt(WL, S), r = euler_pt(WR, S);
     double jp = fabs(l.p - r.p);
     double icl = 1.0 / l.c, icr = 1.0 / r.c;
@@ -458,7 +461,7 @@ __device__ __forceinline__ double df_alpha(const double WL[4], const double WR[4
     return 1.0 / (1.0 + D * D);
 }
 
-__device__ __forceinline__ bool physical_state(const double W[4], double gm1) {
+DFK_HD bool physical_state(const double W[4], double gm1) {
     if (!(W[0] > 0.0)) return false;
     double p = gm1 * (W[3] - 0.5 * (W[1] * W[1] + W[2] * W[2]) / W[0]);
     return p > 0.0;

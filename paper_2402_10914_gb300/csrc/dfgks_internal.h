@@ -109,6 +109,8 @@ struct UpdateArgs {
     int alpha_dense;        // 1: alpha_out is dense [ny][nx]
 };
 
+struct AdjointArgs { const double* Lb; const double* dtLb; const double* dtLtb; };   // dense, may be null
+
 // ---- launchers (dfgks_kernels.cu) -----------------------------------------------------------
 void launch_fill_ghosts(const Mesh& m, double* W, double* alpha, const int* halt, cudaStream_t s, KernelTimer* T = nullptr);
 void launch_cfl_min(const Mesh& m, const double* W, double gamma, DevState* st, cudaStream_t s, KernelTimer* T = nullptr);
@@ -126,5 +128,12 @@ void launch_fill_value(double* p, long long n, double v, cudaStream_t s);
 void launch_check_state(const Mesh& m, const double* W, double gm1, int* bad, cudaStream_t s);
 void launch_set_scalar(double* p, double v, cudaStream_t s);
 void launch_pack_faces(int dir, const Mesh& m, const SweepBuffers& B, double* out, cudaStream_t s);
+
+// ---- reverse sweep (dfgks_adjoint.cu) -------------------------------------------------------
+void launch_adjoint_dir(int dir, const Mesh& m, const SchemeConsts& S, int flux, const AdjointArgs& a,
+                        const double* W, const double* alpha, const double* dtp, const SweepBuffers& B,
+                        double* lb, double* gbuf, double* Wb, cudaStream_t s, KernelTimer* T = nullptr);
+void launch_adjoint_finish(const Mesh& m, double* Wbg, double* Wb_dense, cudaStream_t s);
+void launch_axpby(long long n, double a, const double* x, double b, double* y, cudaStream_t s);
 
 }  // namespace dfk

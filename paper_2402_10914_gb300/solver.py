@@ -280,3 +280,53 @@ class BatchSolver:
             with open(self._cache, "w") as f:
                 json.dump(data, f)
         return self.shapes, best.value
+
+
+def _dev(t):
+    return t if (isinstance(t, torch.Tensor) and t.is_cuda) else torch.as_tensor(
+        np.ascontiguousarray(t), dtype=torch.float64, device="cuda")
+
+
+def adjoint_residual(sol: "Solver", W, alpha, dt, L_bar=None, dtL_bar=None, dtLt_bar=None, flux=None,
+                     W_bar=None) -> torch.Tensor:
+    """W_bar (+)= J^T (L_bar, dtL_bar, dtLt_bar) of the stage operator (dfgks_adjoint_residual)."""
+    flux = sol.settings.flux if flux is None else flux
+    W, alpha = _dev(W).contiguous(), _dev(alpha).contiguous()
+    bars = [None if b is None else _dev(b).contiguous() for b in (L_bar, dtL_bar, dtLt_bar)]
+    out = torch.zeros_like(W) if W_bar is None else W_bar
+    _lib.check(_lib.lib().dfgks_adjoint_residual(sol._h, _ptr(W), _ptr(alpha), float(dt), int(flux),
+                                                 *[_ptr(b) for b in bars], _ptr(out)), "dfgks_adjoint_residual")
+    return out
+
+
+def adjoint_steps(sol: "Solver", W0, dts, WT_bar, ckpt_every: int = 10, flux=None) -> torch.Tensor:
+    """(dW^n/dW0)^T WT_bar through the recorded S2O4 steps (dfgks_adjoint_steps)."""
+    flux = sol.settings.flux if flux is None else flux
+    W0 = _dev(W0).contiguous()
+    WTb = _dev(WT_bar).contiguous()
+    dts = np.ascontiguousarray(np.asarray(dts, dtype=np.float64))
+    out = torch.zeros_like(W0)
+    _lib.check(_lib.lib().dfgks_adjoint_steps(sol._h, _ptr(W0), int(dts.size), dts.ctypes.data_as(C.POINTER(C.c_double)),
+                                              int(flux), int(ckpt_every), _ptr(WTb), _ptr(out)), "dfgks_adjoint_steps")
+    return out
+
+
+class GKSRun(torch.autograd.Function):
+    """W^n = n S2O4 steps of the CUDA solver from W0 (CFL step sizes, recorded); the backward pass is
+    the hand-written adjoint with checkpointed recompute (dfgks_adjoint_steps).  alpha^0 comes from
+    W0 and the alpha sequence and branch decisions of the forward trajectory are held fixed."""
+
+    @staticmethod
+    def forward(ctx, W0, sol, nsteps, ckpt_every=10):
+        W0 = W0.detach().contiguous()
+        sol.set_ic(W0)
+        done, dts = sol.step(int(nsteps), record_dts=True)
+        W, _, _, _ = sol.get_state(device=True)
+        ctx.save_for_backward(W0)
+        ctx.sol, ctx.dts, ctx.k = sol, dts, int(ckpt_every)
+        return W
+
+    @staticmethod
+    def backward(ctx, WT_bar):
+        (W0,) = ctx.saved_tensors
+        return adjoint_steps(ctx.sol, W0, ctx.dts, WT_bar.contiguous(), ctx.k), None, None, None
