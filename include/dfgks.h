@@ -85,7 +85,8 @@ DFGKS_API const char* dfgks_status_string(int status);
 DFGKS_API dfgks_status dfgks_config_default(dfgks_config* cfg, int nx, int ny);
 
 /* Create a solver for cfg on the current CUDA device.  stream: a cudaStream_t to order all work
- * on, or NULL to create a private non-blocking stream.  Allocates every device buffer the step
+ * on (cudaStreamLegacy for the legacy default stream), or NULL to create a private non-blocking
+ * stream, which is not ordered with work the caller puts on other streams.  Allocates every device buffer the step
  * needs (about 140 doubles per cell for the default path).  On success *out owns them. */
 DFGKS_API dfgks_status dfgks_create(const dfgks_config* cfg, void* stream, dfgks** out);
 

@@ -17,19 +17,19 @@
 
 namespace dfk {
 
-__device__ __forceinline__ void aadd(double* p, double v) { if (v != 0.0) atomicAdd(p, v); }
-
-template <int DIR>
-__device__ __forceinline__ void to_global_vec(double W[4]) { to_global<DIR>(W); }
+DFK_HD void aadd(double* p, double v) {
+#ifdef __CUDA_ARCH__
+    if (v != 0.0) atomicAdd(p, v);
+#else
+    *p += v;
+#endif
+}
 
 template <int DIR, int FLUX>
-__global__ void __launch_bounds__(128) ka_flux(Mesh m, SchemeConsts S, AdjointArgs a, const double* __restrict__ lines,
-                                               long long ls, const double* __restrict__ gp, long long gs,
-                                               const double* __restrict__ fr, long long fs, const double* dtp,
-                                               double* __restrict__ lb, double* __restrict__ gb) {
+DFK_HD void ka_flux_body(const Mesh& m, const SchemeConsts& S, const AdjointArgs& a, const double* __restrict__ gp,
+                         long long gs, const double* __restrict__ fr, long long fs, double dt, double* __restrict__ lb,
+                         long long ls, double* __restrict__ gb, int ax, int ay, int mm) {
     Geo<DIR> g(m);
-    int ax = blockIdx.x * blockDim.x + threadIdx.x, ay = blockIdx.y * blockDim.y + threadIdx.y;
-    const int mm = blockIdx.z;
     int f = DIR == 0 ? ax : ay;
     int t = DIR == 0 ? ay : ax;
     if (f > g.nn || t >= g.nt) return;
@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(128) ka_flux(Mesh m, SchemeConsts S, AdjointAr
     }
     GPStateBar Lbar, Rbar;
     for (int k = 0; k < 4; ++k) { Lbar.W[k] = Lbar.Wn[k] = Lbar.Wt[k] = Rbar.W[k] = Rbar.Wn[k] = Rbar.Wt[k] = 0.0; }
-    if (FLUX == 0) gks_flux_vjp(L, R, *dtp, S, Fb, dFb, Lbar, Rbar);
+    if (FLUX == 0) gks_flux_vjp(L, R, dt, S, Fb, dFb, Lbar, Rbar);
     else lf_flux_vjp(L, R, S, Fb, dFb, Lbar, Rbar);
     for (int k = 0; k < 4; ++k) {
         gb[(mm * 12 + k) * gs + eL] = Lbar.W[k];
@@ -90,13 +90,10 @@ __global__ void __launch_bounds__(128) ka_flux(Mesh m, SchemeConsts S, AdjointAr
 }
 
 template <int DIR>
-__global__ void __launch_bounds__(128) ka_faces(Mesh m, SchemeConsts S, const double* __restrict__ W,
-                                                const double* __restrict__ alpha, const double* __restrict__ lines,
-                                                long long ls, const double* __restrict__ gb, long long gs,
-                                                double* __restrict__ lb, double* __restrict__ Wb) {
+DFK_HD void ka_faces_body(const Mesh& m, const SchemeConsts& S, const double* __restrict__ alpha,
+                          const double* __restrict__ lines, long long ls, const double* __restrict__ gb, long long gs,
+                          double* __restrict__ lb, double* __restrict__ Wb, int ax, int ay, int side) {
     Geo<DIR> g(m);
-    int ax = blockIdx.x * blockDim.x + threadIdx.x, ay = blockIdx.y * blockDim.y + threadIdx.y;
-    const int side = blockIdx.z;
     int f = DIR == 0 ? ax : ay;
     int t = DIR == 0 ? ay : ax;
     if (f > g.nn || t >= g.nt) return;
@@ -183,11 +180,10 @@ __global__ void __launch_bounds__(128) ka_faces(Mesh m, SchemeConsts S, const do
 }
 
 template <int DIR>
-__global__ void __launch_bounds__(128) ka_lines(Mesh m, SchemeConsts S, const double* __restrict__ W,
-                                                const double* __restrict__ alpha, const double* __restrict__ lb,
-                                                long long ls, double* __restrict__ Wb) {
+DFK_HD void ka_lines_body(const Mesh& m, const SchemeConsts& S, const double* __restrict__ W,
+                          const double* __restrict__ alpha, const double* __restrict__ lb, long long ls,
+                          double* __restrict__ Wb, int ax, int ay) {
     Geo<DIR> g(m);
-    int ax = blockIdx.x * blockDim.x + threadIdx.x, ay = blockIdx.y * blockDim.y + threadIdx.y;
     int f = DIR == 0 ? ax : ay;
     int tt = DIR == 0 ? ay : ax;
     if (f > g.nn || tt >= g.nt + 4) return;
@@ -295,8 +291,7 @@ __global__ void __launch_bounds__(128) ka_lines(Mesh m, SchemeConsts S, const do
 }
 
 // Reverse of the ghost fill: the y pass (all columns) first, then the x pass (interior rows).
-__global__ void ka_fold_y(Mesh m, double* Wb) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x - G;
+DFK_HD void ka_fold_y_body(const Mesh& m, double* Wb, int i) {
     if (i >= m.nx + G) return;
     for (int gr = 2 * G - 1; gr >= 0; --gr) {
         int j = gr < G ? gr - G : m.ny + gr - G;
@@ -311,8 +306,7 @@ __global__ void ka_fold_y(Mesh m, double* Wb) {
     }
 }
 
-__global__ void ka_fold_x(Mesh m, double* Wb) {
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
+DFK_HD void ka_fold_x_body(const Mesh& m, double* Wb, int j) {
     if (j >= m.ny) return;
     for (int gc = 2 * G - 1; gc >= 0; --gc) {
         int i = gc < G ? gc - G : m.nx + gc - G;
@@ -327,11 +321,43 @@ __global__ void ka_fold_x(Mesh m, double* Wb) {
     }
 }
 
-__global__ void ka_accumulate_dense(Mesh m, const double* __restrict__ Wbg, double* __restrict__ out) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+DFK_HD void ka_accumulate_body(const Mesh& m, const double* __restrict__ Wbg, double* __restrict__ out, int i, int j) {
     if (i >= m.nx || j >= m.ny) return;
     const long long dp = (long long)m.nx * m.ny;
     for (int k = 0; k < 4; ++k) out[k * dp + (long long)j * m.nx + i] += Wbg[k * m.plane + gid(m, i, j)];
+}
+
+// ---- kernels: one thread per body invocation ----
+template <int DIR, int FLUX>
+__global__ void __launch_bounds__(128) ka_flux(Mesh m, SchemeConsts S, AdjointArgs a, const double* __restrict__ gp,
+                                               long long gs, const double* __restrict__ fr, long long fs,
+                                               const double* dtp, double* __restrict__ lb, long long ls,
+                                               double* __restrict__ gb) {
+    ka_flux_body<DIR, FLUX>(m, S, a, gp, gs, fr, fs, *dtp, lb, ls, gb, blockIdx.x * blockDim.x + threadIdx.x,
+                            blockIdx.y * blockDim.y + threadIdx.y, blockIdx.z);
+}
+
+template <int DIR>
+__global__ void __launch_bounds__(128) ka_faces(Mesh m, SchemeConsts S, const double* __restrict__ alpha,
+                                                const double* __restrict__ lines, long long ls,
+                                                const double* __restrict__ gb, long long gs, double* __restrict__ lb,
+                                                double* __restrict__ Wb) {
+    ka_faces_body<DIR>(m, S, alpha, lines, ls, gb, gs, lb, Wb, blockIdx.x * blockDim.x + threadIdx.x,
+                       blockIdx.y * blockDim.y + threadIdx.y, blockIdx.z);
+}
+
+template <int DIR>
+__global__ void __launch_bounds__(128) ka_lines(Mesh m, SchemeConsts S, const double* __restrict__ W,
+                                                const double* __restrict__ alpha, const double* __restrict__ lb,
+                                                long long ls, double* __restrict__ Wb) {
+    ka_lines_body<DIR>(m, S, W, alpha, lb, ls, Wb, blockIdx.x * blockDim.x + threadIdx.x,
+                       blockIdx.y * blockDim.y + threadIdx.y);
+}
+
+__global__ void ka_fold_y(Mesh m, double* Wb) { ka_fold_y_body(m, Wb, blockIdx.x * blockDim.x + threadIdx.x - G); }
+__global__ void ka_fold_x(Mesh m, double* Wb) { ka_fold_x_body(m, Wb, blockIdx.x * blockDim.x + threadIdx.x); }
+__global__ void ka_accumulate_dense(Mesh m, const double* __restrict__ Wbg, double* __restrict__ out) {
+    ka_accumulate_body(m, Wbg, out, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y);
 }
 
 template <int DIR>
@@ -347,13 +373,13 @@ static void adjoint_dir(const Mesh& m, const SchemeConsts& S, int flux, const Ad
     cudaMemsetAsync(lb, 0, sizeof(double) * LR_COUNT * B.line_stride, s);
     if (T) T->begin(KK_FLUX);
     if (flux == 0)
-        ka_flux<DIR, 0><<<gf, blk, 0, s>>>(m, S, a, B.lines, B.line_stride, B.gp, B.gp_stride, B.flux[DIR],
-                                           B.flux_stride[DIR], dtp, lb, gbuf);
+        ka_flux<DIR, 0><<<gf, blk, 0, s>>>(m, S, a, B.gp, B.gp_stride, B.flux[DIR], B.flux_stride[DIR], dtp, lb,
+                                           B.line_stride, gbuf);
     else
-        ka_flux<DIR, 1><<<gf, blk, 0, s>>>(m, S, a, B.lines, B.line_stride, B.gp, B.gp_stride, B.flux[DIR],
-                                           B.flux_stride[DIR], dtp, lb, gbuf);
+        ka_flux<DIR, 1><<<gf, blk, 0, s>>>(m, S, a, B.gp, B.gp_stride, B.flux[DIR], B.flux_stride[DIR], dtp, lb,
+                                           B.line_stride, gbuf);
     if (T) { T->end(KK_FLUX, 1); T->begin(KK_FACES); }
-    ka_faces<DIR><<<gf, blk, 0, s>>>(m, S, W, alpha, B.lines, B.line_stride, gbuf, B.gp_stride, lb, Wb);
+    ka_faces<DIR><<<gf, blk, 0, s>>>(m, S, alpha, B.lines, B.line_stride, gbuf, B.gp_stride, lb, Wb);
     if (T) { T->end(KK_FACES, 1); T->begin(KK_LINES); }
     ka_lines<DIR><<<gl, blk, 0, s>>>(m, S, W, alpha, lb, B.line_stride, Wb);
     if (T) T->end(KK_LINES, 1);

@@ -1,13 +1,14 @@
 // dfgks_bodies.cuh -- per-thread bodies of the step kernels (one face line, face side, Gauss point,
 // cell or ghost cell), shared by the single-problem kernels (dfgks_kernels.cu) and the batched
-// kernels (dfgks_batch.cu), so both run exactly the same arithmetic.
+// kernels (dfgks_batch.cu), so both run exactly the same arithmetic.  The bodies are also
+// host-callable, so a test can run the GPU path's per-thread arithmetic on the CPU.
 #pragma once
 #include <float.h>
 #include "dfgks_internal.h"
 
 namespace dfk {
 
-__device__ __forceinline__ int ghost_src(int k, int n, int lo, int hi, bool& mir) {
+DFK_HD int ghost_src(int k, int n, int lo, int hi, bool& mir) {
     mir = false;
     if (k < 0) {
         if (lo == 0) return k + n;
@@ -26,25 +27,25 @@ template <int DIR>
 struct Geo {
     int nn, nt;                  // cells along normal / tangential
     double dn, dtan;             // cell sizes along normal / tangential
-    __device__ __forceinline__ Geo(const Mesh& m) {
+    DFK_HD Geo(const Mesh& m) {
         nn = DIR == 0 ? m.nx : m.ny;
         nt = DIR == 0 ? m.ny : m.nx;
         dn = DIR == 0 ? m.dx : m.dy;
         dtan = DIR == 0 ? m.dy : m.dx;
     }
     static constexpr int sigma = DIR == 0 ? 1 : -1;
-    __device__ __forceinline__ long long cell(const Mesh& m, int n, int t) const {
+    DFK_HD long long cell(const Mesh& m, int n, int t) const {
         return DIR == 0 ? gid(m, n, t) : gid(m, t, n);
     }
     // line (f, t), t in [-2, nt+2): contiguous along the thread-x direction
-    __device__ __forceinline__ long long line(int f, int t) const {
+    DFK_HD long long line(int f, int t) const {
         return DIR == 0 ? (long long)(t + 2) * (nn + 1) + f : (long long)f * (nt + 4) + (t + 2);
     }
     // face (f, t), t in [0, nt)
-    __device__ __forceinline__ long long face(int f, int t) const {
+    DFK_HD long long face(int f, int t) const {
         return DIR == 0 ? (long long)t * (nn + 1) + f : (long long)f * nt + t;
     }
-    __device__ __forceinline__ long long nfaces() const { return (long long)(nn + 1) * nt; }
+    DFK_HD long long nfaces() const { return (long long)(nn + 1) * nt; }
 };
 
 __device__ __forceinline__ void warp_count_add(unsigned long long* dst, int v) {
@@ -52,13 +53,19 @@ __device__ __forceinline__ void warp_count_add(unsigned long long* dst, int v) {
     if ((threadIdx.x & 31) == 0 && s) atomicAdd(dst, (unsigned long long)s);
 }
 
-__device__ __forceinline__ void report_fail(DevState* st, int key) {
+DFK_HD void report_fail(DevState* st, int key) {
+#ifdef __CUDA_ARCH__
     atomicMin(&st->fail_key, (unsigned long long)key);
     if (atomicCAS(&st->err, 0, 5) == 0) st->fail_step = st->step;
     atomicExch(&st->halt, 1);
+#else   // host build of the bodies (sequential)
+    if ((unsigned long long)key < st->fail_key) st->fail_key = (unsigned long long)key;
+    if (st->err == 0) { st->err = 5; st->fail_step = st->step; }
+    st->halt = 1;
+#endif
 }
 
-__device__ __forceinline__ bool state_ok(const double W[4], double gm1) {
+DFK_HD bool state_ok(const double W[4], double gm1) {
     bool fin = isfinite(W[0]) && isfinite(W[1]) && isfinite(W[2]) && isfinite(W[3]);
     return fin && physical_state(W, gm1);
 }
@@ -90,7 +97,7 @@ __device__ __forceinline__ double block_min(double v) {
 }
 
 // one ghost cell of the x pass: ghost column gc in [0, 2G), interior row j
-__device__ __forceinline__ void ghost_x_body(const Mesh& m, double* W, double* alpha, int gc, int j) {
+DFK_HD void ghost_x_body(const Mesh& m, double* W, double* alpha, int gc, int j) {
     if (gc >= 2 * G || j >= m.ny) return;
     int i = gc < G ? gc - G : m.nx + gc - G;
     bool mir;
@@ -105,7 +112,7 @@ __device__ __forceinline__ void ghost_x_body(const Mesh& m, double* W, double* a
 }
 
 // one ghost cell of the y pass: column i in [-G, nx+G), ghost row gr in [0, 2G)
-__device__ __forceinline__ void ghost_y_body(const Mesh& m, double* W, double* alpha, int i, int gr) {
+DFK_HD void ghost_y_body(const Mesh& m, double* W, double* alpha, int i, int gr) {
     if (i >= m.nx + G) return;
     int j = gr < G ? gr - G : m.ny + gr - G;
     bool mir;
@@ -121,7 +128,7 @@ __device__ __forceinline__ void ghost_y_body(const Mesh& m, double* W, double* a
 
 // one face line (normal reconstruction of both sides); returns the number of DF branches taken
 template <int DIR>
-__device__ __forceinline__ int lines_body(const Mesh& m, const SchemeConsts& S, const double* __restrict__ W,
+DFK_HD int lines_body(const Mesh& m, const SchemeConsts& S, const double* __restrict__ W,
                                           const double* __restrict__ alpha, double* __restrict__ lines,
                                           long long ls, int ax, int ay) {
     Geo<DIR> g(m);
@@ -195,7 +202,7 @@ __device__ __forceinline__ int lines_body(const Mesh& m, const SchemeConsts& S, 
 // one face side (tangential reconstruction at both Gauss points, fallback); returns the number of
 // DF branches taken and sets nfb to the number of fallbacks
 template <int DIR>
-__device__ __forceinline__ int faces_body(const Mesh& m, const SchemeConsts& S, const double* __restrict__ W,
+DFK_HD int faces_body(const Mesh& m, const SchemeConsts& S, const double* __restrict__ W,
                                           const double* __restrict__ alpha, const double* __restrict__ lines,
                                           long long ls, double* __restrict__ gp, long long gs,
                                           int ax, int ay, int side, int& nfb) {
@@ -267,7 +274,7 @@ __device__ __forceinline__ int faces_body(const Mesh& m, const SchemeConsts& S, 
 
 // one Gauss point (flux, time derivative, DF factor, omega^t)
 template <int DIR, int FLUX, bool ALPHA_ONLY>
-__device__ __forceinline__ void flux_body(const Mesh& m, const SchemeConsts& S, const double* __restrict__ lines,
+DFK_HD void flux_body(const Mesh& m, const SchemeConsts& S, const double* __restrict__ lines,
                                           long long ls, const double* __restrict__ gp, long long gs,
                                           double* __restrict__ fr, long long fs, double dt, int ax, int ay, int mm) {
     Geo<DIR> g(m);
@@ -301,7 +308,7 @@ __device__ __forceinline__ void flux_body(const Mesh& m, const SchemeConsts& S, 
 
 // one cell: residual, limited time derivative, stage combination, alpha product, positivity
 template <int MODE>
-__device__ __forceinline__ void update_body(const Mesh& m, const SchemeConsts& S, const UpdateArgs& a,
+DFK_HD void update_body(const Mesh& m, const SchemeConsts& S, const UpdateArgs& a,
                                             const double* __restrict__ frx, long long fsx,
                                             const double* __restrict__ fry, long long fsy,
                                             double dt, DevState* st, int i, int j) {

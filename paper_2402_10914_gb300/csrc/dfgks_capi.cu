@@ -462,7 +462,7 @@ extern "C" dfgks_status dfgks_adjoint_steps(dfgks* h, const double* W0, int n, c
     for (int s = 0; s < n; ++s) if (!(dts[s] > 0.0)) return DFGKS_EINVAL;
     const Mesh& m = h->mesh;
     const long long N = (long long)m.nx * m.ny, N4 = 4 * N;
-    const int k = ckpt_every, nseg = (n + k - 1) / k;
+    const int k = ckpt_every < n ? ckpt_every : n, nseg = (n + k - 1) / k;
     std::vector<double*> bufs;
     auto get = [&](long long cnt) -> double* {
         double* p = nullptr;

@@ -27,6 +27,9 @@ def make_config(s: Settings) -> _lib.Config:
     return c
 
 
+CUDA_STREAM_LEGACY = 0x1        # cudaStreamLegacy
+
+
 def _ptr(t):
     if t is None:
         return None
@@ -45,8 +48,10 @@ class Solver:
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self._cfg = make_config(settings)
         h = C.c_void_p()
-        _lib.check(_lib.lib().dfgks_create(C.byref(self._cfg), C.c_void_p(self.stream.cuda_stream), C.byref(h)),
-                   "dfgks_create")
+        # torch's default stream has the handle 0, the legacy default stream; the C ABI reads NULL as
+        # "create a private stream", so the legacy stream goes in as cudaStreamLegacy
+        handle = self.stream.cuda_stream or CUDA_STREAM_LEGACY
+        _lib.check(_lib.lib().dfgks_create(C.byref(self._cfg), C.c_void_p(handle), C.byref(h)), "dfgks_create")
         self._h = h
 
     # -- lifecycle ---------------------------------------------------------------------
