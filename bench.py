@@ -55,8 +55,12 @@ def parse():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--n", type=int, default=400, help="mesh side of the four-quadrant workload")
-    p.add_argument("--workload", default="quadrants", choices=["quadrants", "batch"],
-                   help="quadrants: the 400x400 GKS step (default); batch: the 64-problem uneven batch")
+    p.add_argument("--workload", default="quadrants", choices=["quadrants", "batch", "adjoint"],
+                   help="quadrants: the 400x400 GKS step (default); batch: the 64-problem uneven batch; "
+                        "adjoint: gradient / forward time on the 256x256 vortex, 100 steps")
+    p.add_argument("--no-adjoint", action="store_true", help="leave the adjoint summary out of the default line")
+    p.add_argument("--adj-n", type=int, default=256, help="mesh side of the adjoint workload")
+    p.add_argument("--adj-steps", type=int, default=100, help="S2O4 steps of the adjoint workload")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     return p.parse_args()
@@ -302,6 +306,66 @@ def bench_batch(args):
     print(json.dumps(line))
 
 
+def adj_workload(n: int, nsteps: int, ckpt: int = 10) -> str:
+    return "vortex_%dx%d_gks_%dsteps_ckpt%d" % (n, n, nsteps, ckpt)
+
+
+def bench_adjoint(reps: int, warmup: int = 1, n: int = 256, nsteps: int = 100, ckpt: int = 10):
+    """Cost of the gradient of J = sum rho^2 after nsteps GKS steps on the isentropic vortex (time
+    limiter on), against the plain forward pass: the forward pass that keeps checkpoints plus the
+    backward pass (segment recompute + reverse sweeps), divided by the plain forward pass over the
+    same steps.  CUDA events on the solver's stream; a 256 MiB L2 flush before each timed region."""
+    import torch
+    from paper_2402_10914_gb300 import inputs as I
+    from paper_2402_10914_gb300.solver import Solver, adjoint_checkpointed, forward_checkpointed
+    w = I.vortex(n, steps=nsteps)
+    flush = torch.empty(32 * 1024 * 1024, dtype=torch.float64, device="cuda")
+    sol = Solver(w.settings)
+    W0 = torch.as_tensor(w.W0, device="cuda")
+    stream = sol.stream
+
+    def timed(fn):
+        flush.fill_(1.0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        out = fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b), out
+
+    def plain():
+        sol.set_ic(W0)
+        return timed(lambda: sol.step(nsteps))[0]
+
+    def gradient():
+        t_f, dts = timed(lambda: forward_checkpointed(sol, W0, nsteps, ckpt))
+        WT = sol.get_state(device=True)[0]
+        WTb = torch.zeros_like(WT)
+        WTb[0] = 2.0 * WT[0]
+        sol.timing(reset=True)
+        t_b, g = timed(lambda: adjoint_checkpointed(sol, WTb))
+        return t_f, t_b, sol.timing(reset=True)
+
+    sol.set_timing(True)
+    for _ in range(warmup):
+        plain()
+        gradient()
+    F, G = [], []
+    for _ in range(reps):
+        F.append(plain())
+        G.append(gradient())
+    sol.set_timing(False)
+    sol.close()
+    fwd = statistics.median(F)
+    tf = statistics.median([g[0] for g in G])
+    tb = statistics.median([g[1] for g in G])
+    rev = G[-1][2]
+    return {"workload": adj_workload(n, nsteps, ckpt), "ratio": (tf + tb) / fwd, "forward_ms": fwd, "forward_checkpointed_ms": tf,
+            "backward_ms": tb, "backward_over_forward": tb / fwd, "reps": reps,
+            "backward_kernel_ms": {k: round(v["ms"], 3) for k, v in rev.items()},
+            "definition": "(checkpointed forward + backward) / plain forward, same %d steps" % nsteps}
+
+
 def oracle_sample(n_threads=None, steps=1, n=400):
     """The CPU oracle as it stands on one full S2O4 step of the same workload."""
     import oracle
@@ -353,6 +417,20 @@ def main():
         if rank == 0:
             bench_batch(args)
         return
+    if args.workload == "adjoint":
+        if rank == 0:
+            a = bench_adjoint(args.steps, args.warmup, n=args.adj_n, nsteps=args.adj_steps)
+            line = {"metric": "adjoint/forward time ratio (gradient of sum rho^2 through %d GKS S2O4 steps)"
+                              % args.adj_steps,
+                    "value": a["ratio"], "unit": "x", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+                    "ms_per_step": (a["forward_checkpointed_ms"] + a["backward_ms"]) / args.adj_steps,
+                    "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                    "data": "synthetic", "config": {"workload": a["workload"], "nx": args.adj_n, "ny": args.adj_n,
+                                                    "flux": "GKS", "time_limiter": 1, "ckpt_every": 10,
+                                                    "l2": "flushed before each timed region"},
+                    "adjoint": a}
+            print(json.dumps(line))
+        return
     r = bench_ours(args, ws, rank, local)
     if rank != 0:
         return
@@ -374,6 +452,11 @@ def main():
         "roofline": r["roofline"], "cpu_baseline": cpu, "e2e": r["e2e"], "gpu_launches": r["launches"],
         "clocks": r["clocks"], "per_kernel_ms_per_step": r["per_kernel_ms_per_step"], "counters": r["counters"],
     }
+    if not args.no_adjoint and ws == 1:
+        try:
+            line["adjoint"] = bench_adjoint(1, 1)
+        except Exception as e:  # the benchmark line must still be printed
+            line["adjoint"] = {"workload": adj_workload(256, 100), "ratio": None, "error": str(e)}
     print(json.dumps(line))
 
 

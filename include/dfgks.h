@@ -157,14 +157,26 @@ DFGKS_API dfgks_status dfgks_adjoint_residual(dfgks* h, const double* W, const d
                                               const double* L_bar, const double* dtL_bar, const double* dtLt_bar,
                                               double* W_bar);
 
-/* Gradient through n S2O4 steps (Eq. 24 with the time limiter) started from W0 (device, dense):
- * W0_bar = (dW^n/dW0)^T WT_bar, with the step sizes dts[n] (host; e.g. those dfgks_step recorded),
- * alpha^0 computed from W0 as in dfgks_set_ic and the alpha sequence and branch decisions of the
- * forward trajectory held fixed.  Checkpointed recompute: the forward pass keeps W and alpha every
- * ckpt_every steps; each segment is recomputed from its checkpoint before its steps are reversed.
- * Allocates its checkpoint and segment buffers for the call.  On return the handle holds the
- * forward solution W^n, its alpha, time and step count.  S2O4 only (DFGKS_ENOTSUP otherwise);
- * DFGKS_ENONPOS if the forward trajectory loses positivity.  Synchronises the stream. */
+/* Forward pass for a later gradient: sets the state to W0 (device, dense; alpha^0 computed from W0
+ * as in dfgks_set_ic, t = 0) and advances n S2O4 steps of flux `flux`, with the step sizes dts_in[n]
+ * (host) or, if dts_in is NULL, the CFL rule; dts_out[n] (host, may be NULL) receives them.  Keeps W
+ * and alpha every ckpt_every steps and the step sizes in the handle (allocated on demand, freed
+ * by dfgks_destroy) for dfgks_adjoint_checkpointed.  Not part of the paper.  S2O4 only
+ * (DFGKS_ENOTSUP otherwise); DFGKS_ENONPOS if the trajectory loses positivity.  Synchronises. */
+DFGKS_API dfgks_status dfgks_forward_checkpointed(dfgks* h, const double* W0, int n, const double* dts_in, int flux,
+                                                  int ckpt_every, double* dts_out);
+
+/* Gradient through the steps of the last dfgks_forward_checkpointed (Eq. 24 with the time
+ * limiter): W0_bar = (dW^n/dW0)^T WT_bar, both device, dense [4][ny][nx], with the alpha sequence,
+ * step sizes and branch decisions of the forward trajectory held fixed.  Each segment of
+ * ckpt_every steps is recomputed from its checkpoint, keeping its stage states and (if they take at
+ * most half of the free device memory) every stage's forward sweep records, and then reversed.
+ * DFGKS_EINVAL if no forward pass was kept or the state changed since (set_ic, set_state, step).
+ * Allocates its segment buffers for the call.  Leaves the handle at W^n.  Synchronises. */
+DFGKS_API dfgks_status dfgks_adjoint_checkpointed(dfgks* h, const double* WT_bar, double* W0_bar);
+
+/* dfgks_forward_checkpointed with the given step sizes dts[n] followed by
+ * dfgks_adjoint_checkpointed: the gradient through n steps from W0 in one call. */
 DFGKS_API dfgks_status dfgks_adjoint_steps(dfgks* h, const double* W0, int n, const double* dts, int flux,
                                            int ckpt_every, const double* WT_bar, double* W0_bar);
 

@@ -69,6 +69,8 @@ SIGNATURES = {
     "dfgks_batch_set_shapes": [_V, _V],
     "dfgks_batch_autotune": [_V, _V, _D],
     "dfgks_adjoint_steps": [_V, _V, C.c_int, _D, C.c_int, C.c_int, _V, _V],
+    "dfgks_forward_checkpointed": [_V, _V, C.c_int, _D, C.c_int, C.c_int, _D],
+    "dfgks_adjoint_checkpointed": [_V, _V, _V],
 }
 
 

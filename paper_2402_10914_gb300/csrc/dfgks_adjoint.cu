@@ -5,11 +5,13 @@
 //   ka_flux  : one thread per Gauss point.  Face adjoints from the cells' L, dL/dt and limited
 //              dL/dt adjoints (Eq. 2 with A_m = 1/2), then the GKS / L-F flux adjoint into the
 //              Gauss-point record adjoints, and the time-limiter weight's adjoint.
-//   ka_faces : one thread per face side.  Recomputes the tangential reconstruction and scatters
-//              (atomically) into the adjoints of the five face lines and of the face basis; a
-//              Gauss point that fell back to the cell average sends its adjoint to that cell.
-//   ka_lines : one thread per face line.  Recomputes the normal reconstruction and the limiter
-//              weight and scatters into the ghosted cell adjoints.
+//   ka_faces : one thread per face side.  Evaluates each tangential reconstruction once, with its
+//              intermediates kept for its reverse, and scatters (atomically) into the adjoints of
+//              the five face lines and of the face basis; a Gauss point that fell back to the cell
+//              average (flagged in the forward record) sends its adjoint to that cell.
+//   ka_lines : one thread per face line.  The same for the eight normal reconstructions and the
+//              limiter weight (the forward record names the reconstruction that set it), then
+//              scatters into the ghosted cell adjoints.
 // A final pass folds ghost-cell adjoints back into the interior cells they were copied from.
 // alpha, dt and every branch decision are those of the forward pass.
 #include "dfgks_adjoint.cuh"
@@ -91,8 +93,9 @@ DFK_HD void ka_flux_body(const Mesh& m, const SchemeConsts& S, const AdjointArgs
 
 template <int DIR>
 DFK_HD void ka_faces_body(const Mesh& m, const SchemeConsts& S, const double* __restrict__ alpha,
-                          const double* __restrict__ lines, long long ls, const double* __restrict__ gb, long long gs,
-                          double* __restrict__ lb, double* __restrict__ Wb, int ax, int ay, int side) {
+                          const double* __restrict__ lines, long long ls, const double* __restrict__ gp,
+                          const double* __restrict__ gb, long long gs, double* __restrict__ lb,
+                          double* __restrict__ Wb, int ax, int ay, int side) {
     Geo<DIR> g(m);
     int f = DIR == 0 ? ax : ay;
     int t = DIR == 0 ? ay : ax;
@@ -114,59 +117,61 @@ DFK_HD void ka_faces_body(const Mesh& m, const SchemeConsts& S, const double* __
     double al[3];
     for (int b = 0; b < 3; ++b) al[b] = alpha[g.cell(m, ncell, t + Geo<DIR>::sigma * (b - 1))];
     const bool df = fmax(fmax(al[0], al[1]), al[2]) < S.alpha_thres;
-    double qv[2][4], qt[2][4];
     const double idt = 1.0 / g.dtan;
-    for (int k = 0; k < 4; ++k) {
-        double sq[5] = {Q[0][k], Q[1][k], Q[2][k], Q[3][k], Q[4][k]};
-        double v[2], s[2];
-        if (df) df_at_gauss(sq, al[1], v, s);
-        else { AO o = weno_ao(sq, S); ao_at_gauss(o, sq[2], v, s); }
-        qv[0][k] = v[0]; qv[1][k] = v[1];
-        qt[0][k] = s[0] * idt; qt[1][k] = s[1] * idt;
-    }
     const long long e = (long long)side * g.nfaces() + g.face(f, t);
-    BasisBar Bb;
-    basis_bar_zero(Bb);
-    double qvb[2][4], slb[2][4];
+    const int fbits = (int)gp[GP_FB * gs + e];
+    // Gauss-point adjoints -> characteristic value and tangential-slope adjoints (R^T, independent
+    // of the reconstruction); a Gauss point that used the cell average sends its adjoint there
+    double wb[2][4], wtb[2][4], qvb[2][4], slb[2][4];
     for (int mm = 0; mm < 2; ++mm) {
-        for (int k = 0; k < 4; ++k) { qvb[mm][k] = 0.0; slb[mm][k] = 0.0; }
-        double Wg[4];
-        back_project(B, qv[mm], Wg);
-        double wb[4], wnb[4], wtb[4];
         for (int k = 0; k < 4; ++k) {
-            wb[k] = gb[(mm * 12 + k) * gs + e];
-            wnb[k] = gb[(mm * 12 + 4 + k) * gs + e];
-            wtb[k] = gb[(mm * 12 + 8 + k) * gs + e];
+            wb[mm][k] = gb[(mm * 12 + k) * gs + e];
+            wtb[mm][k] = gb[(mm * 12 + 8 + k) * gs + e];
+            qvb[mm][k] = 0.0;
+            slb[mm][k] = 0.0;
         }
-        if (S.gp_fallback && !physical_state(Wg, S.gm1)) {
-            // the Gauss point used the (rotated) cell average with zero slopes
-            to_global<DIR>(wb);
+        if ((fbits >> mm) & 1) {
+            double wg[4] = {wb[mm][0], wb[mm][1], wb[mm][2], wb[mm][3]};
+            to_global<DIR>(wg);
             const long long c = g.cell(m, ncell, t);
-            for (int k = 0; k < 4; ++k) aadd(&Wb[k * m.plane + c], wb[k]);
+            for (int k = 0; k < 4; ++k) { aadd(&Wb[k * m.plane + c], wg[k]); wb[mm][k] = 0.0; wtb[mm][k] = 0.0; }
             continue;
         }
-        back_project_vjp(B, qv[mm], wb, qvb[mm], Bb);
         double qtb[4] = {0, 0, 0, 0};
-        back_project_vjp(B, qt[mm], wtb, qtb, Bb);
+        back_project_T(B, wb[mm], qvb[mm]);
+        back_project_T(B, wtb[mm], qtb);
         for (int k = 0; k < 4; ++k) {
             slb[mm][k] = qtb[k] * idt;
-            aadd(&lb[(nbase + k) * ls + l0], wnb[k]);            // normal slope copied from the line
+            aadd(&lb[(nbase + k) * ls + l0], gb[(mm * 12 + 4 + k) * gs + e]);   // normal slope copied from the line
         }
     }
-    double Qb[5][4];
-    for (int b = 0; b < 5; ++b) for (int k = 0; k < 4; ++k) Qb[b][k] = 0.0;
+    // per characteristic component: the reconstruction once, then its reverse
+    double qv[2][4], qt[2][4], Qb[5][4];
     for (int k = 0; k < 4; ++k) {
         double sq[5] = {Q[0][k], Q[1][k], Q[2][k], Q[3][k], Q[4][k]};
         double vb[2] = {qvb[0][k], qvb[1][k]}, sb[2] = {slb[0][k], slb[1][k]};
-        double qb[5] = {0, 0, 0, 0, 0};
-        if (df) df_at_gauss_vjp(al[1], vb, sb, qb);
-        else {
+        double v[2], sl[2], qb[5] = {0, 0, 0, 0, 0};
+        if (df) {
+            df_at_gauss(sq, al[1], v, sl);
+            df_at_gauss_vjp(al[1], vb, sb, qb);
+        } else {
+            AOTape T;
+            AO o = weno_ao_tape(sq, S, T);
+            ao_at_gauss(o, sq[2], v, sl);
             AOBar ob;
             ao_bar_zero(ob);
             ao_at_gauss_vjp(vb, sb, qb[2], ob);
-            weno_ao_vjp(sq, S, ob, qb);
+            weno_ao_tape_vjp(T, S, ob, qb);
         }
+        qv[0][k] = v[0]; qv[1][k] = v[1];
+        qt[0][k] = sl[0] * idt; qt[1][k] = sl[1] * idt;
         for (int b = 0; b < 5; ++b) Qb[b][k] = qb[b];
+    }
+    BasisBar Bb;
+    basis_bar_zero(Bb);
+    for (int mm = 0; mm < 2; ++mm) {          // zero adjoints (fallback) add nothing
+        back_project_basis_vjp(B, qv[mm], wb[mm], Bb);
+        back_project_basis_vjp(B, qt[mm], wtb[mm], Bb);
     }
     for (int b = 0; b < 5; ++b) {
         double wl[4] = {0, 0, 0, 0};
@@ -181,8 +186,8 @@ DFK_HD void ka_faces_body(const Mesh& m, const SchemeConsts& S, const double* __
 
 template <int DIR>
 DFK_HD void ka_lines_body(const Mesh& m, const SchemeConsts& S, const double* __restrict__ W,
-                          const double* __restrict__ alpha, const double* __restrict__ lb, long long ls,
-                          double* __restrict__ Wb, int ax, int ay) {
+                          const double* __restrict__ alpha, const double* __restrict__ lines,
+                          const double* __restrict__ lb, long long ls, double* __restrict__ Wb, int ax, int ay) {
     Geo<DIR> g(m);
     int f = DIR == 0 ? ax : ay;
     int tt = DIR == 0 ? ay : ax;
@@ -202,32 +207,10 @@ DFK_HD void ka_lines_body(const Mesh& m, const SchemeConsts& S, const double* __
     const bool dfL = fmax(fmax(al[1], al[2]), al[3]) < S.alpha_thres;
     const bool dfR = fmax(fmax(al[2], al[3]), al[4]) < S.alpha_thres;
     const double idn = 1.0 / g.dn;
-    // forward values, and the evaluation that sets the limiter weight: the first strict minimum
-    // over components per side (starting from 1), the right side on a tie between the sides
-    double qL[4], qLn[4], qR[4], qRn[4];
-    double tlL = 1.0, tlR = 1.0;
-    int kL = -1, kR = -1;
-    for (int k = 0; k < 4; ++k) {
-        double sL[5] = {Q[0][k], Q[1][k], Q[2][k], Q[3][k], Q[4][k]};
-        double sR[5] = {Q[5][k], Q[4][k], Q[3][k], Q[2][k], Q[1][k]};
-        double v, sl;
-        if (!dfL || S.time_limiter) {
-            AO o = weno_ao(sL, S);
-            if (S.time_limiter) { double la = limiter_alpha(o); if (la < tlL) { tlL = la; kL = k; } }
-            if (!dfL) ao_at_right_edge(o, sL[2], v, sl);
-        }
-        if (dfL) df_at_right_edge(sL, al[2], v, sl);
-        qL[k] = v; qLn[k] = sl * idn;
-        if (!dfR || S.time_limiter) {
-            AO o = weno_ao(sR, S);
-            if (S.time_limiter) { double la = limiter_alpha(o); if (la < tlR) { tlR = la; kR = k; } }
-            if (!dfR) ao_at_right_edge(o, sR[2], v, sl);
-        }
-        if (dfR) df_at_right_edge(sR, al[3], v, sl);
-        qR[k] = v; qRn[k] = -sl * idn;
-    }
+    // the reconstruction that set the limiter weight in the forward pass (2k + side) and the
+    // weight's adjoint
+    const int tlk = S.time_limiter ? (int)lines[LR_TLK * ls + li] : -1;
     const double tlb = S.time_limiter ? lb[LR_TL * ls + li] : 0.0;
-    const bool limL = tlL < tlR;            // the side whose weight is the face's
     BasisBar Bb;
     Bb.u = lb[LR_U * ls + li]; Bb.v = lb[LR_V * ls + li]; Bb.c = lb[LR_C * ls + li]; Bb.ic = lb[LR_IC * ls + li];
     Bb.H = lb[LR_H * ls + li]; Bb.b1 = lb[LR_B1 * ls + li]; Bb.b2 = lb[LR_B2 * ls + li]; Bb.q2 = lb[LR_Q2 * ls + li];
@@ -237,46 +220,49 @@ DFK_HD void ka_lines_body(const Mesh& m, const SchemeConsts& S, const double* __
         WRb[k] = lb[(LR_WR + k) * ls + li]; WRnb[k] = lb[(LR_WRN + k) * ls + li];
     }
     double qLb[4] = {0, 0, 0, 0}, qLnb[4] = {0, 0, 0, 0}, qRb[4] = {0, 0, 0, 0}, qRnb[4] = {0, 0, 0, 0};
-    back_project_vjp(B, qL, WLb, qLb, Bb);
-    back_project_vjp(B, qLn, WLnb, qLnb, Bb);
-    back_project_vjp(B, qR, WRb, qRb, Bb);
-    back_project_vjp(B, qRn, WRnb, qRnb, Bb);
-    double Qb[6][4];
+    back_project_T(B, WLb, qLb);
+    back_project_T(B, WLnb, qLnb);
+    back_project_T(B, WRb, qRb);
+    back_project_T(B, WRnb, qRnb);
+    double qL[4], qLn[4], qR[4], qRn[4], Qb[6][4];
     for (int s = 0; s < 6; ++s) for (int k = 0; k < 4; ++k) Qb[s][k] = 0.0;
     for (int k = 0; k < 4; ++k) {
-        double sL[5] = {Q[0][k], Q[1][k], Q[2][k], Q[3][k], Q[4][k]};
-        double sR[5] = {Q[5][k], Q[4][k], Q[3][k], Q[2][k], Q[1][k]};
-        double qbL[5] = {0, 0, 0, 0, 0}, qbR[5] = {0, 0, 0, 0, 0};
-        // left side: value at xi = +1/2, slope / dn
-        {
-            AOBar ob;
-            ao_bar_zero(ob);
-            bool need = false;
-            if (dfL) df_at_right_edge_vjp(al[2], qLb[k], qLnb[k] * idn, qbL);
-            else { ao_at_right_edge_vjp(qLb[k], qLnb[k] * idn, qbL[2], ob); need = true; }
-            if (S.time_limiter && limL && k == kL && tlb != 0.0) {
-                AO o = weno_ao(sL, S);
-                limiter_alpha_vjp(o, tlb, ob);
-                need = true;
+        for (int sd = 0; sd < 2; ++sd) {
+            // side 0: cell f-1, value at xi = +1/2; side 1: cell f, mirrored stencil, slope sign reversed
+            double sq[5];
+            for (int i = 0; i < 5; ++i) sq[i] = sd == 0 ? Q[i][k] : Q[5 - i][k];
+            const bool dfs = sd == 0 ? dfL : dfR;
+            const double as = sd == 0 ? al[2] : al[3];
+            const double sgn = sd == 0 ? 1.0 : -1.0;
+            const double vb = sd == 0 ? qLb[k] : qRb[k];
+            const double sb = sgn * (sd == 0 ? qLnb[k] : qRnb[k]) * idn;
+            const bool lim = tlk == 2 * k + sd && tlb != 0.0;
+            double v = 0.0, sl = 0.0, qb[5] = {0, 0, 0, 0, 0};
+            if (!dfs || lim) {
+                AOTape T;
+                AO o = weno_ao_tape(sq, S, T);
+                AOBar ob;
+                ao_bar_zero(ob);
+                if (!dfs) {
+                    ao_at_right_edge(o, sq[2], v, sl);
+                    ao_at_right_edge_vjp(vb, sb, qb[2], ob);
+                }
+                if (lim) limiter_alpha_vjp(o, tlb, ob);
+                weno_ao_tape_vjp(T, S, ob, qb);
             }
-            if (need) weno_ao_vjp(sL, S, ob, qbL);
-        }
-        // right side: mirrored stencil, slope sign reversed
-        {
-            AOBar ob;
-            ao_bar_zero(ob);
-            bool need = false;
-            if (dfR) df_at_right_edge_vjp(al[3], qRb[k], -qRnb[k] * idn, qbR);
-            else { ao_at_right_edge_vjp(qRb[k], -qRnb[k] * idn, qbR[2], ob); need = true; }
-            if (S.time_limiter && !limL && k == kR && tlb != 0.0) {
-                AO o = weno_ao(sR, S);
-                limiter_alpha_vjp(o, tlb, ob);
-                need = true;
+            if (dfs) {
+                df_at_right_edge(sq, as, v, sl);
+                df_at_right_edge_vjp(as, vb, sb, qb);
             }
-            if (need) weno_ao_vjp(sR, S, ob, qbR);
+            if (sd == 0) { qL[k] = v; qLn[k] = sl * idn; }
+            else { qR[k] = v; qRn[k] = -sl * idn; }
+            for (int i = 0; i < 5; ++i) Qb[sd == 0 ? i : 5 - i][k] += qb[i];
         }
-        for (int i = 0; i < 5; ++i) { Qb[i][k] += qbL[i]; Qb[5 - i][k] += qbR[i]; }
     }
+    back_project_basis_vjp(B, qL, WLb, Bb);
+    back_project_basis_vjp(B, qLn, WLnb, Bb);
+    back_project_basis_vjp(B, qR, WRb, Bb);
+    back_project_basis_vjp(B, qRn, WRnb, Bb);
     double Wcb[6][4];
     for (int s = 0; s < 6; ++s) {
         for (int k = 0; k < 4; ++k) Wcb[s][k] = 0.0;
@@ -340,17 +326,17 @@ __global__ void __launch_bounds__(128) ka_flux(Mesh m, SchemeConsts S, AdjointAr
 template <int DIR>
 __global__ void __launch_bounds__(128) ka_faces(Mesh m, SchemeConsts S, const double* __restrict__ alpha,
                                                 const double* __restrict__ lines, long long ls,
-                                                const double* __restrict__ gb, long long gs, double* __restrict__ lb,
-                                                double* __restrict__ Wb) {
-    ka_faces_body<DIR>(m, S, alpha, lines, ls, gb, gs, lb, Wb, blockIdx.x * blockDim.x + threadIdx.x,
+                                                const double* __restrict__ gp, const double* __restrict__ gb,
+                                                long long gs, double* __restrict__ lb, double* __restrict__ Wb) {
+    ka_faces_body<DIR>(m, S, alpha, lines, ls, gp, gb, gs, lb, Wb, blockIdx.x * blockDim.x + threadIdx.x,
                        blockIdx.y * blockDim.y + threadIdx.y, blockIdx.z);
 }
 
 template <int DIR>
 __global__ void __launch_bounds__(128) ka_lines(Mesh m, SchemeConsts S, const double* __restrict__ W,
-                                                const double* __restrict__ alpha, const double* __restrict__ lb,
-                                                long long ls, double* __restrict__ Wb) {
-    ka_lines_body<DIR>(m, S, W, alpha, lb, ls, Wb, blockIdx.x * blockDim.x + threadIdx.x,
+                                                const double* __restrict__ alpha, const double* __restrict__ lines,
+                                                const double* __restrict__ lb, long long ls, double* __restrict__ Wb) {
+    ka_lines_body<DIR>(m, S, W, alpha, lines, lb, ls, Wb, blockIdx.x * blockDim.x + threadIdx.x,
                        blockIdx.y * blockDim.y + threadIdx.y);
 }
 
@@ -379,9 +365,9 @@ static void adjoint_dir(const Mesh& m, const SchemeConsts& S, int flux, const Ad
         ka_flux<DIR, 1><<<gf, blk, 0, s>>>(m, S, a, B.gp, B.gp_stride, B.flux[DIR], B.flux_stride[DIR], dtp, lb,
                                            B.line_stride, gbuf);
     if (T) { T->end(KK_FLUX, 1); T->begin(KK_FACES); }
-    ka_faces<DIR><<<gf, blk, 0, s>>>(m, S, alpha, B.lines, B.line_stride, gbuf, B.gp_stride, lb, Wb);
+    ka_faces<DIR><<<gf, blk, 0, s>>>(m, S, alpha, B.lines, B.line_stride, B.gp, gbuf, B.gp_stride, lb, Wb);
     if (T) { T->end(KK_FACES, 1); T->begin(KK_LINES); }
-    ka_lines<DIR><<<gl, blk, 0, s>>>(m, S, W, alpha, lb, B.line_stride, Wb);
+    ka_lines<DIR><<<gl, blk, 0, s>>>(m, S, W, alpha, B.lines, lb, B.line_stride, Wb);
     if (T) T->end(KK_LINES, 1);
 }
 

@@ -67,6 +67,27 @@ DFK_HD void project_vjp(const CharBasis& B, const double W[4], const double Qb[4
     Wb[3] += -tb * B.b1;
 }
 
+// the two halves of the adjoint of back_project (W = R Q): Qb += R^T Wb, which does not depend on
+// Q, and the basis adjoint, which is linear in Q
+DFK_HD void back_project_T(const CharBasis& B, const double Wb[4], double Qb[4]) {
+    double W0b = Wb[0] + Wb[2] * B.v + Wb[1] * B.u;
+    double sb = Wb[3] * B.H + W0b, db = Wb[3] * B.u * B.c + Wb[1] * B.c;
+    Qb[1] += Wb[3] * B.q2 + W0b;
+    Qb[2] += Wb[3] * B.v + Wb[2];
+    Qb[0] += sb - db;
+    Qb[3] += sb + db;
+}
+
+DFK_HD void back_project_basis_vjp(const CharBasis& B, const double Q[4], const double Wb[4], BasisBar& Bb) {
+    double s = Q[0] + Q[3], d = Q[3] - Q[0];
+    double W0 = s + Q[1];
+    Bb.H += Wb[3] * s;
+    Bb.u += Wb[3] * B.c * d + Wb[1] * W0;
+    Bb.c += Wb[3] * B.u * d + Wb[1] * d;
+    Bb.q2 += Wb[3] * Q[1];
+    Bb.v += Wb[3] * Q[2] + Wb[2] * W0;
+}
+
 // adjoint of back_project (W = R Q): Qb += R^T Wb, basis adjoint accumulated
 DFK_HD void back_project_vjp(const CharBasis& B, const double Q[4], const double Wb[4], double Qb[4], BasisBar& Bb) {
     double s = Q[0] + Q[3], d = Q[3] - Q[0];
@@ -104,62 +125,92 @@ struct AOBar { double A1, A2, c3a3, c3a4, rmax, rmin; };
 
 DFK_HD void ao_bar_zero(AOBar& b) { b.A1 = b.A2 = b.c3a3 = b.c3a4 = b.rmax = b.rmin = 0.0; }
 
-DFK_HD void weno_ao_vjp(const double q[5], const SchemeConsts& S, const AOBar& ob, double qb[5]) {
+// WENO-AO with the intermediates its reverse needs kept, so that a reverse sweep evaluates each
+// reconstruction once: the forward values of weno_ao (up to the rounding of the ratios, which
+// here go through 1/(beta_k + eps)) and a tape for weno_ao_tape_vjp.
+struct AOTape {
+    double a1[4], a2[4], a3, a4;   // sub-stencil linear/quadratic coefficients, the quartic's a3, a4
+    double ie[4];                  // 1 / (beta_k + eps)
+    double r[4], w[4], iw, c3;     // tau/(beta_k+eps), unnormalised weights, 1/sum w, c_3
+    double sg[3];                  // sign(beta_3 - beta_k), k < 3
+    int kmax, kmin;                // first indices attaining max / min of r
+};
+
+DFK_HD AO weno_ao_tape(const double q[5], const SchemeConsts& S, AOTape& T) {
     const double qm2 = q[0], qm1 = q[1], q0 = q[2], q1 = q[3], q2 = q[4];
-    double a1[4], a2[4];
-    a1[0] = 0.5 * qm2 - 2.0 * qm1 + 1.5 * q0;
-    a2[0] = 0.5 * (qm2 - 2.0 * qm1 + q0);
-    a1[1] = 0.5 * (q1 - qm1);
-    a2[1] = 0.5 * (qm1 - 2.0 * q0 + q1);
-    a1[2] = -1.5 * q0 + 2.0 * q1 - 0.5 * q2;
-    a2[2] = 0.5 * (q0 - 2.0 * q1 + q2);
-    a1[3] = (5.0 * (qm2 - q2) - 34.0 * (qm1 - q1)) * (1.0 / 48.0);
-    a2[3] = (-(qm2 + q2) + 12.0 * (qm1 + q1) - 22.0 * q0) * (1.0 / 16.0);
-    double a3 = (-(qm2 - q2) + 2.0 * (qm1 - q1)) * (1.0 / 12.0);
-    double a4 = ((qm2 + q2) - 4.0 * (qm1 + q1) + 6.0 * q0) * (1.0 / 24.0);
+    T.a1[0] = 0.5 * qm2 - 2.0 * qm1 + 1.5 * q0;
+    T.a2[0] = 0.5 * (qm2 - 2.0 * qm1 + q0);
+    T.a1[1] = 0.5 * (q1 - qm1);
+    T.a2[1] = 0.5 * (qm1 - 2.0 * q0 + q1);
+    T.a1[2] = -1.5 * q0 + 2.0 * q1 - 0.5 * q2;
+    T.a2[2] = 0.5 * (q0 - 2.0 * q1 + q2);
+    T.a1[3] = (5.0 * (qm2 - q2) - 34.0 * (qm1 - q1)) * (1.0 / 48.0);
+    T.a2[3] = (-(qm2 + q2) + 12.0 * (qm1 + q1) - 22.0 * q0) * (1.0 / 16.0);
+    T.a3 = (-(qm2 - q2) + 2.0 * (qm1 - q1)) * (1.0 / 12.0);
+    T.a4 = ((qm2 + q2) - 4.0 * (qm1 + q1) + 6.0 * q0) * (1.0 / 24.0);
     const double c13_3 = 13.0 / 3.0;
     double b[4];
-    for (int k = 0; k < 3; ++k) b[k] = a1[k] * a1[k] + c13_3 * a2[k] * a2[k];
-    b[3] = a1[3] * (a1[3] + 0.5 * a3) + c13_3 * a2[3] * a2[3] + (21.0 / 5.0) * a2[3] * a4
-         + (3129.0 / 80.0) * a3 * a3 + (87617.0 / 140.0) * a4 * a4;
+    for (int k = 0; k < 3; ++k) b[k] = T.a1[k] * T.a1[k] + c13_3 * T.a2[k] * T.a2[k];
+    b[3] = T.a1[3] * (T.a1[3] + 0.5 * T.a3) + c13_3 * T.a2[3] * T.a2[3] + (21.0 / 5.0) * T.a2[3] * T.a4
+         + (3129.0 / 80.0) * T.a3 * T.a3 + (87617.0 / 140.0) * T.a4 * T.a4;
     double tau = (fabs(b[3] - b[0]) + fabs(b[3] - b[1]) + fabs(b[3] - b[2])) * (1.0 / 3.0);
-    double e[4], r[4], w[4], wsum = 0.0;
-    for (int k = 0; k < 4; ++k) { e[k] = b[k] + S.eps; r[k] = tau / e[k]; w[k] = S.d[k] * (1.0 + r[k] * r[k]); wsum += w[k]; }
-    double iw = 1.0 / wsum;
-    double c3 = w[3] * iw * S.inv_d3;
-    double c[4];
-    for (int k = 0; k < 3; ++k) c[k] = w[k] * iw - c3 * S.d[k];
-    c[3] = c3;
-    // reverse
-    double a1b[4], a2b[4], cb[4];
-    for (int k = 0; k < 4; ++k) { a1b[k] = ob.A1 * c[k]; a2b[k] = ob.A2 * c[k]; cb[k] = ob.A1 * a1[k] + ob.A2 * a2[k]; }
-    cb[3] += ob.c3a3 * a3 + ob.c3a4 * a4;
-    double a3b = ob.c3a3 * c3, a4b = ob.c3a4 * c3;
-    double wb[4] = {0, 0, 0, 0}, iwb = 0.0;
-    for (int k = 0; k < 3; ++k) { wb[k] += cb[k] * iw; iwb += cb[k] * w[k]; cb[3] += -cb[k] * S.d[k]; }
-    wb[3] += cb[3] * iw * S.inv_d3;
-    iwb += cb[3] * w[3] * S.inv_d3;
-    double sumb = -iwb * iw * iw;
-    double rb[4];
-    for (int k = 0; k < 4; ++k) { wb[k] += sumb; rb[k] = wb[k] * S.d[k] * 2.0 * r[k]; }
-    // rmax / rmin: the first index attaining them
-    int kmax = 0, kmin = 0;
-    for (int k = 1; k < 4; ++k) { if (r[k] > r[kmax]) kmax = k; if (r[k] < r[kmin]) kmin = k; }
-    rb[kmax] += ob.rmax;
-    rb[kmin] += ob.rmin;
-    double taub = 0.0, bb[4];
-    for (int k = 0; k < 4; ++k) { taub += rb[k] / e[k]; bb[k] = -rb[k] * r[k] / e[k]; }
-    for (int k = 0; k < 3; ++k) {
-        double sg = (b[3] - b[k]) >= 0.0 ? 1.0 : -1.0;
-        bb[3] += taub * (1.0 / 3.0) * sg;
-        bb[k] -= taub * (1.0 / 3.0) * sg;
+    for (int k = 0; k < 3; ++k) T.sg[k] = (b[3] - b[k]) >= 0.0 ? 1.0 : -1.0;
+    double e0 = b[0] + S.eps, e1 = b[1] + S.eps, e2 = b[2] + S.eps, e3 = b[3] + S.eps;
+    double p01 = e0 * e1, p23 = e2 * e3, prod = p01 * p23;
+    if (prod < 1e300) {                                  // one division for the four reciprocals
+        double ip = 1.0 / prod;
+        T.ie[0] = (e1 * p23) * ip; T.ie[1] = (e0 * p23) * ip; T.ie[2] = (p01 * e3) * ip; T.ie[3] = (p01 * e2) * ip;
+    } else {
+        T.ie[0] = 1.0 / e0; T.ie[1] = 1.0 / e1; T.ie[2] = 1.0 / e2; T.ie[3] = 1.0 / e3;
     }
-    for (int k = 0; k < 3; ++k) { a1b[k] += bb[k] * 2.0 * a1[k]; a2b[k] += bb[k] * 2.0 * c13_3 * a2[k]; }
-    a1b[3] += bb[3] * (2.0 * a1[3] + 0.5 * a3);
-    a3b += bb[3] * (0.5 * a1[3] + 2.0 * (3129.0 / 80.0) * a3);
-    a2b[3] += bb[3] * (2.0 * c13_3 * a2[3] + (21.0 / 5.0) * a4);
-    a4b += bb[3] * ((21.0 / 5.0) * a2[3] + 2.0 * (87617.0 / 140.0) * a4);
-    // coefficients -> stencil values
+    double wsum = 0.0;
+    for (int k = 0; k < 4; ++k) { T.r[k] = tau * T.ie[k]; T.w[k] = S.d[k] * (1.0 + T.r[k] * T.r[k]); wsum += T.w[k]; }
+    T.iw = 1.0 / wsum;
+    T.c3 = T.w[3] * T.iw * S.inv_d3;
+    T.kmax = 0; T.kmin = 0;
+    for (int k = 1; k < 4; ++k) { if (T.r[k] > T.r[T.kmax]) T.kmax = k; if (T.r[k] < T.r[T.kmin]) T.kmin = k; }
+    AO o;
+    o.A1 = T.c3 * T.a1[3];
+    o.A2 = T.c3 * T.a2[3];
+    for (int k = 0; k < 3; ++k) {
+        double ck = T.w[k] * T.iw - T.c3 * S.d[k];
+        o.A1 += ck * T.a1[k];
+        o.A2 += ck * T.a2[k];
+    }
+    o.c3a3 = T.c3 * T.a3;
+    o.c3a4 = T.c3 * T.a4;
+    o.rmax = T.r[T.kmax];
+    o.rmin = T.r[T.kmin];
+    return o;
+}
+
+DFK_HD void weno_ao_tape_vjp(const AOTape& T, const SchemeConsts& S, const AOBar& ob, double qb[5]) {
+    const double c13_3 = 13.0 / 3.0;
+    double c[4];
+    for (int k = 0; k < 3; ++k) c[k] = T.w[k] * T.iw - T.c3 * S.d[k];
+    c[3] = T.c3;
+    double a1b[4], a2b[4], cb[4];
+    for (int k = 0; k < 4; ++k) { a1b[k] = ob.A1 * c[k]; a2b[k] = ob.A2 * c[k]; cb[k] = ob.A1 * T.a1[k] + ob.A2 * T.a2[k]; }
+    cb[3] += ob.c3a3 * T.a3 + ob.c3a4 * T.a4;
+    double a3b = ob.c3a3 * T.c3, a4b = ob.c3a4 * T.c3;
+    double wb[4], iwb = 0.0;
+    for (int k = 0; k < 3; ++k) { wb[k] = cb[k] * T.iw; iwb += cb[k] * T.w[k]; cb[3] -= cb[k] * S.d[k]; }
+    wb[3] = cb[3] * T.iw * S.inv_d3;
+    iwb += cb[3] * T.w[3] * S.inv_d3;
+    const double sumb = -iwb * T.iw * T.iw;
+    double rb[4];
+    for (int k = 0; k < 4; ++k) rb[k] = (wb[k] + sumb) * S.d[k] * 2.0 * T.r[k];
+    rb[T.kmax] += ob.rmax;
+    rb[T.kmin] += ob.rmin;
+    double taub = 0.0, bb[4];
+    for (int k = 0; k < 4; ++k) { double t = rb[k] * T.ie[k]; taub += t; bb[k] = -t * T.r[k]; }
+    const double tb3 = taub * (1.0 / 3.0);
+    for (int k = 0; k < 3; ++k) { bb[3] += tb3 * T.sg[k]; bb[k] -= tb3 * T.sg[k]; }
+    for (int k = 0; k < 3; ++k) { a1b[k] += bb[k] * 2.0 * T.a1[k]; a2b[k] += bb[k] * 2.0 * c13_3 * T.a2[k]; }
+    a1b[3] += bb[3] * (2.0 * T.a1[3] + 0.5 * T.a3);
+    a3b += bb[3] * (0.5 * T.a1[3] + 2.0 * (3129.0 / 80.0) * T.a3);
+    a2b[3] += bb[3] * (2.0 * c13_3 * T.a2[3] + (21.0 / 5.0) * T.a4);
+    a4b += bb[3] * ((21.0 / 5.0) * T.a2[3] + 2.0 * (87617.0 / 140.0) * T.a4);
     qb[0] += 0.5 * a1b[0] + 0.5 * a2b[0] + (5.0 / 48.0) * a1b[3] - (1.0 / 16.0) * a2b[3] - (1.0 / 12.0) * a3b + (1.0 / 24.0) * a4b;
     qb[1] += -2.0 * a1b[0] - a2b[0] - 0.5 * a1b[1] + 0.5 * a2b[1] - (34.0 / 48.0) * a1b[3] + (12.0 / 16.0) * a2b[3]
            + (2.0 / 12.0) * a3b - (4.0 / 24.0) * a4b;

@@ -158,6 +158,7 @@ DFK_HD int lines_body(const Mesh& m, const SchemeConsts& S, const double* __rest
         const double idn = 1.0 / g.dn;
         double qL[4], qLn[4], qR[4], qRn[4];
         double tl = 1.0;
+        int tlk = -1;                                     // the reconstruction that set tl
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             double sL[5] = {Q[0][k], Q[1][k], Q[2][k], Q[3][k], Q[4][k]};
@@ -165,14 +166,14 @@ DFK_HD int lines_body(const Mesh& m, const SchemeConsts& S, const double* __rest
             double v, sl;
             if (!dfL || S.time_limiter) {
                 AO o = weno_ao(sL, S);
-                if (S.time_limiter) tl = fmin(tl, limiter_alpha(o));
+                if (S.time_limiter) { double la = limiter_alpha(o); if (la < tl) { tl = la; tlk = 2 * k; } }
                 if (!dfL) ao_at_right_edge(o, sL[2], v, sl);
             }
             if (dfL) df_at_right_edge(sL, al[2], v, sl);
             qL[k] = v; qLn[k] = sl * idn;
             if (!dfR || S.time_limiter) {
                 AO o = weno_ao(sR, S);
-                if (S.time_limiter) tl = fmin(tl, limiter_alpha(o));
+                if (S.time_limiter) { double la = limiter_alpha(o); if (la < tl) { tl = la; tlk = 2 * k + 1; } }
                 if (!dfR) ao_at_right_edge(o, sR[2], v, sl);
             }
             if (dfR) df_at_right_edge(sR, al[3], v, sl);
@@ -187,6 +188,7 @@ DFK_HD int lines_body(const Mesh& m, const SchemeConsts& S, const double* __rest
 #pragma unroll
         for (int q = 0; q < 16; ++q) lines[q * ls + li] = out[q];
         lines[LR_TL * ls + li] = tl;
+        lines[LR_TLK * ls + li] = (double)tlk;
         lines[LR_U * ls + li] = B.u;
         lines[LR_V * ls + li] = B.v;
         lines[LR_C * ls + li] = B.c;
@@ -247,6 +249,7 @@ DFK_HD int faces_body(const Mesh& m, const SchemeConsts& S, const double* __rest
         }
         const long long e = (long long)side * g.nfaces() + g.face(f, t);
         const int nbase = side == 0 ? LR_WLN : LR_WRN;
+        int fbits = 0;
 #pragma unroll
         for (int mm = 0; mm < 2; ++mm) {
             double Wg[4], Wt[4], Wn[4];
@@ -260,6 +263,7 @@ DFK_HD int faces_body(const Mesh& m, const SchemeConsts& S, const double* __rest
                 for (int k = 0; k < 4; ++k) { Wg[k] = W[k * m.plane + c]; Wn[k] = 0.0; Wt[k] = 0.0; }
                 to_local<DIR>(Wg);
                 ++nfb;
+                fbits |= 1 << mm;
             }
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
@@ -268,6 +272,7 @@ DFK_HD int faces_body(const Mesh& m, const SchemeConsts& S, const double* __rest
                 gp[(mm * 12 + 8 + k) * gs + e] = Wt[k];
             }
         }
+        gp[GP_FB * gs + e] = (double)fbits;
     }
     return ndf;
 }

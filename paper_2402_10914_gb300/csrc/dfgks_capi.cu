@@ -40,6 +40,15 @@ struct dfgks {
     double* adj_lines;     // reverse sweep: face-line record adjoints
     double* adj_gp;        // reverse sweep: Gauss-point record adjoints
     double* adj_Wg;        // reverse sweep: ghosted cell adjoints
+    // checkpointed forward pass kept for dfgks_adjoint_checkpointed
+    double* ck_W;          // dense [nseg][4][ny][nx]: W at steps 0, k, 2k, ...
+    double* ck_A;          // dense [nseg][ny][nx]: alpha at the same steps
+    long long ck_cap;      // checkpoints ck_W / ck_A can hold
+    double* ck_dts;        // host [ck_n]: the steps' dt
+    int ck_dts_cap;
+    int ck_n, ck_k, ck_flux;
+    unsigned long long gen;      // bumped by every call that changes the state
+    unsigned long long ck_gen;   // gen right after the checkpointed forward pass (0: none)
 };
 
 static dfgks_status cuda_status(cudaError_t e) {
@@ -98,6 +107,9 @@ static void free_all(dfgks* h) {
     double* ptrs[] = {h->W[0], h->W[1], h->A[0], h->A[1], h->Ws, h->As, h->acc, h->B.lines, h->B.gp,
                       h->B.flux[0], h->B.flux[1], h->dt_scratch, h->dts, h->adj_lines, h->adj_gp, h->adj_Wg};
     for (double* p : ptrs) if (p) cudaFree(p);
+    if (h->ck_W) cudaFree(h->ck_W);
+    if (h->ck_A) cudaFree(h->ck_A);
+    free(h->ck_dts);
     if (h->st) cudaFree(h->st);
     if (h->flag) cudaFree(h->flag);
     if (h->st_host) cudaFreeHost(h->st_host);
@@ -263,6 +275,7 @@ static dfgks_status load_state(dfgks* h, const double* W, const double* alpha, d
     }
     CK_LAUNCH();
     h->fail_step = -1; h->fail_i = -1; h->fail_j = -1;
+    ++h->gen;
     return reset_devstate(h, t, step);
 }
 
@@ -298,7 +311,10 @@ extern "C" dfgks_status dfgks_get_state(dfgks* h, double* W, double* alpha, doub
 }
 
 // one step of Algorithm 1 on buffers (in -> out); every kernel returns at once once st->halt is set
-static void enqueue_step(dfgks* h, int s, double dt, int flux, double t_end, int cur0, double* Wstar_store = nullptr) {
+// rec (optional): four sweep-buffer sets, [stage][direction], that keep the stage's face-line,
+// Gauss-point and flux records for the reverse sweep instead of the handle's shared buffers
+static void enqueue_step(dfgks* h, int s, double dt, int flux, double t_end, int cur0, double* Wstar_store = nullptr,
+                         const SweepBuffers* rec = nullptr) {
     const Mesh& m = h->mesh;
     const SchemeConsts& S = h->S;
     cudaStream_t st = h->stream;
@@ -315,14 +331,21 @@ static void enqueue_step(dfgks* h, int s, double dt, int flux, double t_end, int
     UpdateArgs a;
     memset(&a, 0, sizeof(a));
     if (h->cfg.time_scheme == DFGKS_TIME_S2O4) {
-        for (int d = 0; d < 2; ++d) launch_sweep(d, m, S, flux, false, in, ain, dtp, h->B, h->st, halt, st, T);
+        SweepBuffers Bu[2] = {h->B, h->B};
+        if (rec)
+            for (int q = 0; q < 2; ++q) {
+                Bu[q].flux[0] = rec[2 * q].flux[0]; Bu[q].flux_stride[0] = rec[2 * q].flux_stride[0];
+                Bu[q].flux[1] = rec[2 * q + 1].flux[1]; Bu[q].flux_stride[1] = rec[2 * q + 1].flux_stride[1];
+            }
+        for (int d = 0; d < 2; ++d) launch_sweep(d, m, S, flux, false, in, ain, dtp, rec ? rec[d] : h->B, h->st, halt, st, T);
         a.Win = in; a.Wout = h->Ws; a.acc = h->acc;
-        launch_update(UM_S2O4_1, m, S, a, h->B, dtp, h->st, halt, st, T);
+        launch_update(UM_S2O4_1, m, S, a, Bu[0], dtp, h->st, halt, st, T);
         if (Wstar_store) launch_ghosted_to_dense(m, h->Ws, 4, Wstar_store, st);
         launch_fill_ghosts(m, h->Ws, nullptr, halt, st, T);
-        for (int d = 0; d < 2; ++d) launch_sweep(d, m, S, flux, false, h->Ws, ain, dtp, h->B, h->st, halt, st, T);
+        for (int d = 0; d < 2; ++d)
+            launch_sweep(d, m, S, flux, false, h->Ws, ain, dtp, rec ? rec[2 + d] : h->B, h->st, halt, st, T);
         a.Win = h->Ws; a.Wout = out; a.alpha_out = aout;
-        launch_update(UM_S2O4_2, m, S, a, h->B, dtp, h->st, halt, st, T);
+        launch_update(UM_S2O4_2, m, S, a, Bu[1], dtp, h->st, halt, st, T);
     } else {
         for (int d = 0; d < 2; ++d) launch_sweep(d, m, S, flux, false, in, ain, dtp, h->B, h->st, halt, st, T);
         a.Win = in; a.Wout = h->Ws;
@@ -343,6 +366,7 @@ extern "C" dfgks_status dfgks_step(dfgks* h, int n, double dt, int flux, double 
     if (steps_done) *steps_done = 0;
     if (!h || n < 0 || (flux != DFGKS_FLUX_GKS && flux != DFGKS_FLUX_LF)) return DFGKS_EINVAL;
     if (n == 0) return DFGKS_OK;
+    ++h->gen;
     if (n > h->dts_cap) {
         cudaFree(h->dts);
         h->bytes -= (unsigned long long)h->dts_cap * sizeof(double);
@@ -426,8 +450,11 @@ static dfgks_status ensure_adjoint_buffers(dfgks* h) {
 }
 
 // reverse sweep of the stage operator at (W, alpha, dt); W_bar (dense, device) += J^T (L_bar, ...)
+// rec (optional): the stage's forward records per direction, kept by the forward pass; without
+// them each direction's forward sweep is recomputed first
 static dfgks_status adjoint_stage(dfgks* h, const double* W, const double* alpha, double dt, int flux,
-                                  const double* L_bar, const double* dtL_bar, const double* dtLt_bar, double* W_bar) {
+                                  const double* L_bar, const double* dtL_bar, const double* dtLt_bar, double* W_bar,
+                                  const SweepBuffers* rec = nullptr) {
     dfgks_status r = ensure_adjoint_buffers(h);
     if (r) return r;
     launch_dense_to_ghosted(h->mesh, W, 4, h->Ws, h->stream);
@@ -438,9 +465,10 @@ static dfgks_status adjoint_stage(dfgks* h, const double* W, const double* alpha
     AdjointArgs a = {L_bar, dtL_bar, dtLt_bar};
     for (int d = 0; d < 2; ++d) {
         // the records of this direction, then its reverse sweep
-        launch_sweep(d, h->mesh, h->S, flux, false, h->Ws, h->As, h->dt_scratch, h->B, nullptr, nullptr, h->stream);
-        launch_adjoint_dir(d, h->mesh, h->S, flux, a, h->Ws, h->As, h->dt_scratch, h->B, h->adj_lines, h->adj_gp,
-                           h->adj_Wg, h->stream, h->timer->on ? h->timer : nullptr);
+        if (!rec)
+            launch_sweep(d, h->mesh, h->S, flux, false, h->Ws, h->As, h->dt_scratch, h->B, nullptr, nullptr, h->stream);
+        launch_adjoint_dir(d, h->mesh, h->S, flux, a, h->Ws, h->As, h->dt_scratch, rec ? rec[d] : h->B, h->adj_lines,
+                           h->adj_gp, h->adj_Wg, h->stream, h->timer->on ? h->timer : nullptr);
     }
     launch_adjoint_finish(h->mesh, h->adj_Wg, W_bar, h->stream);
     CK_LAUNCH();
@@ -454,15 +482,87 @@ extern "C" dfgks_status dfgks_adjoint_residual(dfgks* h, const double* W, const 
     return adjoint_stage(h, W, alpha, dt, flux, L_bar, dtL_bar, dtLt_bar, W_bar);
 }
 
-extern "C" dfgks_status dfgks_adjoint_steps(dfgks* h, const double* W0, int n, const double* dts, int flux, int ckpt_every,
-                                            const double* WT_bar, double* W0_bar) {
-    if (!h || !W0 || !dts || !WT_bar || !W0_bar || n < 1 || ckpt_every < 1 || (flux != 0 && flux != 1))
-        return DFGKS_EINVAL;
-    if (h->cfg.time_scheme != DFGKS_TIME_S2O4) return DFGKS_ENOTSUP;
-    for (int s = 0; s < n; ++s) if (!(dts[s] > 0.0)) return DFGKS_EINVAL;
+// Forward pass from W0 (alpha^0 from W0) over n S2O4 steps, dt from dts_in or, if that is NULL, the
+// CFL rule; W and alpha are kept every k steps and the dts on the host, for the reverse pass.
+static dfgks_status forward_checkpointed(dfgks* h, const double* W0, int n, const double* dts_in, int k, int flux) {
     const Mesh& m = h->mesh;
     const long long N = (long long)m.nx * m.ny, N4 = 4 * N;
-    const int k = ckpt_every < n ? ckpt_every : n, nseg = (n + k - 1) / k;
+    const int nseg = (n + k - 1) / k;
+    h->ck_gen = 0;
+    if (nseg > h->ck_cap) {
+        if (h->ck_W) { cudaFree(h->ck_W); h->bytes -= (unsigned long long)h->ck_cap * N4 * sizeof(double); h->ck_W = nullptr; }
+        if (h->ck_A) { cudaFree(h->ck_A); h->bytes -= (unsigned long long)h->ck_cap * N * sizeof(double); h->ck_A = nullptr; }
+        h->ck_cap = 0;
+        CK(dalloc(h, &h->ck_W, (long long)nseg * N4));
+        CK(dalloc(h, &h->ck_A, (long long)nseg * N));
+        h->ck_cap = nseg;
+    }
+    if (n > h->ck_dts_cap) {
+        double* p = (double*)realloc(h->ck_dts, (size_t)n * sizeof(double));
+        if (!p) return DFGKS_ENOMEM;
+        h->ck_dts = p;
+        h->ck_dts_cap = n;
+    }
+    if (n > h->dts_cap) {
+        cudaFree(h->dts);
+        h->bytes -= (unsigned long long)h->dts_cap * sizeof(double);
+        h->dts = nullptr;
+        CK(dalloc(h, &h->dts, n));
+        h->dts_cap = n;
+    }
+    dfgks_status r = load_state(h, W0, nullptr, 0.0, 0, 1);
+    if (r) return r;
+    const int cur0 = h->cur;
+    for (int s = 0; s < n; ++s) {
+        const int c = (cur0 + s) & 1;
+        if (s % k == 0) {
+            launch_ghosted_to_dense(m, h->W[c], 4, h->ck_W + (long long)(s / k) * N4, h->stream);
+            launch_ghosted_to_dense(m, h->A[c], 1, h->ck_A + (long long)(s / k) * N, h->stream);
+        }
+        enqueue_step(h, s, dts_in ? dts_in[s] : 0.0, flux, 0.0, cur0);
+    }
+    CK_LAUNCH();
+    CK(cudaMemcpyAsync(h->st_host, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    h->timer->harvest();
+    const long long done = h->st_host->step;
+    h->cur = (int)((cur0 + done) & 1);
+    if (h->st_host->err || done != n) return DFGKS_ENONPOS;
+    CK(cudaMemcpy(h->ck_dts, h->dts, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost));
+    h->ck_n = n; h->ck_k = k; h->ck_flux = flux;
+    h->ck_gen = ++h->gen;
+    return DFGKS_OK;
+}
+
+// doubles of one step's forward records: two stages x two directions of face lines, Gauss points and fluxes
+static long long record_doubles_per_step(const dfgks* h) {
+    const SweepBuffers& B = h->B;
+    long long per_dir = (long long)LR_COUNT * B.line_stride + (long long)GP_COUNT * B.gp_stride;
+    return 2 * (2 * per_dir + (long long)FR_COUNT * (B.flux_stride[0] + B.flux_stride[1]));
+}
+
+static void record_sets(const dfgks* h, double* base, SweepBuffers rec[4]) {
+    const SweepBuffers& B = h->B;
+    double* p = base;
+    for (int q = 0; q < 4; ++q) {
+        const int d = q & 1;
+        rec[q] = B;
+        rec[q].lines = p; p += (long long)LR_COUNT * B.line_stride;
+        rec[q].gp = p; p += (long long)GP_COUNT * B.gp_stride;
+        rec[q].flux[0] = rec[q].flux[1] = nullptr;
+        rec[q].flux[d] = p; p += (long long)FR_COUNT * B.flux_stride[d];
+    }
+}
+
+// Reverse pass over the checkpointed forward pass: dJ/dW0 = (dW^n/dW0)^T WT_bar.  Each segment of
+// k steps is recomputed from its checkpoint, keeping W^s, alpha^s, W* and, if they fit in
+// the memory budget, every stage's forward records; then its steps are reversed (Eq. 24 with the
+// time limiter):  W* = W + dt/2 L + dt^2/8 dL,  W' = W + dt L + dt^2/2 dL - dt^2/3 dLt + dt^2/3 dLt(W*).
+static dfgks_status backward_checkpointed(dfgks* h, const double* WT_bar, double* W0_bar) {
+    const Mesh& m = h->mesh;
+    const long long N = (long long)m.nx * m.ny, N4 = 4 * N;
+    const int n = h->ck_n, k = h->ck_k, flux = h->ck_flux, nseg = (n + k - 1) / k;
+    const double* dts = h->ck_dts;
     std::vector<double*> bufs;
     auto get = [&](long long cnt) -> double* {
         double* p = nullptr;
@@ -470,8 +570,6 @@ extern "C" dfgks_status dfgks_adjoint_steps(dfgks* h, const double* W0, int n, c
         bufs.push_back(p);
         return p;
     };
-    double* ckW = get(nseg * N4);
-    double* ckA = get(nseg * N);
     double* segW = get(k * N4);
     double* segA = get(k * N);
     double* segWs = get(k * N4);
@@ -484,51 +582,48 @@ extern "C" dfgks_status dfgks_adjoint_steps(dfgks* h, const double* W0, int n, c
     double* ATs = get(N);
     dfgks_status r = DFGKS_OK;
     for (double* p : bufs) if (!p) r = DFGKS_ENOMEM;
-    if (bufs.size() != 12) r = DFGKS_ENOMEM;
-    auto cleanup = [&]() { cudaStreamSynchronize(h->stream); for (double* p : bufs) cudaFree(p); };
-    if (r) { cleanup(); return r; }
-    // forward pass from W0 with the recorded steps, keeping a checkpoint every k steps
-    r = load_state(h, W0, nullptr, 0.0, 0, 1);
-    if (r) { cleanup(); return r; }
-    CK(cudaMemsetAsync(&h->st->halt, 0, sizeof(int), h->stream));
-    auto one_step = [&](double dt, double* Wstar) {
-        enqueue_step(h, 0, dt, flux, 0.0, h->cur, Wstar);
-        h->cur ^= 1;
-    };
-    for (int s = 0; s < n; ++s) {
-        if (s % k == 0) {
-            launch_ghosted_to_dense(m, h->W[h->cur], 4, ckW + (s / k) * N4, h->stream);
-            launch_ghosted_to_dense(m, h->A[h->cur], 1, ckA + (s / k) * N, h->stream);
-        }
-        one_step(dts[s], nullptr);
+    if (bufs.size() != 10) r = DFGKS_ENOMEM;
+    // forward records of the whole segment when they take at most half of the free memory
+    double* recs = nullptr;
+    if (r == DFGKS_OK) {
+        size_t free_b = 0, total_b = 0;
+        cudaMemGetInfo(&free_b, &total_b);
+        const double want = (double)k * (double)record_doubles_per_step(h) * sizeof(double);
+        if (want <= 0.5 * (double)free_b) recs = get((long long)k * record_doubles_per_step(h));
+        cudaGetLastError();      // a refused allocation only means recompute-in-reverse
     }
+    auto cleanup = [&]() { cudaStreamSynchronize(h->stream); for (double* p : bufs) if (p) cudaFree(p); };
+    if (r) { cleanup(); return r; }
+    r = ensure_adjoint_buffers(h);
+    if (r) { cleanup(); return r; }
     CK(cudaMemcpyAsync(h->st_host, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
-    if (h->st_host->err) { cleanup(); return DFGKS_ENONPOS; }
     const DevState stT = *h->st_host;
     launch_ghosted_to_dense(m, h->W[h->cur], 4, WTs, h->stream);
     launch_ghosted_to_dense(m, h->A[h->cur], 1, ATs, h->stream);
     CK(cudaMemcpyAsync(Wb, WT_bar, (size_t)N4 * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
     for (int seg = nseg - 1; seg >= 0 && r == DFGKS_OK; --seg) {
         const int s0 = seg * k, s1 = (s0 + k < n) ? s0 + k : n;
-        // recompute the segment from its checkpoint, keeping W^s, alpha^s and W* of every step
-        launch_dense_to_ghosted(m, ckW + seg * N4, 4, h->W[h->cur], h->stream);
-        launch_dense_to_ghosted(m, ckA + seg * N, 1, h->A[h->cur], h->stream);
+        launch_dense_to_ghosted(m, h->ck_W + (long long)seg * N4, 4, h->W[h->cur], h->stream);
+        launch_dense_to_ghosted(m, h->ck_A + (long long)seg * N, 1, h->A[h->cur], h->stream);
         for (int s = s0; s < s1; ++s) {
             launch_ghosted_to_dense(m, h->W[h->cur], 4, segW + (s - s0) * N4, h->stream);
             launch_ghosted_to_dense(m, h->A[h->cur], 1, segA + (s - s0) * N, h->stream);
-            one_step(dts[s], segWs + (s - s0) * N4);
+            SweepBuffers rec[4];
+            if (recs) record_sets(h, recs + (long long)(s - s0) * record_doubles_per_step(h), rec);
+            enqueue_step(h, 0, dts[s], flux, 0.0, h->cur, segWs + (s - s0) * N4, recs ? rec : nullptr);
+            h->cur ^= 1;
         }
-        // reverse through the segment: Eq. 24 with the time limiter,
-        //   W* = W + dt/2 L + dt^2/8 dL,  W' = W + dt L + dt^2/2 dL - dt^2/3 dLt + dt^2/3 dLt(W*)
         for (int s = s1 - 1; s >= s0 && r == DFGKS_OK; --s) {
             const double dt = dts[s], dt2 = dt * dt;
             const double* Wn = segW + (s - s0) * N4;
             const double* An = segA + (s - s0) * N;
             const double* Wst = segWs + (s - s0) * N4;
+            SweepBuffers rec[4];
+            if (recs) record_sets(h, recs + (long long)(s - s0) * record_doubles_per_step(h), rec);
             CK(cudaMemsetAsync(Wsb, 0, (size_t)N4 * sizeof(double), h->stream));
             launch_axpby(N4, dt2 / 3.0, Wb, 0.0, bdLt, h->stream);
-            r = adjoint_stage(h, Wst, An, dt, flux, nullptr, nullptr, bdLt, Wsb);
+            r = adjoint_stage(h, Wst, An, dt, flux, nullptr, nullptr, bdLt, Wsb, recs ? rec + 2 : nullptr);
             if (r) break;
             launch_axpby(N4, dt, Wb, 0.0, bL, h->stream);
             launch_axpby(N4, 0.5 * dt, Wsb, 1.0, bL, h->stream);
@@ -536,7 +631,7 @@ extern "C" dfgks_status dfgks_adjoint_steps(dfgks* h, const double* W0, int n, c
             launch_axpby(N4, 0.125 * dt2, Wsb, 1.0, bdL, h->stream);
             launch_axpby(N4, -dt2 / 3.0, Wb, 0.0, bdLt, h->stream);
             launch_axpby(N4, 1.0, Wsb, 1.0, Wb, h->stream);
-            r = adjoint_stage(h, Wn, An, dt, flux, bL, bdL, bdLt, Wb);
+            r = adjoint_stage(h, Wn, An, dt, flux, bL, bdL, bdLt, Wb, recs ? rec : nullptr);
         }
     }
     if (r == DFGKS_OK) CK(cudaMemcpyAsync(W0_bar, Wb, (size_t)N4 * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
@@ -546,8 +641,35 @@ extern "C" dfgks_status dfgks_adjoint_steps(dfgks* h, const double* W0, int n, c
     *h->st_host = stT;
     CK(cudaMemcpyAsync(h->st, h->st_host, sizeof(DevState), cudaMemcpyHostToDevice, h->stream));
     cleanup();
+    h->timer->harvest();
     CK_LAUNCH();
     return r;
+}
+
+extern "C" dfgks_status dfgks_forward_checkpointed(dfgks* h, const double* W0, int n, const double* dts_in, int flux,
+                                                   int ckpt_every, double* dts_out) {
+    if (!h || !W0 || n < 1 || ckpt_every < 1 || (flux != 0 && flux != 1)) return DFGKS_EINVAL;
+    if (h->cfg.time_scheme != DFGKS_TIME_S2O4) return DFGKS_ENOTSUP;
+    if (dts_in) for (int s = 0; s < n; ++s) if (!(dts_in[s] > 0.0)) return DFGKS_EINVAL;
+    const int k = ckpt_every < n ? ckpt_every : n;
+    dfgks_status r = forward_checkpointed(h, W0, n, dts_in, k, flux);
+    if (r == DFGKS_OK && dts_out) memcpy(dts_out, h->ck_dts, (size_t)n * sizeof(double));
+    return r;
+}
+
+extern "C" dfgks_status dfgks_adjoint_checkpointed(dfgks* h, const double* WT_bar, double* W0_bar) {
+    if (!h || !WT_bar || !W0_bar) return DFGKS_EINVAL;
+    if (h->ck_gen == 0 || h->ck_gen != h->gen) return DFGKS_EINVAL;     // no forward pass, or the state changed since
+    return backward_checkpointed(h, WT_bar, W0_bar);
+}
+
+extern "C" dfgks_status dfgks_adjoint_steps(dfgks* h, const double* W0, int n, const double* dts, int flux, int ckpt_every,
+                                            const double* WT_bar, double* W0_bar) {
+    if (!h || !W0 || !dts || !WT_bar || !W0_bar || n < 1 || ckpt_every < 1 || (flux != 0 && flux != 1))
+        return DFGKS_EINVAL;
+    dfgks_status r = dfgks_forward_checkpointed(h, W0, n, dts, flux, ckpt_every, nullptr);
+    if (r) return r;
+    return backward_checkpointed(h, WT_bar, W0_bar);
 }
 
 extern "C" dfgks_status dfgks_get_counters(dfgks* h, dfgks_counters* out) {

@@ -81,10 +81,13 @@ struct DevState {
 };
 
 // Per-face-line record of the normal reconstruction (Algorithm 1, normal step), SoA planes
+// (LR_TLK: which of the face's eight reconstructions set the limiter weight, 2k + side, or -1)
 enum LineField { LR_WL = 0, LR_WLN = 4, LR_WR = 8, LR_WRN = 12, LR_TL = 16,
-                 LR_U = 17, LR_V, LR_C, LR_IC, LR_H, LR_B1, LR_B2, LR_Q2, LR_COUNT };
-// Per-(face, side) Gauss-point record of the tangential step: m=1 {W, Wn, Wt}, m=2 {W, Wn, Wt}
-constexpr int GP_COUNT = 24;
+                 LR_U = 17, LR_V, LR_C, LR_IC, LR_H, LR_B1, LR_B2, LR_Q2, LR_TLK, LR_COUNT };
+// Per-(face, side) Gauss-point record of the tangential step: m=1 {W, Wn, Wt}, m=2 {W, Wn, Wt},
+// then GP_FB: bit m set if Gauss point m fell back to the cell average
+constexpr int GP_FB = 24;
+constexpr int GP_COUNT = 25;
 // Per-(face, Gauss point) flux record: F[4], dF[4] (global frame), alpha_{p,m}, omega^t
 enum FluxField { FR_F = 0, FR_DF = 4, FR_ALPHA = 8, FR_OMEGA = 9, FR_COUNT = 10 };
 

@@ -316,22 +316,45 @@ def adjoint_steps(sol: "Solver", W0, dts, WT_bar, ckpt_every: int = 10, flux=Non
     return out
 
 
+def forward_checkpointed(sol: "Solver", W0, nsteps: int, ckpt_every: int = 10, dts=None, flux=None):
+    """Set the state to W0 and advance nsteps S2O4 steps (CFL dt unless dts is given), keeping
+    checkpoints for adjoint_checkpointed (dfgks_forward_checkpointed).  Returns the step sizes."""
+    flux = sol.settings.flux if flux is None else flux
+    W0 = _dev(W0).contiguous()
+    out = np.zeros(int(nsteps))
+    dp = None
+    if dts is not None:
+        dts = np.ascontiguousarray(np.asarray(dts, dtype=np.float64))
+        assert dts.size == nsteps
+        dp = dts.ctypes.data_as(C.POINTER(C.c_double))
+    _lib.check(_lib.lib().dfgks_forward_checkpointed(sol._h, _ptr(W0), int(nsteps), dp, int(flux), int(ckpt_every),
+                                                     out.ctypes.data_as(C.POINTER(C.c_double))),
+               "dfgks_forward_checkpointed")
+    return out
+
+
+def adjoint_checkpointed(sol: "Solver", WT_bar) -> torch.Tensor:
+    """(dW^n/dW0)^T WT_bar through the last forward_checkpointed (dfgks_adjoint_checkpointed)."""
+    WTb = _dev(WT_bar).contiguous()
+    out = torch.zeros_like(WTb)
+    _lib.check(_lib.lib().dfgks_adjoint_checkpointed(sol._h, _ptr(WTb), _ptr(out)), "dfgks_adjoint_checkpointed")
+    return out
+
+
 class GKSRun(torch.autograd.Function):
-    """W^n = n S2O4 steps of the CUDA solver from W0 (CFL step sizes, recorded); the backward pass is
-    the hand-written adjoint with checkpointed recompute (dfgks_adjoint_steps).  alpha^0 comes from
-    W0 and the alpha sequence and branch decisions of the forward trajectory are held fixed."""
+    """W^n = n S2O4 steps of the CUDA solver from W0 (CFL step sizes); the forward pass keeps a
+    checkpoint every ckpt_every steps and the backward pass is the hand-written adjoint with
+    checkpointed recompute (dfgks_forward_checkpointed / dfgks_adjoint_checkpointed).  alpha^0 comes
+    from W0 and the alpha sequence, step sizes and branch decisions of the forward trajectory are
+    held fixed.  The solver handle must not be stepped or reset between forward and backward."""
 
     @staticmethod
     def forward(ctx, W0, sol, nsteps, ckpt_every=10):
-        W0 = W0.detach().contiguous()
-        sol.set_ic(W0)
-        done, dts = sol.step(int(nsteps), record_dts=True)
+        ctx.dts = forward_checkpointed(sol, W0.detach(), int(nsteps), int(ckpt_every))
+        ctx.sol = sol
         W, _, _, _ = sol.get_state(device=True)
-        ctx.save_for_backward(W0)
-        ctx.sol, ctx.dts, ctx.k = sol, dts, int(ckpt_every)
         return W
 
     @staticmethod
     def backward(ctx, WT_bar):
-        (W0,) = ctx.saved_tensors
-        return adjoint_steps(ctx.sol, W0, ctx.dts, WT_bar.contiguous(), ctx.k), None, None, None
+        return adjoint_checkpointed(ctx.sol, WT_bar), None, None, None

@@ -182,3 +182,27 @@ def test_c4_vortex_gradient_against_finite_differences():
                 fd = sum_rho2_difference(run_fixed(sol, Wp, dts), run_fixed(sol, Wm, dts)) / (2 * h)
                 worst = max(worst, abs(g[k, j, i] - fd))
     assert worst <= 1e-6 * np.abs(g).max(), (worst, np.abs(g).max())
+
+
+def test_checkpointed_forward_and_backward():
+    # forward_checkpointed + adjoint_checkpointed = adjoint_steps with the same step sizes; the
+    # reverse pass refuses once the state has moved on
+    from paper_2402_10914_gb300 import _lib
+    from paper_2402_10914_gb300.solver import Solver, adjoint_checkpointed, adjoint_steps, forward_checkpointed
+    w = I.random_smooth(20, 18, seed=47, flux=I.GKS, time_limiter=0)
+    s = w.settings
+    WTb = np.random.default_rng(9).normal(size=w.W0.shape)
+    with Solver(s) as sol:
+        dts = forward_checkpointed(sol, w.W0, 7, ckpt_every=3)
+        W7 = sol.get_state()[0]
+        g1 = host(adjoint_checkpointed(sol, WTb))
+        g1b = host(adjoint_checkpointed(sol, WTb))           # repeatable: the handle stays at W^7
+        W, _, _, step = sol.get_state()
+        assert step == 7 and np.array_equal(W, W7)
+        g2 = host(adjoint_steps(sol, w.W0, dts, WTb, ckpt_every=3))
+        sol.step(1)
+        with pytest.raises(_lib.DfgksError) as e:
+            adjoint_checkpointed(sol, WTb)
+        assert e.value.status == _lib.EINVAL
+    # the reverse sweep accumulates with atomics: repeated passes agree to rounding, not bitwise
+    assert comp_rel_err(g1, g2) <= 1e-11 and comp_rel_err(g1, g1b) <= 1e-11

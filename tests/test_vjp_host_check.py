@@ -21,4 +21,4 @@ def test_reverse_products_match_finite_differences(tmp_path):
     r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
     print(r.stdout)
     assert r.returncode == 0, r.stdout
-    assert r.stdout.count(" ok") >= 8
+    assert r.stdout.count(" ok") >= 10

@@ -106,8 +106,28 @@ int main() {
     }
     report("project", worst, 1e-6);
     report("back_project", worst2, 1e-6);
+    // back_project_T + back_project_basis_vjp = back_project_vjp
+    {
+        double split = 0;
+        for (int t = 0; t < 5; ++t) {
+            double Wl[4], Wr[4], q[4], wb[4];
+            state(Wl); state(Wr);
+            CharBasis B = make_basis(Wl, Wr, S);
+            for (int i = 0; i < 4; ++i) { q[i] = U(-1, 1); wb[i] = U(-1, 1); }
+            double qa[4] = {0, 0, 0, 0}, qc[4] = {0, 0, 0, 0};
+            BasisBar A, C; basis_bar_zero(A); basis_bar_zero(C);
+            back_project_vjp(B, q, wb, qa, A);
+            back_project_T(B, wb, qc);
+            back_project_basis_vjp(B, q, wb, C);
+            double av[12] = {qa[0], qa[1], qa[2], qa[3], A.u, A.v, A.c, A.ic, A.H, A.b1, A.b2, A.q2};
+            double cv[12] = {qc[0], qc[1], qc[2], qc[3], C.u, C.v, C.c, C.ic, C.H, C.b1, C.b2, C.q2};
+            for (int i = 0; i < 12; ++i) split = std::fmax(split, std::fabs(av[i] - cv[i]) / std::fmax(std::fabs(av[i]), 1e-12));
+        }
+        report("back_project split", split, 1e-13);
+    }
     // WENO-AO and its evaluations: q[5] -> (edge value, edge slope, gauss values/slopes, limiter)
     worst = 0;
+    double worst_tape = 0;
     for (int t = 0; t < 40; ++t) {
         double x[5];
         double amp = (t % 4 == 0) ? 1e-3 : (t % 4 == 1 ? 1.0 : 0.1);
@@ -119,16 +139,23 @@ int main() {
             y[6] = limiter_alpha(o);
         };
         auto g = [&](const double* q, const double* yb, double* qb) {
-            AO o = weno_ao(q, S);
+            AOTape T;
+            AO o = weno_ao_tape(q, S, T);
             AOBar ob; ao_bar_zero(ob);
             ao_at_right_edge_vjp(yb[0], yb[1], qb[2], ob);
             ao_at_gauss_vjp(yb + 2, yb + 4, qb[2], ob);
             limiter_alpha_vjp(o, yb[6], ob);
-            weno_ao_vjp(q, S, ob, qb);
+            weno_ao_tape_vjp(T, S, ob, qb);
         };
         worst = std::fmax(worst, check(5, 7, x, f, g));
+        // the taped forward evaluates the same reconstruction as weno_ao
+        AOTape T;
+        AO a = weno_ao(x, S), b = weno_ao_tape(x, S, T);
+        const double av[6] = {a.A1, a.A2, a.c3a3, a.c3a4, a.rmax, a.rmin}, bv[6] = {b.A1, b.A2, b.c3a3, b.c3a4, b.rmax, b.rmin};
+        for (int i = 0; i < 6; ++i) worst_tape = std::fmax(worst_tape, std::fabs(av[i] - bv[i]) / std::fmax(std::fabs(av[i]), 1e-300));
     }
     report("weno_ao + evaluations", worst, 1e-5);
+    report("weno_ao_tape forward", worst_tape, 1e-12);
     // DF quadratic
     worst = 0;
     for (int t = 0; t < 5; ++t) {
