@@ -160,8 +160,9 @@ DFGKS_API dfgks_status dfgks_adjoint_residual(dfgks* h, const double* W, const d
 /* Forward pass for a later gradient: sets the state to W0 (device, dense; alpha^0 computed from W0
  * as in dfgks_set_ic, t = 0) and advances n S2O4 steps of flux `flux`, with the step sizes dts_in[n]
  * (host) or, if dts_in is NULL, the CFL rule; dts_out[n] (host, may be NULL) receives them.  Keeps W
- * and alpha every ckpt_every steps and the step sizes in the handle (allocated on demand, freed
- * by dfgks_destroy) for dfgks_adjoint_checkpointed.  Not part of the paper.  S2O4 only
+ * and alpha every ckpt_every steps, the step sizes, and the last segment's stage states and (if they
+ * fit in half of the free device memory) its sweep records and tapes, in the handle (allocated on
+ * demand, freed by dfgks_destroy) for dfgks_adjoint_checkpointed.  Not part of the paper.  S2O4 only
  * (DFGKS_ENOTSUP otherwise); DFGKS_ENONPOS if the trajectory loses positivity.  Synchronises. */
 DFGKS_API dfgks_status dfgks_forward_checkpointed(dfgks* h, const double* W0, int n, const double* dts_in, int flux,
                                                   int ckpt_every, double* dts_out);
@@ -169,8 +170,10 @@ DFGKS_API dfgks_status dfgks_forward_checkpointed(dfgks* h, const double* W0, in
 /* Gradient through the steps of the last dfgks_forward_checkpointed (Eq. 24 with the time
  * limiter): W0_bar = (dW^n/dW0)^T WT_bar, both device, dense [4][ny][nx], with the alpha sequence,
  * step sizes and branch decisions of the forward trajectory held fixed.  Each segment of
- * ckpt_every steps is recomputed from its checkpoint, keeping its stage states and (if they take at
- * most half of the free device memory) every stage's forward sweep records, and then reversed.
+ * ckpt_every steps is recomputed from its checkpoint (the last one only if the forward pass could not
+ * keep it), keeping its stage states and (if they take at most half of the free device memory) every
+ * stage's forward sweep records with the reconstructions' and GKS flux's intermediates, and then
+ * reversed.
  * DFGKS_EINVAL if no forward pass was kept or the state changed since (set_ic, set_state, step).
  * Allocates its segment buffers for the call.  Leaves the handle at W^n.  Synchronises. */
 DFGKS_API dfgks_status dfgks_adjoint_checkpointed(dfgks* h, const double* WT_bar, double* W0_bar);

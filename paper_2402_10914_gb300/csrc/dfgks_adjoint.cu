@@ -4,9 +4,12 @@
 // three kernels walk that direction's sweep backwards:
 //   ka_flux  : one thread per Gauss point.  Face adjoints from the cells' L, dL/dt and limited
 //              dL/dt adjoints (Eq. 2 with A_m = 1/2), then the GKS / L-F flux adjoint into the
-//              Gauss-point record adjoints, and the time-limiter weight's adjoint.
+//              Gauss-point record adjoints, and the time-limiter weight's adjoint.  When the
+//              forward sweep taped the GKS flux's intermediates, its reverse reads them instead
+//              of recomputing the flux.
 //   ka_faces : one thread per face side.  Evaluates each tangential reconstruction once, with its
-//              intermediates kept for its reverse, and scatters (atomically) into the adjoints of
+//              intermediates kept for its reverse (or reads them from the forward sweep's tape),
+//              and scatters (atomically) into the adjoints of
 //              the five face lines and of the face basis; a Gauss point that fell back to the cell
 //              average (flagged in the forward record) sends its adjoint to that cell.
 //   ka_lines : one thread per face line.  The same for the eight normal reconstructions and the
@@ -27,10 +30,12 @@ DFK_HD void aadd(double* p, double v) {
 #endif
 }
 
-template <int DIR, int FLUX>
+// TAPED: the GKS forward intermediates are read from the tape the forward sweep wrote
+template <int DIR, int FLUX, bool TAPED = false>
 DFK_HD void ka_flux_body(const Mesh& m, const SchemeConsts& S, const AdjointArgs& a, const double* __restrict__ gp,
                          long long gs, const double* __restrict__ fr, long long fs, double dt, double* __restrict__ lb,
-                         long long ls, double* __restrict__ gb, int ax, int ay, int mm) {
+                         long long ls, double* __restrict__ gb, int ax, int ay, int mm,
+                         double* __restrict__ tape = nullptr) {
     Geo<DIR> g(m);
     int f = DIR == 0 ? ax : ay;
     int t = DIR == 0 ? ay : ax;
@@ -79,7 +84,8 @@ DFK_HD void ka_flux_body(const Mesh& m, const SchemeConsts& S, const AdjointArgs
     }
     GPStateBar Lbar, Rbar;
     for (int k = 0; k < 4; ++k) { Lbar.W[k] = Lbar.Wn[k] = Lbar.Wt[k] = Rbar.W[k] = Rbar.Wn[k] = Rbar.Wt[k] = 0.0; }
-    if (FLUX == 0) gks_flux_vjp(L, R, dt, S, Fb, dFb, Lbar, Rbar);
+    if (FLUX == 0 && TAPED) gks_flux_reverse(PlaneTape{tape + (long long)mm * nf + fid, fs}, L, R, dt, S, Fb, dFb, Lbar, Rbar);
+    else if (FLUX == 0) gks_flux_vjp(L, R, dt, S, Fb, dFb, Lbar, Rbar);
     else lf_flux_vjp(L, R, S, Fb, dFb, Lbar, Rbar);
     for (int k = 0; k < 4; ++k) {
         gb[(mm * 12 + k) * gs + eL] = Lbar.W[k];
@@ -91,11 +97,12 @@ DFK_HD void ka_flux_body(const Mesh& m, const SchemeConsts& S, const AdjointArgs
     }
 }
 
-template <int DIR>
+// TAPED: the tangential reconstructions' intermediates are read from the tape the forward sweep wrote
+template <int DIR, bool TAPED = false>
 DFK_HD void ka_faces_body(const Mesh& m, const SchemeConsts& S, const double* __restrict__ alpha,
                           const double* __restrict__ lines, long long ls, const double* __restrict__ gp,
                           const double* __restrict__ gb, long long gs, double* __restrict__ lb,
-                          double* __restrict__ Wb, int ax, int ay, int side) {
+                          double* __restrict__ Wb, int ax, int ay, int side, double* __restrict__ ftape = nullptr) {
     Geo<DIR> g(m);
     int f = DIR == 0 ? ax : ay;
     int t = DIR == 0 ? ay : ax;
@@ -154,14 +161,23 @@ DFK_HD void ka_faces_body(const Mesh& m, const SchemeConsts& S, const double* __
         if (df) {
             df_at_gauss(sq, al[1], v, sl);
             df_at_gauss_vjp(al[1], vb, sb, qb);
-        } else {
-            AOTape T;
-            AO o = weno_ao_tape(sq, S, T);
+        } else if (TAPED) {
+            const PlaneTape T{ftape + e, gs};
+            AO o = ao_from_tape(T, k * AT_COUNT, S);
             ao_at_gauss(o, sq[2], v, sl);
             AOBar ob;
             ao_bar_zero(ob);
             ao_at_gauss_vjp(vb, sb, qb[2], ob);
-            weno_ao_tape_vjp(T, S, ob, qb);
+            weno_ao_rev(T, k * AT_COUNT, S, ob, qb);
+        } else {
+            double tb[AT_COUNT];
+            const ArrayTape T{tb};
+            AO o = weno_ao_t(sq, S, T, 0);
+            ao_at_gauss(o, sq[2], v, sl);
+            AOBar ob;
+            ao_bar_zero(ob);
+            ao_at_gauss_vjp(vb, sb, qb[2], ob);
+            weno_ao_rev(T, 0, S, ob, qb);
         }
         qv[0][k] = v[0]; qv[1][k] = v[1];
         qt[0][k] = sl[0] * idt; qt[1][k] = sl[1] * idt;
@@ -184,10 +200,12 @@ DFK_HD void ka_faces_body(const Mesh& m, const SchemeConsts& S, const double* __
     aadd(&lb[LR_B2 * ls + l0], Bb.b2); aadd(&lb[LR_Q2 * ls + l0], Bb.q2);
 }
 
-template <int DIR>
+// TAPED: the normal reconstructions' intermediates are read from the tape the forward sweep wrote
+template <int DIR, bool TAPED = false>
 DFK_HD void ka_lines_body(const Mesh& m, const SchemeConsts& S, const double* __restrict__ W,
                           const double* __restrict__ alpha, const double* __restrict__ lines,
-                          const double* __restrict__ lb, long long ls, double* __restrict__ Wb, int ax, int ay) {
+                          const double* __restrict__ lb, long long ls, double* __restrict__ Wb, int ax, int ay,
+                          double* __restrict__ ltape = nullptr) {
     Geo<DIR> g(m);
     int f = DIR == 0 ? ax : ay;
     int tt = DIR == 0 ? ay : ax;
@@ -239,8 +257,11 @@ DFK_HD void ka_lines_body(const Mesh& m, const SchemeConsts& S, const double* __
             const bool lim = tlk == 2 * k + sd && tlb != 0.0;
             double v = 0.0, sl = 0.0, qb[5] = {0, 0, 0, 0, 0};
             if (!dfs || lim) {
-                AOTape T;
-                AO o = weno_ao_tape(sq, S, T);
+                double tb[AT_COUNT];
+                const int base = TAPED ? (2 * k + sd) * AT_COUNT : 0;
+                const PlaneTape PT{ltape + (TAPED ? li : 0), ls};
+                const ArrayTape AT{tb};
+                AO o = TAPED ? ao_from_tape(PT, base, S) : weno_ao_t(sq, S, AT, 0);
                 AOBar ob;
                 ao_bar_zero(ob);
                 if (!dfs) {
@@ -248,7 +269,8 @@ DFK_HD void ka_lines_body(const Mesh& m, const SchemeConsts& S, const double* __
                     ao_at_right_edge_vjp(vb, sb, qb[2], ob);
                 }
                 if (lim) limiter_alpha_vjp(o, tlb, ob);
-                weno_ao_tape_vjp(T, S, ob, qb);
+                if (TAPED) weno_ao_rev(PT, base, S, ob, qb);
+                else weno_ao_rev(AT, 0, S, ob, qb);
             }
             if (dfs) {
                 df_at_right_edge(sq, as, v, sl);
@@ -314,30 +336,32 @@ DFK_HD void ka_accumulate_body(const Mesh& m, const double* __restrict__ Wbg, do
 }
 
 // ---- kernels: one thread per body invocation ----
-template <int DIR, int FLUX>
+template <int DIR, int FLUX, bool TAPED = false>
 __global__ void __launch_bounds__(128) ka_flux(Mesh m, SchemeConsts S, AdjointArgs a, const double* __restrict__ gp,
                                                long long gs, const double* __restrict__ fr, long long fs,
                                                const double* dtp, double* __restrict__ lb, long long ls,
-                                               double* __restrict__ gb) {
-    ka_flux_body<DIR, FLUX>(m, S, a, gp, gs, fr, fs, *dtp, lb, ls, gb, blockIdx.x * blockDim.x + threadIdx.x,
-                            blockIdx.y * blockDim.y + threadIdx.y, blockIdx.z);
+                                               double* __restrict__ gb, double* __restrict__ tape = nullptr) {
+    ka_flux_body<DIR, FLUX, TAPED>(m, S, a, gp, gs, fr, fs, *dtp, lb, ls, gb, blockIdx.x * blockDim.x + threadIdx.x,
+                                   blockIdx.y * blockDim.y + threadIdx.y, blockIdx.z, tape);
 }
 
-template <int DIR>
+template <int DIR, bool TAPED>
 __global__ void __launch_bounds__(128) ka_faces(Mesh m, SchemeConsts S, const double* __restrict__ alpha,
                                                 const double* __restrict__ lines, long long ls,
                                                 const double* __restrict__ gp, const double* __restrict__ gb,
-                                                long long gs, double* __restrict__ lb, double* __restrict__ Wb) {
-    ka_faces_body<DIR>(m, S, alpha, lines, ls, gp, gb, gs, lb, Wb, blockIdx.x * blockDim.x + threadIdx.x,
-                       blockIdx.y * blockDim.y + threadIdx.y, blockIdx.z);
+                                                long long gs, double* __restrict__ lb, double* __restrict__ Wb,
+                                                double* __restrict__ ftape) {
+    ka_faces_body<DIR, TAPED>(m, S, alpha, lines, ls, gp, gb, gs, lb, Wb, blockIdx.x * blockDim.x + threadIdx.x,
+                              blockIdx.y * blockDim.y + threadIdx.y, blockIdx.z, ftape);
 }
 
-template <int DIR>
+template <int DIR, bool TAPED>
 __global__ void __launch_bounds__(128) ka_lines(Mesh m, SchemeConsts S, const double* __restrict__ W,
                                                 const double* __restrict__ alpha, const double* __restrict__ lines,
-                                                const double* __restrict__ lb, long long ls, double* __restrict__ Wb) {
-    ka_lines_body<DIR>(m, S, W, alpha, lines, lb, ls, Wb, blockIdx.x * blockDim.x + threadIdx.x,
-                       blockIdx.y * blockDim.y + threadIdx.y);
+                                                const double* __restrict__ lb, long long ls, double* __restrict__ Wb,
+                                                double* __restrict__ ltape) {
+    ka_lines_body<DIR, TAPED>(m, S, W, alpha, lines, lb, ls, Wb, blockIdx.x * blockDim.x + threadIdx.x,
+                              blockIdx.y * blockDim.y + threadIdx.y, ltape);
 }
 
 __global__ void ka_fold_y(Mesh m, double* Wb) { ka_fold_y_body(m, Wb, blockIdx.x * blockDim.x + threadIdx.x - G); }
@@ -358,16 +382,25 @@ static void adjoint_dir(const Mesh& m, const SchemeConsts& S, int flux, const Ad
     dim3 gl((lx + 31) / 32, (ly + 3) / 4);
     cudaMemsetAsync(lb, 0, sizeof(double) * LR_COUNT * B.line_stride, s);
     if (T) T->begin(KK_FLUX);
-    if (flux == 0)
+    if (flux == 0 && B.tape[DIR])
+        ka_flux<DIR, 0, true><<<gf, blk, 0, s>>>(m, S, a, B.gp, B.gp_stride, B.flux[DIR], B.flux_stride[DIR], dtp, lb,
+                                                 B.line_stride, gbuf, B.tape[DIR]);
+    else if (flux == 0)
         ka_flux<DIR, 0><<<gf, blk, 0, s>>>(m, S, a, B.gp, B.gp_stride, B.flux[DIR], B.flux_stride[DIR], dtp, lb,
                                            B.line_stride, gbuf);
     else
         ka_flux<DIR, 1><<<gf, blk, 0, s>>>(m, S, a, B.gp, B.gp_stride, B.flux[DIR], B.flux_stride[DIR], dtp, lb,
                                            B.line_stride, gbuf);
     if (T) { T->end(KK_FLUX, 1); T->begin(KK_FACES); }
-    ka_faces<DIR><<<gf, blk, 0, s>>>(m, S, alpha, B.lines, B.line_stride, B.gp, gbuf, B.gp_stride, lb, Wb);
+    if (B.ftape)
+        ka_faces<DIR, true><<<gf, blk, 0, s>>>(m, S, alpha, B.lines, B.line_stride, B.gp, gbuf, B.gp_stride, lb, Wb, B.ftape);
+    else
+        ka_faces<DIR, false><<<gf, blk, 0, s>>>(m, S, alpha, B.lines, B.line_stride, B.gp, gbuf, B.gp_stride, lb, Wb, nullptr);
     if (T) { T->end(KK_FACES, 1); T->begin(KK_LINES); }
-    ka_lines<DIR><<<gl, blk, 0, s>>>(m, S, W, alpha, B.lines, lb, B.line_stride, Wb);
+    if (B.ltape)
+        ka_lines<DIR, true><<<gl, blk, 0, s>>>(m, S, W, alpha, B.lines, lb, B.line_stride, Wb, B.ltape);
+    else
+        ka_lines<DIR, false><<<gl, blk, 0, s>>>(m, S, W, alpha, B.lines, lb, B.line_stride, Wb, nullptr);
     if (T) T->end(KK_LINES, 1);
 }
 

@@ -125,92 +125,57 @@ struct AOBar { double A1, A2, c3a3, c3a4, rmax, rmin; };
 
 DFK_HD void ao_bar_zero(AOBar& b) { b.A1 = b.A2 = b.c3a3 = b.c3a4 = b.rmax = b.rmin = 0.0; }
 
-// WENO-AO with the intermediates its reverse needs kept, so that a reverse sweep evaluates each
-// reconstruction once: the forward values of weno_ao (up to the rounding of the ratios, which
-// here go through 1/(beta_k + eps)) and a tape for weno_ao_tape_vjp.
-struct AOTape {
-    double a1[4], a2[4], a3, a4;   // sub-stencil linear/quadratic coefficients, the quartic's a3, a4
-    double ie[4];                  // 1 / (beta_k + eps)
-    double r[4], w[4], iw, c3;     // tau/(beta_k+eps), unnormalised weights, 1/sum w, c_3
-    double sg[3];                  // sign(beta_3 - beta_k), k < 3
-    int kmax, kmin;                // first indices attaining max / min of r
-};
-
-DFK_HD AO weno_ao_tape(const double q[5], const SchemeConsts& S, AOTape& T) {
-    const double qm2 = q[0], qm1 = q[1], q0 = q[2], q1 = q[3], q2 = q[4];
-    T.a1[0] = 0.5 * qm2 - 2.0 * qm1 + 1.5 * q0;
-    T.a2[0] = 0.5 * (qm2 - 2.0 * qm1 + q0);
-    T.a1[1] = 0.5 * (q1 - qm1);
-    T.a2[1] = 0.5 * (qm1 - 2.0 * q0 + q1);
-    T.a1[2] = -1.5 * q0 + 2.0 * q1 - 0.5 * q2;
-    T.a2[2] = 0.5 * (q0 - 2.0 * q1 + q2);
-    T.a1[3] = (5.0 * (qm2 - q2) - 34.0 * (qm1 - q1)) * (1.0 / 48.0);
-    T.a2[3] = (-(qm2 + q2) + 12.0 * (qm1 + q1) - 22.0 * q0) * (1.0 / 16.0);
-    T.a3 = (-(qm2 - q2) + 2.0 * (qm1 - q1)) * (1.0 / 12.0);
-    T.a4 = ((qm2 + q2) - 4.0 * (qm1 + q1) + 6.0 * q0) * (1.0 / 24.0);
-    const double c13_3 = 13.0 / 3.0;
-    double b[4];
-    for (int k = 0; k < 3; ++k) b[k] = T.a1[k] * T.a1[k] + c13_3 * T.a2[k] * T.a2[k];
-    b[3] = T.a1[3] * (T.a1[3] + 0.5 * T.a3) + c13_3 * T.a2[3] * T.a2[3] + (21.0 / 5.0) * T.a2[3] * T.a4
-         + (3129.0 / 80.0) * T.a3 * T.a3 + (87617.0 / 140.0) * T.a4 * T.a4;
-    double tau = (fabs(b[3] - b[0]) + fabs(b[3] - b[1]) + fabs(b[3] - b[2])) * (1.0 / 3.0);
-    for (int k = 0; k < 3; ++k) T.sg[k] = (b[3] - b[k]) >= 0.0 ? 1.0 : -1.0;
-    double e0 = b[0] + S.eps, e1 = b[1] + S.eps, e2 = b[2] + S.eps, e3 = b[3] + S.eps;
-    double p01 = e0 * e1, p23 = e2 * e3, prod = p01 * p23;
-    if (prod < 1e300) {                                  // one division for the four reciprocals
-        double ip = 1.0 / prod;
-        T.ie[0] = (e1 * p23) * ip; T.ie[1] = (e0 * p23) * ip; T.ie[2] = (p01 * e3) * ip; T.ie[3] = (p01 * e2) * ip;
-    } else {
-        T.ie[0] = 1.0 / e0; T.ie[1] = 1.0 / e1; T.ie[2] = 1.0 / e2; T.ie[3] = 1.0 / e3;
-    }
-    double wsum = 0.0;
-    for (int k = 0; k < 4; ++k) { T.r[k] = tau * T.ie[k]; T.w[k] = S.d[k] * (1.0 + T.r[k] * T.r[k]); wsum += T.w[k]; }
-    T.iw = 1.0 / wsum;
-    T.c3 = T.w[3] * T.iw * S.inv_d3;
-    T.kmax = 0; T.kmin = 0;
-    for (int k = 1; k < 4; ++k) { if (T.r[k] > T.r[T.kmax]) T.kmax = k; if (T.r[k] < T.r[T.kmin]) T.kmin = k; }
+// The outputs of a taped WENO-AO reconstruction (weno_ao_t), rebuilt from its tape
+template <class Tape>
+DFK_HD AO ao_from_tape(const Tape& tp, int base, const SchemeConsts& S) {
+    const double iw = tp.get(base + AT_IW), c3 = tp.get(base + AT_C3);
+    const double c0 = tp.get(base + AT_W) * iw - c3 * S.d[0], c1 = tp.get(base + AT_W + 1) * iw - c3 * S.d[1];
+    const double c2 = tp.get(base + AT_W + 2) * iw - c3 * S.d[2];
     AO o;
-    o.A1 = T.c3 * T.a1[3];
-    o.A2 = T.c3 * T.a2[3];
-    for (int k = 0; k < 3; ++k) {
-        double ck = T.w[k] * T.iw - T.c3 * S.d[k];
-        o.A1 += ck * T.a1[k];
-        o.A2 += ck * T.a2[k];
-    }
-    o.c3a3 = T.c3 * T.a3;
-    o.c3a4 = T.c3 * T.a4;
-    o.rmax = T.r[T.kmax];
-    o.rmin = T.r[T.kmin];
+    o.A1 = c0 * tp.get(base + AT_A1) + c1 * tp.get(base + AT_A1 + 1) + c2 * tp.get(base + AT_A1 + 2) + c3 * tp.get(base + AT_A1 + 3);
+    o.A2 = c0 * tp.get(base + AT_A2) + c1 * tp.get(base + AT_A2 + 1) + c2 * tp.get(base + AT_A2 + 2) + c3 * tp.get(base + AT_A2 + 3);
+    o.c3a3 = c3 * tp.get(base + AT_A3);
+    o.c3a4 = c3 * tp.get(base + AT_A4);
+    o.rmax = tp.get(base + AT_R + (int)tp.get(base + AT_KMAX));
+    o.rmin = tp.get(base + AT_R + (int)tp.get(base + AT_KMIN));
     return o;
 }
 
-DFK_HD void weno_ao_tape_vjp(const AOTape& T, const SchemeConsts& S, const AOBar& ob, double qb[5]) {
+// reverse of weno_ao_t from its tape: qb += (d AO / d q)^T ob
+template <class Tape>
+DFK_HD void weno_ao_rev(const Tape& tp, int base, const SchemeConsts& S, const AOBar& ob, double qb[5]) {
     const double c13_3 = 13.0 / 3.0;
+    double a1[4], a2[4], w[4], r[4], ie[4];
+    for (int k = 0; k < 4; ++k) {
+        a1[k] = tp.get(base + AT_A1 + k); a2[k] = tp.get(base + AT_A2 + k);
+        w[k] = tp.get(base + AT_W + k); r[k] = tp.get(base + AT_R + k); ie[k] = tp.get(base + AT_IE + k);
+    }
+    const double a3 = tp.get(base + AT_A3), a4 = tp.get(base + AT_A4), iw = tp.get(base + AT_IW), c3 = tp.get(base + AT_C3);
     double c[4];
-    for (int k = 0; k < 3; ++k) c[k] = T.w[k] * T.iw - T.c3 * S.d[k];
-    c[3] = T.c3;
+    for (int k = 0; k < 3; ++k) c[k] = w[k] * iw - c3 * S.d[k];
+    c[3] = c3;
     double a1b[4], a2b[4], cb[4];
-    for (int k = 0; k < 4; ++k) { a1b[k] = ob.A1 * c[k]; a2b[k] = ob.A2 * c[k]; cb[k] = ob.A1 * T.a1[k] + ob.A2 * T.a2[k]; }
-    cb[3] += ob.c3a3 * T.a3 + ob.c3a4 * T.a4;
-    double a3b = ob.c3a3 * T.c3, a4b = ob.c3a4 * T.c3;
+    for (int k = 0; k < 4; ++k) { a1b[k] = ob.A1 * c[k]; a2b[k] = ob.A2 * c[k]; cb[k] = ob.A1 * a1[k] + ob.A2 * a2[k]; }
+    cb[3] += ob.c3a3 * a3 + ob.c3a4 * a4;
+    double a3b = ob.c3a3 * c3, a4b = ob.c3a4 * c3;
     double wb[4], iwb = 0.0;
-    for (int k = 0; k < 3; ++k) { wb[k] = cb[k] * T.iw; iwb += cb[k] * T.w[k]; cb[3] -= cb[k] * S.d[k]; }
-    wb[3] = cb[3] * T.iw * S.inv_d3;
-    iwb += cb[3] * T.w[3] * S.inv_d3;
-    const double sumb = -iwb * T.iw * T.iw;
+    for (int k = 0; k < 3; ++k) { wb[k] = cb[k] * iw; iwb += cb[k] * w[k]; cb[3] -= cb[k] * S.d[k]; }
+    wb[3] = cb[3] * iw * S.inv_d3;
+    iwb += cb[3] * w[3] * S.inv_d3;
+    const double sumb = -iwb * iw * iw;
     double rb[4];
-    for (int k = 0; k < 4; ++k) rb[k] = (wb[k] + sumb) * S.d[k] * 2.0 * T.r[k];
-    rb[T.kmax] += ob.rmax;
-    rb[T.kmin] += ob.rmin;
+    for (int k = 0; k < 4; ++k) rb[k] = (wb[k] + sumb) * S.d[k] * 2.0 * r[k];
+    rb[(int)tp.get(base + AT_KMAX)] += ob.rmax;
+    rb[(int)tp.get(base + AT_KMIN)] += ob.rmin;
     double taub = 0.0, bb[4];
-    for (int k = 0; k < 4; ++k) { double t = rb[k] * T.ie[k]; taub += t; bb[k] = -t * T.r[k]; }
+    for (int k = 0; k < 4; ++k) { double t = rb[k] * ie[k]; taub += t; bb[k] = -t * r[k]; }
     const double tb3 = taub * (1.0 / 3.0);
-    for (int k = 0; k < 3; ++k) { bb[3] += tb3 * T.sg[k]; bb[k] -= tb3 * T.sg[k]; }
-    for (int k = 0; k < 3; ++k) { a1b[k] += bb[k] * 2.0 * T.a1[k]; a2b[k] += bb[k] * 2.0 * c13_3 * T.a2[k]; }
-    a1b[3] += bb[3] * (2.0 * T.a1[3] + 0.5 * T.a3);
-    a3b += bb[3] * (0.5 * T.a1[3] + 2.0 * (3129.0 / 80.0) * T.a3);
-    a2b[3] += bb[3] * (2.0 * c13_3 * T.a2[3] + (21.0 / 5.0) * T.a4);
-    a4b += bb[3] * ((21.0 / 5.0) * T.a2[3] + 2.0 * (87617.0 / 140.0) * T.a4);
+    for (int k = 0; k < 3; ++k) { const double sg = tp.get(base + AT_SG + k); bb[3] += tb3 * sg; bb[k] -= tb3 * sg; }
+    for (int k = 0; k < 3; ++k) { a1b[k] += bb[k] * 2.0 * a1[k]; a2b[k] += bb[k] * 2.0 * c13_3 * a2[k]; }
+    a1b[3] += bb[3] * (2.0 * a1[3] + 0.5 * a3);
+    a3b += bb[3] * (0.5 * a1[3] + 2.0 * (3129.0 / 80.0) * a3);
+    a2b[3] += bb[3] * (2.0 * c13_3 * a2[3] + (21.0 / 5.0) * a4);
+    a4b += bb[3] * ((21.0 / 5.0) * a2[3] + 2.0 * (87617.0 / 140.0) * a4);
     qb[0] += 0.5 * a1b[0] + 0.5 * a2b[0] + (5.0 / 48.0) * a1b[3] - (1.0 / 16.0) * a2b[3] - (1.0 / 12.0) * a3b + (1.0 / 24.0) * a4b;
     qb[1] += -2.0 * a1b[0] - a2b[0] - 0.5 * a1b[1] + 0.5 * a2b[1] - (34.0 / 48.0) * a1b[3] + (12.0 / 16.0) * a2b[3]
            + (2.0 / 12.0) * a3b - (4.0 / 24.0) * a4b;
@@ -354,33 +319,68 @@ DFK_HD void psi_mom_vjp(const Mom& m, const double ob[4], MomBar& mb) {
     M_vjp<k, l, c + 1>(m, 0.5 * ob[3], mb);
 }
 
+// adjoint of the factorised a_mom (see its comment): ab += d out/d a ^T ob, moment adjoints accumulated
 template <int k, int l>
 DFK_HD void a_mom_vjp(const Mom& m, const double a[4], const double ob[4], MomBar& mb, double ab[4]) {
-    double t0[4], t1[4], t2[4], t3[4], t4[4], t5[4];
-    psi_mom<k, l, 0>(m, t0);
-    psi_mom<k + 1, l, 0>(m, t1);
-    psi_mom<k, l + 1, 0>(m, t2);
-    psi_mom<k + 2, l, 0>(m, t3);
-    psi_mom<k, l + 2, 0>(m, t4);
-    psi_mom<k, l, 1>(m, t5);
-    double h = 0.5 * a[3];
-    double tb[4];
-    for (int i = 0; i < 4; ++i) {
-        ab[0] += ob[i] * t0[i];
-        ab[1] += ob[i] * t1[i];
-        ab[2] += ob[i] * t2[i];
-        ab[3] += 0.5 * ob[i] * (t3[i] + t4[i] + t5[i]);
+    const double* mu = m.mu;
+    const double* mv = m.mv;
+    const double h = 0.5 * a[3], x1 = m.mx[1], x2 = m.mx[2], hx1 = h * x1;
+    double P[3], Qp[3];
+    for (int j = 0; j < 3; ++j) {
+        P[j] = a[0] * mu[k + j] + a[1] * mu[k + j + 1] + h * mu[k + j + 2];
+        Qp[j] = a[2] * mv[l + j + 1] + h * mv[l + j + 2] + hx1 * mv[l + j];
     }
-    for (int i = 0; i < 4; ++i) tb[i] = ob[i] * a[0];
-    psi_mom_vjp<k, l, 0>(m, tb, mb);
-    for (int i = 0; i < 4; ++i) tb[i] = ob[i] * a[1];
-    psi_mom_vjp<k + 1, l, 0>(m, tb, mb);
-    for (int i = 0; i < 4; ++i) tb[i] = ob[i] * a[2];
-    psi_mom_vjp<k, l + 1, 0>(m, tb, mb);
-    for (int i = 0; i < 4; ++i) tb[i] = ob[i] * h;
-    psi_mom_vjp<k + 2, l, 0>(m, tb, mb);
-    psi_mom_vjp<k, l + 2, 0>(m, tb, mb);
-    psi_mom_vjp<k, l, 1>(m, tb, mb);
+    const double Ql = a[2] * mv[l + 1] + h * mv[l + 2];
+    const double g0 = ob[0], g1 = ob[1], g2 = ob[2], g3 = 0.5 * ob[3];
+    double Pb[3] = {0.0, 0.0, 0.0}, Qpb[3] = {0.0, 0.0, 0.0}, Qlb = 0.0, hb = 0.0;
+    // out0 = mv_l P0 + mu_k Qp0, out1 = mv_l P1 + mu_{k+1} Qp0, out2 = mv_{l+1} P0 + mu_k Qp1
+    mb.mv[l] += g0 * P[0] + g1 * P[1] + g3 * P[2];
+    mb.mu[k] += g0 * Qp[0] + g2 * Qp[1] + g3 * Qp[2];
+    mb.mu[k + 1] += g1 * Qp[0];
+    mb.mv[l + 1] += g2 * P[0];
+    Pb[0] += g0 * mv[l] + g2 * mv[l + 1] + g3 * mv[l + 2];
+    Pb[1] += g1 * mv[l];
+    Pb[2] += g3 * mv[l];
+    Qpb[0] += g0 * mu[k] + g1 * mu[k + 1] + g3 * mu[k + 2];
+    Qpb[1] += g2 * mu[k];
+    Qpb[2] += g3 * mu[k];
+    // out3 / 2 = G(k+2,l,0) + G(k,l+2,0) + G(k,l,1): the first two above, then
+    // G(k,l,1) = x1 (mv_l P0 + mu_k Ql) + h mu_k mv_l x2
+    mb.mu[k + 2] += g3 * Qp[0];
+    mb.mv[l + 2] += g3 * P[0];
+    {
+        const double gi = g3 * x1, t = g3 * h * x2;
+        mb.mx[1] += g3 * (mv[l] * P[0] + mu[k] * Ql);
+        mb.mv[l] += gi * P[0] + t * mu[k];
+        mb.mu[k] += gi * Ql + t * mv[l];
+        mb.mx[2] += g3 * h * mu[k] * mv[l];
+        Pb[0] += gi * mv[l];
+        Qlb += gi * mu[k];
+        hb += g3 * mu[k] * mv[l] * x2;
+    }
+    // Qp_j = a2 mv_{l+j+1} + h mv_{l+j+2} + h x1 mv_{l+j},  Ql = a2 mv_{l+1} + h mv_{l+2}
+    for (int j = 0; j < 3; ++j) {
+        ab[2] += Qpb[j] * mv[l + j + 1];
+        hb += Qpb[j] * (mv[l + j + 2] + x1 * mv[l + j]);
+        mb.mv[l + j + 1] += Qpb[j] * a[2];
+        mb.mv[l + j + 2] += Qpb[j] * h;
+        mb.mv[l + j] += Qpb[j] * hx1;
+        mb.mx[1] += Qpb[j] * h * mv[l + j];
+    }
+    ab[2] += Qlb * mv[l + 1];
+    hb += Qlb * mv[l + 2];
+    mb.mv[l + 1] += Qlb * a[2];
+    mb.mv[l + 2] += Qlb * h;
+    // P_j = a0 mu_{k+j} + a1 mu_{k+j+1} + h mu_{k+j+2}
+    for (int j = 0; j < 3; ++j) {
+        ab[0] += Pb[j] * mu[k + j];
+        ab[1] += Pb[j] * mu[k + j + 1];
+        hb += Pb[j] * mu[k + j + 2];
+        mb.mu[k + j] += Pb[j] * a[0];
+        mb.mu[k + j + 1] += Pb[j] * a[1];
+        mb.mu[k + j + 2] += Pb[j] * h;
+    }
+    ab[3] += 0.5 * hb;
 }
 
 // adjoint of slope_solve: bb += S^T ab, state adjoints accumulated
@@ -466,53 +466,55 @@ DFK_HD TimeCoeffs time_coeffs(double rT, double dt, int tau_reading) {
 
 struct GPStateBar { double W[4], Wn[4], Wt[4]; };
 
-// adjoint of gks_flux: given Fb, dFb (local frame) accumulates into Lb, Rb
-DFK_HD void gks_flux_vjp(const GPState& L, const GPState& R, double dt, const SchemeConsts& S,
-                         const double Fb[4], const double dFb[4], GPStateBar& Lb, GPStateBar& Rb) {
+template <class Tape>
+DFK_HD Maxw tape_get_maxw(const Tape& tp, int b) {
+    Maxw s;
+    s.rho = tp.get(b); s.ir = tp.get(b + 1); s.U = tp.get(b + 2); s.V = tp.get(b + 3); s.p = tp.get(b + 4);
+    s.il2 = tp.get(b + 5); s.tl = tp.get(b + 6); s.f4 = tp.get(b + 7); s.qK = tp.get(b + 8);
+    return s;
+}
+template <class Tape>
+DFK_HD void tape_get_mom(const Tape& tp, int b, Mom& m) {
+    for (int n = 0; n < 7; ++n) m.mu[n] = tp.get(b + n);
+    for (int n = 0; n < 6; ++n) m.mv[n] = tp.get(b + 7 + n);
+    for (int n = 0; n < 3; ++n) m.mx[n] = tp.get(b + 13 + n);
+}
+template <class Tape>
+DFK_HD void tape_get_vec(const Tape& tp, int b, double v[4]) {
+    for (int i = 0; i < 4; ++i) v[i] = tp.get(b + i);
+}
+
+// reverse of gks_flux from its taped forward intermediates: given Fb, dFb (local frame) accumulates
+// into Lb, Rb.  The tau = tau_n reading's extra terms are recomputed from the tape.
+template <class Tape>
+DFK_HD void gks_flux_reverse(const Tape& tp, const GPState& L, const GPState& R, double dt, const SchemeConsts& S,
+                             const double Fb[4], const double dFb[4], GPStateBar& Lb, GPStateBar& Rb) {
     const double K = S.K;
-    // ---- forward recompute
-    Maxw sl = maxw_of(L.W, S), sr = maxw_of(R.W, S);
-    Mom ml, mr;
-    fill_moments<+1>(sl, K, ml);
-    fill_moments<-1>(sr, K, mr);
-    double bLx[4], bLy[4], bRx[4], bRy[4], alx[4], aly[4], arx[4], ary[4];
-    for (int i = 0; i < 4; ++i) { bLx[i] = L.Wn[i] * sl.ir; bLy[i] = L.Wt[i] * sl.ir; bRx[i] = R.Wn[i] * sr.ir; bRy[i] = R.Wt[i] * sr.ir; }
-    slope_solve(sl, bLx, alx);
-    slope_solve(sl, bLy, aly);
-    slope_solve(sr, bRx, arx);
-    slope_solve(sr, bRy, ary);
-    double Wc[4], Wcx[4], Wcy[4], t1[4], t2[4];
-    double pl0[4], pr0[4], lx0[4], rx0[4], ly0[4], ry0[4];
-    psi_mom<0, 0, 0>(ml, pl0); psi_mom<0, 0, 0>(mr, pr0);
-    a_mom<0, 0>(ml, alx, lx0); a_mom<0, 0>(mr, arx, rx0);
-    a_mom<0, 0>(ml, aly, ly0); a_mom<0, 0>(mr, ary, ry0);
-    for (int i = 0; i < 4; ++i) {
-        Wc[i] = sl.rho * pl0[i] + sr.rho * pr0[i];
-        Wcx[i] = sl.rho * lx0[i] + sr.rho * rx0[i];
-        Wcy[i] = sl.rho * ly0[i] + sr.rho * ry0[i];
-    }
-    Maxw sc = maxw_of(Wc, S);
-    Mom mc;
-    fill_moments<0>(sc, K, mc);
-    double bcx[4], bcy[4], bct[4], acx[4], acy[4], Ac[4];
-    for (int i = 0; i < 4; ++i) { bcx[i] = Wcx[i] * sc.ir; bcy[i] = Wcy[i] * sc.ir; }
-    slope_solve(sc, bcx, acx);
-    slope_solve(sc, bcy, acy);
-    a_mom<1, 0>(mc, acx, t1); a_mom<0, 1>(mc, acy, t2);
-    for (int i = 0; i < 4; ++i) bct[i] = -(t1[i] + t2[i]);
-    slope_solve(sc, bct, Ac);
+    const Maxw sl = tape_get_maxw(tp, TG_SL), sr = tape_get_maxw(tp, TG_SR), sc = tape_get_maxw(tp, TG_SC);
+    Mom ml, mr, mc;
+    tape_get_mom(tp, TG_ML, ml);
+    tape_get_mom(tp, TG_MR, mr);
+    tape_get_mom(tp, TG_MC, mc);
+    double alx[4], aly[4], arx[4], ary[4], acx[4], acy[4], Ac[4], bct[4];
+    tape_get_vec(tp, TG_ALX, alx); tape_get_vec(tp, TG_ALY, aly);
+    tape_get_vec(tp, TG_ARX, arx); tape_get_vec(tp, TG_ARY, ary);
+    tape_get_vec(tp, TG_ACX, acx); tape_get_vec(tp, TG_ACY, acy);
+    tape_get_vec(tp, TG_AC, Ac); tape_get_vec(tp, TG_BCT, bct);
+    double Wc[4], Wcx[4], Wcy[4], pl0[4], pr0[4], lx0[4], rx0[4], ly0[4], ry0[4];
+    tape_get_vec(tp, TG_WC, Wc); tape_get_vec(tp, TG_WCX, Wcx); tape_get_vec(tp, TG_WCY, Wcy);
+    tape_get_vec(tp, TG_PL0, pl0); tape_get_vec(tp, TG_PR0, pr0);
+    tape_get_vec(tp, TG_LX0, lx0); tape_get_vec(tp, TG_RX0, rx0);
+    tape_get_vec(tp, TG_LY0, ly0); tape_get_vec(tp, TG_RY0, ry0);
     double Mc0[4], Mc1[4], Mc2[4], Ml0[4], Mr0[4], Ml1[4], Mr1[4];
-    psi_mom<1, 0, 0>(mc, Mc0);
-    a_mom<2, 0>(mc, acx, t1); a_mom<1, 1>(mc, acy, t2);
-    for (int i = 0; i < 4; ++i) Mc1[i] = t1[i] + t2[i];
-    a_mom<1, 0>(mc, Ac, Mc2);
-    psi_mom<1, 0, 0>(ml, Ml0);
-    psi_mom<1, 0, 0>(mr, Mr0);
-    a_mom<2, 0>(ml, alx, t1); a_mom<1, 1>(ml, aly, t2);
-    for (int i = 0; i < 4; ++i) Ml1[i] = t1[i] + t2[i];
-    a_mom<2, 0>(mr, arx, t1); a_mom<1, 1>(mr, ary, t2);
-    for (int i = 0; i < 4; ++i) Mr1[i] = t1[i] + t2[i];
-    double q = (sl.p - sr.p) / (sl.p + sr.p);
+    tape_get_vec(tp, TG_MC0, Mc0); tape_get_vec(tp, TG_MC1, Mc1); tape_get_vec(tp, TG_MC2, Mc2);
+    tape_get_vec(tp, TG_ML0, Ml0); tape_get_vec(tp, TG_MR0, Mr0);
+    tape_get_vec(tp, TG_ML1, Ml1); tape_get_vec(tp, TG_MR1, Mr1);
+    const double q = tp.get(TG_Q);
+    double bLx[4], bLy[4], bRx[4], bRy[4], bcx[4], bcy[4], t1[4], t2[4];
+    for (int i = 0; i < 4; ++i) {
+        bLx[i] = L.Wn[i] * sl.ir; bLy[i] = L.Wt[i] * sl.ir; bRx[i] = R.Wn[i] * sr.ir; bRy[i] = R.Wt[i] * sr.ir;
+        bcx[i] = Wcx[i] * sc.ir; bcy[i] = Wcy[i] * sc.ir;
+    }
     double rT = S.C1 + S.C2 * fabs(q);
     TimeCoeffs tc = time_coeffs(rT, dt, S.tau_reading);
     double Ml2[4] = {0, 0, 0, 0}, Mr2[4] = {0, 0, 0, 0}, Al[4] = {0, 0, 0, 0}, Ar[4] = {0, 0, 0, 0};
@@ -648,6 +650,15 @@ DFK_HD void gks_flux_vjp(const GPState& L, const GPState& R, double dt, const Sc
     fill_moments_vjp<-1>(sr, K, mr, mrb, srb);
     maxw_of_vjp(L.W, S, sl, slb, Lb.W);
     maxw_of_vjp(R.W, S, sr, srb, Rb.W);
+}
+
+// adjoint of gks_flux: the forward recomputed into a local tape, then its reverse
+DFK_HD void gks_flux_vjp(const GPState& L, const GPState& R, double dt, const SchemeConsts& S,
+                         const double Fb[4], const double dFb[4], GPStateBar& Lb, GPStateBar& Rb) {
+    double t[TG_COUNT], F[4], dF[4];
+    ArrayTape tp{t};
+    gks_flux_t(L, R, dt, S, F, dF, tp);
+    gks_flux_reverse(tp, L, R, dt, S, Fb, dFb, Lb, Rb);
 }
 
 // ------------------------------------------------------------------------------------------

@@ -127,10 +127,11 @@ DFK_HD void ghost_y_body(const Mesh& m, double* W, double* alpha, int i, int gr)
 }
 
 // one face line (normal reconstruction of both sides); returns the number of DF branches taken
-template <int DIR>
+// TAPE: also write the reconstructions' intermediates for a reverse sweep (ltape, see SweepBuffers)
+template <int DIR, bool TAPE = false>
 DFK_HD int lines_body(const Mesh& m, const SchemeConsts& S, const double* __restrict__ W,
                                           const double* __restrict__ alpha, double* __restrict__ lines,
-                                          long long ls, int ax, int ay) {
+                                          long long ls, int ax, int ay, double* __restrict__ ltape = nullptr) {
     Geo<DIR> g(m);
     int f = DIR == 0 ? ax : ay;
     int tt = DIR == 0 ? ay : ax;                           // t + 2
@@ -156,6 +157,7 @@ DFK_HD int lines_body(const Mesh& m, const SchemeConsts& S, const double* __rest
         const bool dfR = fmax(fmax(al[2], al[3]), al[4]) < S.alpha_thres;     // Eq. 34, cell f
         ndf = (int)dfL + (int)dfR;
         const double idn = 1.0 / g.dn;
+        const long long li = g.line(f, t);
         double qL[4], qLn[4], qR[4], qRn[4];
         double tl = 1.0;
         int tlk = -1;                                     // the reconstruction that set tl
@@ -165,14 +167,14 @@ DFK_HD int lines_body(const Mesh& m, const SchemeConsts& S, const double* __rest
             double sR[5] = {Q[5][k], Q[4][k], Q[3][k], Q[2][k], Q[1][k]};   // mirrored about cell f
             double v, sl;
             if (!dfL || S.time_limiter) {
-                AO o = weno_ao(sL, S);
+                AO o = TAPE ? weno_ao_t(sL, S, PlaneTape{ltape + li, ls}, 2 * k * AT_COUNT) : weno_ao(sL, S);
                 if (S.time_limiter) { double la = limiter_alpha(o); if (la < tl) { tl = la; tlk = 2 * k; } }
                 if (!dfL) ao_at_right_edge(o, sL[2], v, sl);
             }
             if (dfL) df_at_right_edge(sL, al[2], v, sl);
             qL[k] = v; qLn[k] = sl * idn;
             if (!dfR || S.time_limiter) {
-                AO o = weno_ao(sR, S);
+                AO o = TAPE ? weno_ao_t(sR, S, PlaneTape{ltape + li, ls}, (2 * k + 1) * AT_COUNT) : weno_ao(sR, S);
                 if (S.time_limiter) { double la = limiter_alpha(o); if (la < tl) { tl = la; tlk = 2 * k + 1; } }
                 if (!dfR) ao_at_right_edge(o, sR[2], v, sl);
             }
@@ -184,7 +186,6 @@ DFK_HD int lines_body(const Mesh& m, const SchemeConsts& S, const double* __rest
         back_project(B, qLn, out + LR_WLN);
         back_project(B, qR, out + LR_WR);
         back_project(B, qRn, out + LR_WRN);
-        long long li = g.line(f, t);
 #pragma unroll
         for (int q = 0; q < 16; ++q) lines[q * ls + li] = out[q];
         lines[LR_TL * ls + li] = tl;
@@ -203,11 +204,13 @@ DFK_HD int lines_body(const Mesh& m, const SchemeConsts& S, const double* __rest
 
 // one face side (tangential reconstruction at both Gauss points, fallback); returns the number of
 // DF branches taken and sets nfb to the number of fallbacks
-template <int DIR>
+// TAPE: also write the reconstructions' intermediates for a reverse sweep (ftape, see SweepBuffers)
+template <int DIR, bool TAPE = false>
 DFK_HD int faces_body(const Mesh& m, const SchemeConsts& S, const double* __restrict__ W,
                                           const double* __restrict__ alpha, const double* __restrict__ lines,
                                           long long ls, double* __restrict__ gp, long long gs,
-                                          int ax, int ay, int side, int& nfb) {
+                                          int ax, int ay, int side, int& nfb,
+                                          double* __restrict__ ftape = nullptr) {
     Geo<DIR> g(m);
     int f = DIR == 0 ? ax : ay;
     int t = DIR == 0 ? ay : ax;
@@ -238,16 +241,19 @@ DFK_HD int faces_body(const Mesh& m, const SchemeConsts& S, const double* __rest
         ndf = (int)df;
         double qv[2][4], qt[2][4];
         const double idt = 1.0 / g.dtan;
+        const long long e = (long long)side * g.nfaces() + g.face(f, t);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             double sq[5] = {Q[0][k], Q[1][k], Q[2][k], Q[3][k], Q[4][k]};
             double v[2], s[2];
             if (df) df_at_gauss(sq, al[1], v, s);
-            else { AO o = weno_ao(sq, S); ao_at_gauss(o, sq[2], v, s); }
+            else {
+                AO o = TAPE ? weno_ao_t(sq, S, PlaneTape{ftape + e, gs}, k * AT_COUNT) : weno_ao(sq, S);
+                ao_at_gauss(o, sq[2], v, s);
+            }
             qv[0][k] = v[0]; qv[1][k] = v[1];
             qt[0][k] = s[0] * idt; qt[1][k] = s[1] * idt;
         }
-        const long long e = (long long)side * g.nfaces() + g.face(f, t);
         const int nbase = side == 0 ? LR_WLN : LR_WRN;
         int fbits = 0;
 #pragma unroll
@@ -278,10 +284,11 @@ DFK_HD int faces_body(const Mesh& m, const SchemeConsts& S, const double* __rest
 }
 
 // one Gauss point (flux, time derivative, DF factor, omega^t)
-template <int DIR, int FLUX, bool ALPHA_ONLY>
+template <int DIR, int FLUX, bool ALPHA_ONLY, bool TAPE = false>
 DFK_HD void flux_body(const Mesh& m, const SchemeConsts& S, const double* __restrict__ lines,
                                           long long ls, const double* __restrict__ gp, long long gs,
-                                          double* __restrict__ fr, long long fs, double dt, int ax, int ay, int mm) {
+                                          double* __restrict__ fr, long long fs, double dt, int ax, int ay, int mm,
+                         double* __restrict__ tape = nullptr) {
     Geo<DIR> g(m);
     int f = DIR == 0 ? ax : ay;
     int t = DIR == 0 ? ay : ax;
@@ -302,7 +309,14 @@ DFK_HD void flux_body(const Mesh& m, const SchemeConsts& S, const double* __rest
     fr[FR_ALPHA * fs + e] = df_alpha(L.W, R.W, S);
     if (ALPHA_ONLY) return;
     double F[4], dF[4];
-    if (FLUX == 0) gks_flux(L, R, dt, S, F, dF);
+    if (FLUX == 0) {
+        if (TAPE) {
+            PlaneTape tp{tape + e, fs};
+            gks_flux_t(L, R, dt, S, F, dF, tp);
+        } else {
+            gks_flux(L, R, dt, S, F, dF);
+        }
+    }
     else lf_flux(L, R, S, F, dF);
     to_global<DIR>(F);
     to_global<DIR>(dF);

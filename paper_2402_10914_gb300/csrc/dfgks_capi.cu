@@ -49,6 +49,12 @@ struct dfgks {
     int ck_n, ck_k, ck_flux;
     unsigned long long gen;      // bumped by every call that changes the state
     unsigned long long ck_gen;   // gen right after the checkpointed forward pass (0: none)
+    // segment arena of the reverse pass: per step of one segment W^s, alpha^s, W* (dense) and,
+    // when they fit, the forward sweep records (with tapes); the forward pass fills it for the
+    // last segment, so the reverse pass recomputes only the earlier ones
+    double* seg_arena;
+    long long seg_cap;           // doubles allocated
+    int seg_k, seg_records, seg_tape, seg_gks, seg_last_kept;
 };
 
 static dfgks_status cuda_status(cudaError_t e) {
@@ -107,6 +113,7 @@ static void free_all(dfgks* h) {
     double* ptrs[] = {h->W[0], h->W[1], h->A[0], h->A[1], h->Ws, h->As, h->acc, h->B.lines, h->B.gp,
                       h->B.flux[0], h->B.flux[1], h->dt_scratch, h->dts, h->adj_lines, h->adj_gp, h->adj_Wg};
     for (double* p : ptrs) if (p) cudaFree(p);
+    if (h->seg_arena) cudaFree(h->seg_arena);
     if (h->ck_W) cudaFree(h->ck_W);
     if (h->ck_A) cudaFree(h->ck_A);
     free(h->ck_dts);
@@ -482,6 +489,87 @@ extern "C" dfgks_status dfgks_adjoint_residual(dfgks* h, const double* W, const 
     return adjoint_stage(h, W, alpha, dt, flux, L_bar, dtL_bar, dtLt_bar, W_bar);
 }
 
+// doubles of one step's forward records: two stages x two directions of face lines, Gauss points and
+// fluxes, and (tape) the reconstructions' intermediates and, for GKS, the flux's intermediates
+static long long record_doubles_per_step(const dfgks* h, bool tape, bool gks) {
+    const SweepBuffers& B = h->B;
+    long long per_dir = (long long)(LR_COUNT + (tape ? 8 * AT_COUNT : 0)) * B.line_stride
+                      + (long long)(GP_COUNT + (tape ? 4 * AT_COUNT : 0)) * B.gp_stride;
+    long long flux = (long long)(FR_COUNT + (tape && gks ? TG_COUNT : 0)) * (B.flux_stride[0] + B.flux_stride[1]);
+    return 2 * (2 * per_dir + flux);
+}
+
+static void record_sets(const dfgks* h, double* base, bool tape, bool gks, SweepBuffers rec[4]) {
+    const SweepBuffers& B = h->B;
+    double* p = base;
+    for (int q = 0; q < 4; ++q) {
+        const int d = q & 1;
+        rec[q] = B;
+        rec[q].lines = p; p += (long long)LR_COUNT * B.line_stride;
+        rec[q].gp = p; p += (long long)GP_COUNT * B.gp_stride;
+        rec[q].flux[0] = rec[q].flux[1] = nullptr;
+        rec[q].flux[d] = p; p += (long long)FR_COUNT * B.flux_stride[d];
+        rec[q].tape[0] = rec[q].tape[1] = nullptr;
+        rec[q].ltape = rec[q].ftape = nullptr;
+        if (tape) {
+            rec[q].ltape = p; p += (long long)8 * AT_COUNT * B.line_stride;
+            rec[q].ftape = p; p += (long long)4 * AT_COUNT * B.gp_stride;
+            if (gks) { rec[q].tape[d] = p; p += (long long)TG_COUNT * B.flux_stride[d]; }
+        }
+    }
+}
+
+// Lay out (and allocate if needed) the segment arena for k steps: W^s, alpha^s, W* per step and,
+// if they fit in half of the free device memory, the sweep records (with the reconstruction and GKS
+// flux tapes when those fit too).
+struct SegArena { double* W; double* A; double* Ws; double* recs; bool tape, gks; long long rec_step; };
+
+// the arena's layout as last decided (seg_k, seg_records, seg_tape, seg_gks)
+static void arena_view(const dfgks* h, SegArena& a) {
+    const long long N = (long long)h->mesh.nx * h->mesh.ny, N4 = 4 * N;
+    const int k = h->seg_k;
+    a.W = h->seg_arena;
+    a.A = a.W + (long long)k * N4;
+    a.Ws = a.A + (long long)k * N;
+    a.recs = h->seg_records ? a.Ws + (long long)k * N4 : nullptr;
+    a.tape = h->seg_tape != 0; a.gks = h->seg_gks != 0;
+    a.rec_step = record_doubles_per_step(h, a.tape, a.gks);
+}
+
+static dfgks_status ensure_segment_arena(dfgks* h, int k, int flux, SegArena& a) {
+    const Mesh& m = h->mesh;
+    const long long N = (long long)m.nx * m.ny, N4 = 4 * N;
+    const bool gks = flux == DFGKS_FLUX_GKS;
+    const long long base = (long long)k * (2 * N4 + N);
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    const double budget = 0.5 * ((double)free_b + (double)h->seg_cap * sizeof(double));
+    auto need = [&](int records, bool tape) {
+        return base + (records ? (long long)k * record_doubles_per_step(h, tape, gks) : 0);
+    };
+    int records = 1;
+    bool tape = true;
+    if ((double)need(1, true) * sizeof(double) > budget) tape = false;
+    if ((double)need(1, false) * sizeof(double) > budget) records = 0;
+    const long long want = need(records, tape);
+    if (want > h->seg_cap) {
+        if (h->seg_arena) { cudaFree(h->seg_arena); h->bytes -= (unsigned long long)h->seg_cap * sizeof(double); }
+        h->seg_arena = nullptr;
+        h->seg_cap = 0;
+        if (dalloc(h, &h->seg_arena, want) != cudaSuccess) {
+            cudaGetLastError();
+            if (!records || dalloc(h, &h->seg_arena, base) != cudaSuccess) { cudaGetLastError(); return DFGKS_ENOMEM; }
+            records = 0;
+            h->seg_cap = base;
+        } else {
+            h->seg_cap = want;
+        }
+    }
+    h->seg_k = k; h->seg_records = records; h->seg_tape = tape; h->seg_gks = gks;
+    arena_view(h, a);
+    return DFGKS_OK;
+}
+
 // Forward pass from W0 (alpha^0 from W0) over n S2O4 steps, dt from dts_in or, if that is NULL, the
 // CFL rule; W and alpha are kept every k steps and the dts on the host, for the reverse pass.
 static dfgks_status forward_checkpointed(dfgks* h, const double* W0, int n, const double* dts_in, int k, int flux) {
@@ -510,16 +598,31 @@ static dfgks_status forward_checkpointed(dfgks* h, const double* W0, int n, cons
         CK(dalloc(h, &h->dts, n));
         h->dts_cap = n;
     }
-    dfgks_status r = load_state(h, W0, nullptr, 0.0, 0, 1);
+    SegArena a;
+    h->seg_last_kept = 0;
+    dfgks_status r = ensure_segment_arena(h, k, flux, a);
+    if (r) return r;
+    r = load_state(h, W0, nullptr, 0.0, 0, 1);
     if (r) return r;
     const int cur0 = h->cur;
+    const int last0 = (nseg - 1) * k;          // the last segment's steps fill the arena as they run
     for (int s = 0; s < n; ++s) {
         const int c = (cur0 + s) & 1;
         if (s % k == 0) {
             launch_ghosted_to_dense(m, h->W[c], 4, h->ck_W + (long long)(s / k) * N4, h->stream);
             launch_ghosted_to_dense(m, h->A[c], 1, h->ck_A + (long long)(s / k) * N, h->stream);
         }
-        enqueue_step(h, s, dts_in ? dts_in[s] : 0.0, flux, 0.0, cur0);
+        if (s >= last0) {
+            const int j = s - last0;
+            launch_ghosted_to_dense(m, h->W[c], 4, a.W + (long long)j * N4, h->stream);
+            launch_ghosted_to_dense(m, h->A[c], 1, a.A + (long long)j * N, h->stream);
+            SweepBuffers rec[4];
+            if (a.recs) record_sets(h, a.recs + (long long)j * a.rec_step, a.tape, a.gks, rec);
+            enqueue_step(h, s, dts_in ? dts_in[s] : 0.0, flux, 0.0, cur0, a.Ws + (long long)j * N4,
+                         a.recs ? rec : nullptr);
+        } else {
+            enqueue_step(h, s, dts_in ? dts_in[s] : 0.0, flux, 0.0, cur0);
+        }
     }
     CK_LAUNCH();
     CK(cudaMemcpyAsync(h->st_host, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
@@ -530,39 +633,28 @@ static dfgks_status forward_checkpointed(dfgks* h, const double* W0, int n, cons
     if (h->st_host->err || done != n) return DFGKS_ENONPOS;
     CK(cudaMemcpy(h->ck_dts, h->dts, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost));
     h->ck_n = n; h->ck_k = k; h->ck_flux = flux;
+    h->seg_last_kept = 1;
     h->ck_gen = ++h->gen;
     return DFGKS_OK;
 }
 
-// doubles of one step's forward records: two stages x two directions of face lines, Gauss points and fluxes
-static long long record_doubles_per_step(const dfgks* h) {
-    const SweepBuffers& B = h->B;
-    long long per_dir = (long long)LR_COUNT * B.line_stride + (long long)GP_COUNT * B.gp_stride;
-    return 2 * (2 * per_dir + (long long)FR_COUNT * (B.flux_stride[0] + B.flux_stride[1]));
-}
-
-static void record_sets(const dfgks* h, double* base, SweepBuffers rec[4]) {
-    const SweepBuffers& B = h->B;
-    double* p = base;
-    for (int q = 0; q < 4; ++q) {
-        const int d = q & 1;
-        rec[q] = B;
-        rec[q].lines = p; p += (long long)LR_COUNT * B.line_stride;
-        rec[q].gp = p; p += (long long)GP_COUNT * B.gp_stride;
-        rec[q].flux[0] = rec[q].flux[1] = nullptr;
-        rec[q].flux[d] = p; p += (long long)FR_COUNT * B.flux_stride[d];
-    }
-}
-
 // Reverse pass over the checkpointed forward pass: dJ/dW0 = (dW^n/dW0)^T WT_bar.  Each segment of
-// k steps is recomputed from its checkpoint, keeping W^s, alpha^s, W* and, if they fit in
-// the memory budget, every stage's forward records; then its steps are reversed (Eq. 24 with the
-// time limiter):  W* = W + dt/2 L + dt^2/8 dL,  W' = W + dt L + dt^2/2 dL - dt^2/3 dLt + dt^2/3 dLt(W*).
+// k steps is recomputed from its checkpoint (the last one only if the forward pass could not keep
+// it), keeping W^s, alpha^s, W* and, if they fit in the memory budget, every stage's forward records;
+// then its steps are reversed (Eq. 24 with the time limiter):  W* = W + dt/2 L + dt^2/8 dL,  W' = W + dt L + dt^2/2 dL - dt^2/3 dLt + dt^2/3 dLt(W*).
 static dfgks_status backward_checkpointed(dfgks* h, const double* WT_bar, double* W0_bar) {
     const Mesh& m = h->mesh;
     const long long N = (long long)m.nx * m.ny, N4 = 4 * N;
     const int n = h->ck_n, k = h->ck_k, flux = h->ck_flux, nseg = (n + k - 1) / k;
     const double* dts = h->ck_dts;
+    // the last segment's states and records are still in the arena if the forward pass kept them
+    const bool kept = h->seg_last_kept && h->seg_arena && h->seg_k == k && h->seg_gks == (flux == DFGKS_FLUX_GKS);
+    h->seg_last_kept = 0;                       // the recompute below overwrites the arena
+    SegArena a;
+    dfgks_status r = DFGKS_OK;
+    if (kept) arena_view(h, a);                 // the layout the forward pass wrote
+    else r = ensure_segment_arena(h, k, flux, a);
+    if (r) return r;
     std::vector<double*> bufs;
     auto get = [&](long long cnt) -> double* {
         double* p = nullptr;
@@ -570,9 +662,6 @@ static dfgks_status backward_checkpointed(dfgks* h, const double* WT_bar, double
         bufs.push_back(p);
         return p;
     };
-    double* segW = get(k * N4);
-    double* segA = get(k * N);
-    double* segWs = get(k * N4);
     double* Wb = get(N4);
     double* Wsb = get(N4);
     double* bL = get(N4);
@@ -580,18 +669,7 @@ static dfgks_status backward_checkpointed(dfgks* h, const double* WT_bar, double
     double* bdLt = get(N4);
     double* WTs = get(N4);
     double* ATs = get(N);
-    dfgks_status r = DFGKS_OK;
-    for (double* p : bufs) if (!p) r = DFGKS_ENOMEM;
-    if (bufs.size() != 10) r = DFGKS_ENOMEM;
-    // forward records of the whole segment when they take at most half of the free memory
-    double* recs = nullptr;
-    if (r == DFGKS_OK) {
-        size_t free_b = 0, total_b = 0;
-        cudaMemGetInfo(&free_b, &total_b);
-        const double want = (double)k * (double)record_doubles_per_step(h) * sizeof(double);
-        if (want <= 0.5 * (double)free_b) recs = get((long long)k * record_doubles_per_step(h));
-        cudaGetLastError();      // a refused allocation only means recompute-in-reverse
-    }
+    if (bufs.size() != 7) r = DFGKS_ENOMEM;
     auto cleanup = [&]() { cudaStreamSynchronize(h->stream); for (double* p : bufs) if (p) cudaFree(p); };
     if (r) { cleanup(); return r; }
     r = ensure_adjoint_buffers(h);
@@ -604,26 +682,31 @@ static dfgks_status backward_checkpointed(dfgks* h, const double* WT_bar, double
     CK(cudaMemcpyAsync(Wb, WT_bar, (size_t)N4 * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
     for (int seg = nseg - 1; seg >= 0 && r == DFGKS_OK; --seg) {
         const int s0 = seg * k, s1 = (s0 + k < n) ? s0 + k : n;
-        launch_dense_to_ghosted(m, h->ck_W + (long long)seg * N4, 4, h->W[h->cur], h->stream);
-        launch_dense_to_ghosted(m, h->ck_A + (long long)seg * N, 1, h->A[h->cur], h->stream);
-        for (int s = s0; s < s1; ++s) {
-            launch_ghosted_to_dense(m, h->W[h->cur], 4, segW + (s - s0) * N4, h->stream);
-            launch_ghosted_to_dense(m, h->A[h->cur], 1, segA + (s - s0) * N, h->stream);
-            SweepBuffers rec[4];
-            if (recs) record_sets(h, recs + (long long)(s - s0) * record_doubles_per_step(h), rec);
-            enqueue_step(h, 0, dts[s], flux, 0.0, h->cur, segWs + (s - s0) * N4, recs ? rec : nullptr);
-            h->cur ^= 1;
+        if (!(kept && seg == nseg - 1)) {
+            // recompute the segment from its checkpoint, keeping W^s, alpha^s, W* and the records
+            launch_dense_to_ghosted(m, h->ck_W + (long long)seg * N4, 4, h->W[h->cur], h->stream);
+            launch_dense_to_ghosted(m, h->ck_A + (long long)seg * N, 1, h->A[h->cur], h->stream);
+            for (int s = s0; s < s1; ++s) {
+                launch_ghosted_to_dense(m, h->W[h->cur], 4, a.W + (s - s0) * N4, h->stream);
+                launch_ghosted_to_dense(m, h->A[h->cur], 1, a.A + (s - s0) * N, h->stream);
+                SweepBuffers rec[4];
+                if (a.recs) record_sets(h, a.recs + (long long)(s - s0) * a.rec_step, a.tape, a.gks, rec);
+                enqueue_step(h, 0, dts[s], flux, 0.0, h->cur, a.Ws + (s - s0) * N4, a.recs ? rec : nullptr);
+                h->cur ^= 1;
+            }
         }
+        // reverse through the segment: Eq. 24 with the time limiter,
+        //   W* = W + dt/2 L + dt^2/8 dL,  W' = W + dt L + dt^2/2 dL - dt^2/3 dLt + dt^2/3 dLt(W*)
         for (int s = s1 - 1; s >= s0 && r == DFGKS_OK; --s) {
             const double dt = dts[s], dt2 = dt * dt;
-            const double* Wn = segW + (s - s0) * N4;
-            const double* An = segA + (s - s0) * N;
-            const double* Wst = segWs + (s - s0) * N4;
+            const double* Wn = a.W + (s - s0) * N4;
+            const double* An = a.A + (s - s0) * N;
+            const double* Wst = a.Ws + (s - s0) * N4;
             SweepBuffers rec[4];
-            if (recs) record_sets(h, recs + (long long)(s - s0) * record_doubles_per_step(h), rec);
+            if (a.recs) record_sets(h, a.recs + (long long)(s - s0) * a.rec_step, a.tape, a.gks, rec);
             CK(cudaMemsetAsync(Wsb, 0, (size_t)N4 * sizeof(double), h->stream));
             launch_axpby(N4, dt2 / 3.0, Wb, 0.0, bdLt, h->stream);
-            r = adjoint_stage(h, Wst, An, dt, flux, nullptr, nullptr, bdLt, Wsb, recs ? rec + 2 : nullptr);
+            r = adjoint_stage(h, Wst, An, dt, flux, nullptr, nullptr, bdLt, Wsb, a.recs ? rec + 2 : nullptr);
             if (r) break;
             launch_axpby(N4, dt, Wb, 0.0, bL, h->stream);
             launch_axpby(N4, 0.5 * dt, Wsb, 1.0, bL, h->stream);
@@ -631,7 +714,7 @@ static dfgks_status backward_checkpointed(dfgks* h, const double* WT_bar, double
             launch_axpby(N4, 0.125 * dt2, Wsb, 1.0, bdL, h->stream);
             launch_axpby(N4, -dt2 / 3.0, Wb, 0.0, bdLt, h->stream);
             launch_axpby(N4, 1.0, Wsb, 1.0, Wb, h->stream);
-            r = adjoint_stage(h, Wn, An, dt, flux, bL, bdL, bdLt, Wb, recs ? rec : nullptr);
+            r = adjoint_stage(h, Wn, An, dt, flux, bL, bdL, bdLt, Wb, a.recs ? rec : nullptr);
         }
     }
     if (r == DFGKS_OK) CK(cudaMemcpyAsync(W0_bar, Wb, (size_t)N4 * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));

@@ -103,7 +103,30 @@ struct AO {
     double rmax, rmin;      // tau_Z/(beta_min+eps), tau_Z/(beta_max+eps): the time limiter's ratios
 };
 
-DFK_HD AO weno_ao(const double q[5], const SchemeConsts& S) {
+// Optional record of a reconstruction's intermediates for its reverse (a "tape"): a sink with
+// put(index, value).  NoTape discards everything, so the plain forward compiles to the arithmetic
+// alone; ArrayTape writes a local array, PlaneTape one element of SoA planes in global memory.
+struct NoTape { DFK_HD void put(int, double) const {} };
+struct ArrayTape {
+    double* t;
+    DFK_HD void put(int i, double v) const { t[i] = v; }
+    DFK_HD double get(int i) const { return t[i]; }
+};
+struct PlaneTape {
+    double* p;
+    long long s;
+    DFK_HD void put(int i, double v) const { p[(long long)i * s] = v; }
+    DFK_HD double get(int i) const { return p[(long long)i * s]; }
+};
+
+// WENO-AO tape of one reconstruction: sub-stencil coefficients a1[4], a2[4], the quartic's a3, a4,
+// 1/(beta_k+eps), the ratios r_k, unnormalised weights w_k, 1/sum w, c_3, sign(beta_3 - beta_k)
+// and the indices of max / min r (first attaining)
+enum AOTapeField { AT_A1 = 0, AT_A2 = 4, AT_A3 = 8, AT_A4 = 9, AT_IE = 10, AT_R = 14, AT_W = 18, AT_IW = 22,
+                   AT_C3 = 23, AT_SG = 24, AT_KMAX = 27, AT_KMIN = 28, AT_COUNT = 29 };
+
+template <class Tape>
+DFK_HD AO weno_ao_t(const double q[5], const SchemeConsts& S, const Tape& tp, int base) {
     const double qm2 = q[0], qm1 = q[1], q0 = q[2], q1 = q[3], q2 = q[4];
     // quadratic sub-stencils {i-2,i-1,i}, {i-1,i,i+1}, {i,i+1,i+2}
     double a1_0 = 0.5 * qm2 - 2.0 * qm1 + 1.5 * q0;
@@ -133,8 +156,13 @@ DFK_HD AO weno_ao(const double q[5], const SchemeConsts& S) {
     if (prod < 1e300) {                              // beta+eps >= eps, so prod >= eps^4 > 0
         double ti = tau / prod;
         r0 = ti * (e1 * p23); r1 = ti * (e0 * p23); r2 = ti * (p01 * e3); r3 = ti * (p01 * e2);
+        const double ip = 1.0 / prod;                // the reciprocals, for the tape only
+        tp.put(base + AT_IE, (e1 * p23) * ip); tp.put(base + AT_IE + 1, (e0 * p23) * ip);
+        tp.put(base + AT_IE + 2, (p01 * e3) * ip); tp.put(base + AT_IE + 3, (p01 * e2) * ip);
     } else {
         r0 = tau / e0; r1 = tau / e1; r2 = tau / e2; r3 = tau / e3;
+        tp.put(base + AT_IE, 1.0 / e0); tp.put(base + AT_IE + 1, 1.0 / e1);
+        tp.put(base + AT_IE + 2, 1.0 / e2); tp.put(base + AT_IE + 3, 1.0 / e3);
     }
     double w0 = S.d[0] * (1.0 + r0 * r0), w1 = S.d[1] * (1.0 + r1 * r1);
     double w2 = S.d[2] * (1.0 + r2 * r2), w3 = S.d[3] * (1.0 + r3 * r3);
@@ -149,8 +177,25 @@ DFK_HD AO weno_ao(const double q[5], const SchemeConsts& S) {
     // tau >= 0, so the ratio is largest at beta_min and smallest at beta_max
     o.rmax = fmax(fmax(r0, r1), fmax(r2, r3));
     o.rmin = fmin(fmin(r0, r1), fmin(r2, r3));
+    tp.put(base + AT_A1, a1_0); tp.put(base + AT_A1 + 1, a1_1); tp.put(base + AT_A1 + 2, a1_2); tp.put(base + AT_A1 + 3, a1_3);
+    tp.put(base + AT_A2, a2_0); tp.put(base + AT_A2 + 1, a2_1); tp.put(base + AT_A2 + 2, a2_2); tp.put(base + AT_A2 + 3, a2_3);
+    tp.put(base + AT_A3, a3_3); tp.put(base + AT_A4, a4_3);
+    tp.put(base + AT_R, r0); tp.put(base + AT_R + 1, r1); tp.put(base + AT_R + 2, r2); tp.put(base + AT_R + 3, r3);
+    tp.put(base + AT_W, w0); tp.put(base + AT_W + 1, w1); tp.put(base + AT_W + 2, w2); tp.put(base + AT_W + 3, w3);
+    tp.put(base + AT_IW, iw); tp.put(base + AT_C3, c3);
+    tp.put(base + AT_SG, (b3 - b0) >= 0.0 ? 1.0 : -1.0);
+    tp.put(base + AT_SG + 1, (b3 - b1) >= 0.0 ? 1.0 : -1.0);
+    tp.put(base + AT_SG + 2, (b3 - b2) >= 0.0 ? 1.0 : -1.0);
+    int kmax = 0, kmin = 0;
+    const double rr[4] = {r0, r1, r2, r3};
+#pragma unroll
+    for (int k = 1; k < 4; ++k) { if (rr[k] > rr[kmax]) kmax = k; if (rr[k] < rr[kmin]) kmin = k; }
+    tp.put(base + AT_KMAX, (double)kmax);
+    tp.put(base + AT_KMIN, (double)kmin);
     return o;
 }
+
+DFK_HD AO weno_ao(const double q[5], const SchemeConsts& S) { return weno_ao_t(q, S, NoTape{}, 0); }
 
 // time-limiter ingredient 2 at2 / (at1 + at2) of one reconstruction (Sect. 2.2)
 DFK_HD double limiter_alpha(const AO& o) {
@@ -258,19 +303,27 @@ DFK_HD void psi_mom(const Mom& m, double out[4]) {
     out[3] = 0.5 * (M<k + 2, l, c>(m) + M<k, l + 2, c>(m) + M<k, l, c + 1>(m));
 }
 
-// <u^k v^l a psi> with a = a0 + a1 u + a2 v + a3 (u^2+v^2+xi^2)/2
+// <u^k v^l a psi> with a = a0 + a1 u + a2 v + a3 (u^2+v^2+xi^2)/2.  With h = a3/2 and the
+// factorised moments <u^k v^l xi^2c> = mu_k mv_l mx_c (mx_0 = 1):
+//   G(k,l,c) = <u^k v^l xi^2c a> = mx_c (mv_l P_k + mu_k Q_l) + h mu_k mv_l mx_{c+1},
+//   P_k = a0 mu_k + a1 mu_{k+1} + h mu_{k+2},   Q_l = a2 mv_{l+1} + h mv_{l+2},
+// and out = (G(k,l,0), G(k+1,l,0), G(k,l+1,0), [G(k+2,l,0) + G(k,l+2,0) + G(k,l,1)] / 2).
+// Qp_j = Q_{l+j} + h mx_1 mv_{l+j} folds the xi^2 term into the c = 0 forms.
 template <int k, int l>
 DFK_HD void a_mom(const Mom& m, const double a[4], double out[4]) {
-    double t0[4], t1[4], t2[4], t3[4], t4[4], t5[4];
-    psi_mom<k, l, 0>(m, t0);
-    psi_mom<k + 1, l, 0>(m, t1);
-    psi_mom<k, l + 1, 0>(m, t2);
-    psi_mom<k + 2, l, 0>(m, t3);
-    psi_mom<k, l + 2, 0>(m, t4);
-    psi_mom<k, l, 1>(m, t5);
-    double h = 0.5 * a[3];
+    const double h = 0.5 * a[3], hx1 = h * m.mx[1];
+    double P[3], Qp[3];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) out[i] = a[0] * t0[i] + a[1] * t1[i] + a[2] * t2[i] + h * (t3[i] + t4[i] + t5[i]);
+    for (int j = 0; j < 3; ++j) {
+        P[j] = a[0] * m.mu[k + j] + a[1] * m.mu[k + j + 1] + h * m.mu[k + j + 2];
+        Qp[j] = a[2] * m.mv[l + j + 1] + h * m.mv[l + j + 2] + hx1 * m.mv[l + j];
+    }
+    const double Ql = a[2] * m.mv[l + 1] + h * m.mv[l + 2];
+    const double G1 = m.mx[1] * (m.mv[l] * P[0] + m.mu[k] * Ql) + h * m.mu[k] * m.mv[l] * m.mx[2];
+    out[0] = m.mv[l] * P[0] + m.mu[k] * Qp[0];
+    out[1] = m.mv[l] * P[1] + m.mu[k + 1] * Qp[0];
+    out[2] = m.mv[l + 1] * P[0] + m.mu[k] * Qp[1];
+    out[3] = 0.5 * ((m.mv[l] * P[2] + m.mu[k + 2] * Qp[0]) + (m.mv[l + 2] * P[0] + m.mu[k] * Qp[2]) + G1);
 }
 
 // closed-form solution of <a psi> = b for a Maxwellian (U, V, lambda)
@@ -284,8 +337,44 @@ DFK_HD void slope_solve(const Maxw& s, const double b[4], double a[4]) {
 
 struct GPState { double W[4], Wn[4], Wt[4]; };   // one side of one Gauss point, local frame
 
-DFK_HD void gks_flux(const GPState& L, const GPState& R, double dt, const SchemeConsts& S,
-                                         double F[4], double dF[4]) {
+// Forward intermediates of gks_flux that its reverse reads (the tau = 0 reading's part), as a
+// tape of doubles: the three Maxwellians (rho, 1/rho, U, V, p, 1/(2 lambda), 2 lambda, f4, qK),
+// their moments (mu[7], mv[6], mx[3]), the slope coefficients, the compatibility right-hand side,
+// the equilibrium state and slopes, the kinetic-weighting moments, the flux moments and the
+// pressure ratio of tau_n.  A reverse sweep can read them back instead of recomputing the flux.
+enum GksTapeField {
+    TG_SL = 0, TG_SR = 9, TG_SC = 18, TG_ML = 27, TG_MR = 43, TG_MC = 59,
+    TG_ALX = 75, TG_ALY = 79, TG_ARX = 83, TG_ARY = 87, TG_ACX = 91, TG_ACY = 95, TG_AC = 99, TG_BCT = 103,
+    TG_WC = 107, TG_WCX = 111, TG_WCY = 115,
+    TG_PL0 = 119, TG_PR0 = 123, TG_LX0 = 127, TG_RX0 = 131, TG_LY0 = 135, TG_RY0 = 139,
+    TG_MC0 = 143, TG_MC1 = 147, TG_MC2 = 151, TG_ML0 = 155, TG_MR0 = 159, TG_ML1 = 163, TG_MR1 = 167,
+    TG_Q = 171, TG_COUNT = 172
+};
+
+
+template <class Tape>
+DFK_HD void tape_maxw(const Tape& tp, int b, const Maxw& s) {
+    tp.put(b, s.rho); tp.put(b + 1, s.ir); tp.put(b + 2, s.U); tp.put(b + 3, s.V); tp.put(b + 4, s.p);
+    tp.put(b + 5, s.il2); tp.put(b + 6, s.tl); tp.put(b + 7, s.f4); tp.put(b + 8, s.qK);
+}
+template <class Tape>
+DFK_HD void tape_mom(const Tape& tp, int b, const Mom& m) {
+#pragma unroll
+    for (int n = 0; n < 7; ++n) tp.put(b + n, m.mu[n]);
+#pragma unroll
+    for (int n = 0; n < 6; ++n) tp.put(b + 7 + n, m.mv[n]);
+#pragma unroll
+    for (int n = 0; n < 3; ++n) tp.put(b + 13 + n, m.mx[n]);
+}
+template <class Tape>
+DFK_HD void tape_vec(const Tape& tp, int b, const double v[4]) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) tp.put(b + i, v[i]);
+}
+
+template <class Tape>
+DFK_HD void gks_flux_t(const GPState& L, const GPState& R, double dt, const SchemeConsts& S,
+                       double F[4], double dF[4], const Tape& tp) {
     const double K = S.K;
     Maxw sl = maxw_of(L.W, S), sr = maxw_of(R.W, S);
     Mom ml, mr;
@@ -305,20 +394,28 @@ DFK_HD void gks_flux(const GPState& L, const GPState& R, double dt, const Scheme
 #pragma unroll
     for (int i = 0; i < 4; ++i) b[i] = R.Wt[i] * irr;
     slope_solve(sr, b, ary);
+    tape_maxw(tp, TG_SL, sl); tape_maxw(tp, TG_SR, sr);
+    tape_mom(tp, TG_ML, ml); tape_mom(tp, TG_MR, mr);
+    tape_vec(tp, TG_ALX, alx); tape_vec(tp, TG_ALY, aly); tape_vec(tp, TG_ARX, arx); tape_vec(tp, TG_ARY, ary);
     // Sect. 3.4: equilibrium state and slopes by kinetic weighting
     double Wc[4], Wcx[4], Wcy[4], t1[4], t2[4];
     psi_mom<0, 0, 0>(ml, t1); psi_mom<0, 0, 0>(mr, t2);
+    tape_vec(tp, TG_PL0, t1); tape_vec(tp, TG_PR0, t2);
 #pragma unroll
     for (int i = 0; i < 4; ++i) Wc[i] = sl.rho * t1[i] + sr.rho * t2[i];
     a_mom<0, 0>(ml, alx, t1); a_mom<0, 0>(mr, arx, t2);
+    tape_vec(tp, TG_LX0, t1); tape_vec(tp, TG_RX0, t2);
 #pragma unroll
     for (int i = 0; i < 4; ++i) Wcx[i] = sl.rho * t1[i] + sr.rho * t2[i];
     a_mom<0, 0>(ml, aly, t1); a_mom<0, 0>(mr, ary, t2);
+    tape_vec(tp, TG_LY0, t1); tape_vec(tp, TG_RY0, t2);
 #pragma unroll
     for (int i = 0; i < 4; ++i) Wcy[i] = sl.rho * t1[i] + sr.rho * t2[i];
+    tape_vec(tp, TG_WC, Wc); tape_vec(tp, TG_WCX, Wcx); tape_vec(tp, TG_WCY, Wcy);
     Maxw sc = maxw_of(Wc, S);
     Mom mc;
     fill_moments<0>(sc, K, mc);
+    tape_maxw(tp, TG_SC, sc); tape_mom(tp, TG_MC, mc);
     double acx[4], acy[4], Ac[4];
     const double irc = sc.ir;
 #pragma unroll
@@ -332,6 +429,7 @@ DFK_HD void gks_flux(const GPState& L, const GPState& R, double dt, const Scheme
 #pragma unroll
     for (int i = 0; i < 4; ++i) b[i] = -(t1[i] + t2[i]);
     slope_solve(sc, b, Ac);
+    tape_vec(tp, TG_ACX, acx); tape_vec(tp, TG_ACY, acy); tape_vec(tp, TG_AC, Ac); tape_vec(tp, TG_BCT, b);
     // moments entering the flux
     double Mc0[4], Mc1[4], Mc2[4], Ml0[4], Mr0[4], Ml1[4], Mr1[4];
     psi_mom<1, 0, 0>(mc, Mc0);
@@ -347,8 +445,12 @@ DFK_HD void gks_flux(const GPState& L, const GPState& R, double dt, const Scheme
     a_mom<2, 0>(mr, arx, t1); a_mom<1, 1>(mr, ary, t2);
 #pragma unroll
     for (int i = 0; i < 4; ++i) Mr1[i] = t1[i] + t2[i];
+    tape_vec(tp, TG_MC0, Mc0); tape_vec(tp, TG_MC1, Mc1); tape_vec(tp, TG_MC2, Mc2);
+    tape_vec(tp, TG_ML0, Ml0); tape_vec(tp, TG_MR0, Mr0); tape_vec(tp, TG_ML1, Ml1); tape_vec(tp, TG_MR1, Mr1);
     // numerical collision time (Sect. 2.2) and the combined time coefficients of Eq. 27
-    double rT = S.C1 + S.C2 * fabs((sl.p - sr.p) / (sl.p + sr.p));   // tau_n / dt
+    const double q = (sl.p - sr.p) / (sl.p + sr.p);
+    tp.put(TG_Q, q);
+    double rT = S.C1 + S.C2 * fabs(q);   // tau_n / dt
     double T = rT * dt;
     double tau = (S.tau_reading == 1) ? T : 0.0;
     double E2 = 0.0, r = 0.0;
@@ -393,6 +495,10 @@ DFK_HD void gks_flux(const GPState& L, const GPState& R, double dt, const Scheme
         F[i] = gcF * c0 + acF * c1 + AcF * c2 + glrF * g0 + alrF * g1 + AlrF * g2;
         dF[i] = gcD * c0 + acD * c1 + AcD * c2 + glrD * g0 + alrD * g1 + AlrD * g2;
     }
+}
+
+DFK_HD void gks_flux(const GPState& L, const GPState& R, double dt, const SchemeConsts& S, double F[4], double dF[4]) {
+    gks_flux_t(L, R, dt, S, F, dF, NoTape{});
 }
 
 // ------------------------------------------------------------------------------------------

@@ -98,6 +98,14 @@ struct SweepBuffers {
     long long gp_stride;
     double* flux[2];        // per direction: FR_COUNT planes of flux_stride[dir] (2 Gauss points x faces)
     long long flux_stride[2];
+    // optional, per direction: the GKS flux's forward intermediates (TG_COUNT planes of
+    // flux_stride[dir]), written by the forward sweep when set and read by the reverse sweep
+    double* tape[2] = {nullptr, nullptr};
+    // optional: the WENO-AO intermediates of the face lines' 8 reconstructions (8 x AT_COUNT planes
+    // of line_stride, reconstruction 2k + side) and of the face sides' 4 tangential ones (4 x AT_COUNT
+    // planes of gp_stride), written by the forward sweep when set and read by the reverse sweep
+    double* ltape = nullptr;
+    double* ftape = nullptr;
 };
 
 enum UpdateMode { UM_RESIDUAL = 0, UM_S2O4_1, UM_S2O4_2, UM_RK_1, UM_RK_2, UM_RK_3, UM_ALPHA };

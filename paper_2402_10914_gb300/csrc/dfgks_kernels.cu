@@ -97,37 +97,38 @@ void launch_end_step(DevState* st, double t_end, cudaStream_t s, KernelTimer* T)
 // DIR 1: y-faces in the frame rotated by pi/2: normal = +y, tangential = -x, so the local
 // tangential offset b maps to global column t - b.  Face f lies between normal cells f-1, f.
 // ---------------------------------------------------------------------------------------------
-template <int DIR>
+template <int DIR, bool TAPE = false>
 __global__ void __launch_bounds__(128) k_lines(Mesh m, SchemeConsts S, const double* __restrict__ W,
                                                const double* __restrict__ alpha, double* __restrict__ lines,
-                                               long long ls, DevState* st, const int* halt) {
+                                               long long ls, DevState* st, const int* halt,
+                                               double* __restrict__ ltape = nullptr) {
     if (halted(halt)) return;
-    int ndf = lines_body<DIR>(m, S, W, alpha, lines, ls, blockIdx.x * blockDim.x + threadIdx.x,
-                              blockIdx.y * blockDim.y + threadIdx.y);
+    int ndf = lines_body<DIR, TAPE>(m, S, W, alpha, lines, ls, blockIdx.x * blockDim.x + threadIdx.x,
+                                    blockIdx.y * blockDim.y + threadIdx.y, ltape);
     if (st) warp_count_add(&st->df_normal, ndf);
 }
 
-template <int DIR>
+template <int DIR, bool TAPE = false>
 __global__ void __launch_bounds__(128) k_faces(Mesh m, SchemeConsts S, const double* __restrict__ W,
                                                const double* __restrict__ alpha, const double* __restrict__ lines,
                                                long long ls, double* __restrict__ gp, long long gs,
-                                               DevState* st, const int* halt) {
+                                               DevState* st, const int* halt, double* __restrict__ ftape = nullptr) {
     if (halted(halt)) return;
     int nfb;
-    int ndf = faces_body<DIR>(m, S, W, alpha, lines, ls, gp, gs, blockIdx.x * blockDim.x + threadIdx.x,
-                              blockIdx.y * blockDim.y + threadIdx.y, blockIdx.z, nfb);
+    int ndf = faces_body<DIR, TAPE>(m, S, W, alpha, lines, ls, gp, gs, blockIdx.x * blockDim.x + threadIdx.x,
+                                    blockIdx.y * blockDim.y + threadIdx.y, blockIdx.z, nfb, ftape);
     if (st) { warp_count_add(&st->df_tangential, ndf); warp_count_add(&st->fallbacks, nfb); }
 }
 
-template <int DIR, int FLUX, bool ALPHA_ONLY>
+template <int DIR, int FLUX, bool ALPHA_ONLY, bool TAPE = false>
 __global__ void __launch_bounds__(128) k_flux(Mesh m, SchemeConsts S, const double* __restrict__ lines,
                                               long long ls, const double* __restrict__ gp, long long gs,
                                               double* __restrict__ fr, long long fs, const double* dtp,
-                                              const int* halt) {
+                                              const int* halt, double* __restrict__ tape = nullptr) {
     if (halted(halt)) return;
-    flux_body<DIR, FLUX, ALPHA_ONLY>(m, S, lines, ls, gp, gs, fr, fs, ALPHA_ONLY ? 0.0 : *dtp,
-                                     blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y,
-                                     blockIdx.z);
+    flux_body<DIR, FLUX, ALPHA_ONLY, TAPE>(m, S, lines, ls, gp, gs, fr, fs, ALPHA_ONLY ? 0.0 : *dtp,
+                                           blockIdx.x * blockDim.x + threadIdx.x,
+                                           blockIdx.y * blockDim.y + threadIdx.y, blockIdx.z, tape);
 }
 
 template <int DIR>
@@ -140,17 +141,24 @@ static void sweep_dir(const Mesh& m, const SchemeConsts& S, int flux, bool alpha
     int lx = DIR == 0 ? nn + 1 : nt + 4, ly = DIR == 0 ? nt + 4 : nn + 1;
     dim3 gl((lx + 31) / 32, (ly + 3) / 4);
     if (T) T->begin(KK_LINES);
-    k_lines<DIR><<<gl, blk, 0, s>>>(m, S, W, alpha, B.lines, B.line_stride, st, halt);
+    if (B.ltape) k_lines<DIR, true><<<gl, blk, 0, s>>>(m, S, W, alpha, B.lines, B.line_stride, st, halt, B.ltape);
+    else k_lines<DIR><<<gl, blk, 0, s>>>(m, S, W, alpha, B.lines, B.line_stride, st, halt);
     if (T) T->end(KK_LINES, 1);
     int fx = DIR == 0 ? nn + 1 : nt, fy = DIR == 0 ? nt : nn + 1;
     dim3 gf((fx + 31) / 32, (fy + 3) / 4, 2);
     if (T) T->begin(KK_FACES);
-    k_faces<DIR><<<gf, blk, 0, s>>>(m, S, W, alpha, B.lines, B.line_stride, B.gp, B.gp_stride, st, halt);
+    if (B.ftape)
+        k_faces<DIR, true><<<gf, blk, 0, s>>>(m, S, W, alpha, B.lines, B.line_stride, B.gp, B.gp_stride, st, halt, B.ftape);
+    else
+        k_faces<DIR><<<gf, blk, 0, s>>>(m, S, W, alpha, B.lines, B.line_stride, B.gp, B.gp_stride, st, halt);
     if (T) T->end(KK_FACES, 1);
     double* fr = B.flux[DIR];
     long long fs = B.flux_stride[DIR];
     if (T) T->begin(KK_FLUX);
     if (alpha_only) k_flux<DIR, 1, true><<<gf, blk, 0, s>>>(m, S, B.lines, B.line_stride, B.gp, B.gp_stride, fr, fs, dtp, halt);
+    else if (flux == 0 && B.tape[DIR])      // GKS forward that also tapes its intermediates for a reverse sweep
+        k_flux<DIR, 0, false, true><<<gf, blk, 0, s>>>(m, S, B.lines, B.line_stride, B.gp, B.gp_stride, fr, fs, dtp, halt,
+                                                       B.tape[DIR]);
     else if (flux == 0) k_flux<DIR, 0, false><<<gf, blk, 0, s>>>(m, S, B.lines, B.line_stride, B.gp, B.gp_stride, fr, fs, dtp, halt);
     else k_flux<DIR, 1, false><<<gf, blk, 0, s>>>(m, S, B.lines, B.line_stride, B.gp, B.gp_stride, fr, fs, dtp, halt);
     if (T) T->end(KK_FLUX, 1);

@@ -1,7 +1,8 @@
 // Host build of the CUDA path's per-thread bodies: the stage operator (ghost fill, both sweeps,
 // residual) and its reverse sweep, run one body invocation at a time on the CPU exactly as the
 // kernels call them.  Reads a problem from argv[1] (the In header, then W, alpha, L_bar, dtL_bar,
-// dtLt_bar as dense doubles) and writes L, dL/dt, limited dL/dt and W_bar to argv[2].  Used by
+// dtLt_bar as dense doubles) and writes L, dL/dt, limited dL/dt, W_bar, and W_bar once more with the
+// reverse sweep reading the tapes of the forward intermediates, to argv[2].  Used by
 // tests/test_host_emulation.py, which compares the results with the oracle.
 #include <algorithm>
 #include <cstdio>
@@ -63,12 +64,18 @@ int main(int argc, char** argv) {
         const int nn = DIR == 0 ? m.nx : m.ny, nt = DIR == 0 ? m.ny : m.nx;
         int lx = DIR == 0 ? nn + 1 : nt + 4, ly = DIR == 0 ? nt + 4 : nn + 1;
         int fx = DIR == 0 ? nn + 1 : nt, fy = DIR == 0 ? nt : nn + 1;
-        for (int y = 0; y < ly; ++y) for (int x = 0; x < lx; ++x) lines_body<DIR>(m, S, Wg.data(), Ag.data(), B.lines, B.line_stride, x, y);
-        for (int z = 0; z < 2; ++z) for (int y = 0; y < fy; ++y) for (int x = 0; x < fx; ++x) {
-            int nfb; faces_body<DIR>(m, S, Wg.data(), Ag.data(), B.lines, B.line_stride, B.gp, B.gp_stride, x, y, z, nfb);
+        for (int y = 0; y < ly; ++y) for (int x = 0; x < lx; ++x) {
+            if (B.ltape) lines_body<DIR, true>(m, S, Wg.data(), Ag.data(), B.lines, B.line_stride, x, y, B.ltape);
+            else lines_body<DIR>(m, S, Wg.data(), Ag.data(), B.lines, B.line_stride, x, y);
         }
         for (int z = 0; z < 2; ++z) for (int y = 0; y < fy; ++y) for (int x = 0; x < fx; ++x) {
-            if (in.flux == 0) flux_body<DIR, 0, false>(m, S, B.lines, B.line_stride, B.gp, B.gp_stride, B.flux[DIR], B.flux_stride[DIR], in.dt, x, y, z);
+            int nfb;
+            if (B.ftape) faces_body<DIR, true>(m, S, Wg.data(), Ag.data(), B.lines, B.line_stride, B.gp, B.gp_stride, x, y, z, nfb, B.ftape);
+            else faces_body<DIR>(m, S, Wg.data(), Ag.data(), B.lines, B.line_stride, B.gp, B.gp_stride, x, y, z, nfb);
+        }
+        for (int z = 0; z < 2; ++z) for (int y = 0; y < fy; ++y) for (int x = 0; x < fx; ++x) {
+            if (in.flux == 0 && B.tape[DIR]) flux_body<DIR, 0, false, true>(m, S, B.lines, B.line_stride, B.gp, B.gp_stride, B.flux[DIR], B.flux_stride[DIR], in.dt, x, y, z, B.tape[DIR]);
+            else if (in.flux == 0) flux_body<DIR, 0, false>(m, S, B.lines, B.line_stride, B.gp, B.gp_stride, B.flux[DIR], B.flux_stride[DIR], in.dt, x, y, z);
             else flux_body<DIR, 1, false>(m, S, B.lines, B.line_stride, B.gp, B.gp_stride, B.flux[DIR], B.flux_stride[DIR], in.dt, x, y, z);
         }
     };
@@ -80,13 +87,20 @@ int main(int argc, char** argv) {
         std::fill(lb.begin(), lb.end(), 0.0);
         std::fill(gb.begin(), gb.end(), -9.0);
         for (int z = 0; z < 2; ++z) for (int y = 0; y < fy; ++y) for (int x = 0; x < fx; ++x) {
-            if (in.flux == 0) ka_flux_body<DIR, 0>(m, S, a, B.gp, B.gp_stride, B.flux[DIR], B.flux_stride[DIR], in.dt, lb.data(), B.line_stride, gb.data(), x, y, z);
+            if (in.flux == 0 && B.tape[DIR]) ka_flux_body<DIR, 0, true>(m, S, a, B.gp, B.gp_stride, B.flux[DIR], B.flux_stride[DIR], in.dt, lb.data(), B.line_stride, gb.data(), x, y, z, B.tape[DIR]);
+            else if (in.flux == 0) ka_flux_body<DIR, 0>(m, S, a, B.gp, B.gp_stride, B.flux[DIR], B.flux_stride[DIR], in.dt, lb.data(), B.line_stride, gb.data(), x, y, z);
             else ka_flux_body<DIR, 1>(m, S, a, B.gp, B.gp_stride, B.flux[DIR], B.flux_stride[DIR], in.dt, lb.data(), B.line_stride, gb.data(), x, y, z);
         }
         for (int z = 0; z < 2; ++z) for (int y = 0; y < fy; ++y) for (int x = 0; x < fx; ++x)
-            ka_faces_body<DIR>(m, S, Ag.data(), B.lines, B.line_stride, B.gp, gb.data(), B.gp_stride, lb.data(), Wbg.data(), x, y, z);
+        {
+            if (B.ftape) ka_faces_body<DIR, true>(m, S, Ag.data(), B.lines, B.line_stride, B.gp, gb.data(), B.gp_stride, lb.data(), Wbg.data(), x, y, z, B.ftape);
+            else ka_faces_body<DIR>(m, S, Ag.data(), B.lines, B.line_stride, B.gp, gb.data(), B.gp_stride, lb.data(), Wbg.data(), x, y, z);
+        }
         for (int y = 0; y < ly; ++y) for (int x = 0; x < lx; ++x)
-            ka_lines_body<DIR>(m, S, Wg.data(), Ag.data(), B.lines, lb.data(), B.line_stride, Wbg.data(), x, y);
+        {
+            if (B.ltape) ka_lines_body<DIR, true>(m, S, Wg.data(), Ag.data(), B.lines, lb.data(), B.line_stride, Wbg.data(), x, y, B.ltape);
+            else ka_lines_body<DIR>(m, S, Wg.data(), Ag.data(), B.lines, lb.data(), B.line_stride, Wbg.data(), x, y);
+        }
     };
     // forward residual (both directions), for a sanity check of the emulation
     sweep(std::integral_constant<int, 0>());
@@ -96,14 +110,25 @@ int main(int argc, char** argv) {
     for (int j = 0; j < m.ny; ++j) for (int i = 0; i < m.nx; ++i)
         update_body<UM_RESIDUAL>(m, S, ua, B.flux[0], B.flux_stride[0], B.flux[1], B.flux_stride[1], 0.0, nullptr, i, j);
     // reverse
-    sweep(std::integral_constant<int, 0>()); reverse(std::integral_constant<int, 0>());
-    sweep(std::integral_constant<int, 1>()); reverse(std::integral_constant<int, 1>());
-    for (int i = -G; i < m.nx + G; ++i) ka_fold_y_body(m, Wbg.data(), i);
-    for (int j = 0; j < m.ny; ++j) ka_fold_x_body(m, Wbg.data(), j);
-    for (int j = 0; j < m.ny; ++j) for (int i = 0; i < m.nx; ++i) ka_accumulate_body(m, Wbg.data(), out.data(), i, j);
+    auto adjoint = [&](std::vector<double>& res) {
+        std::fill(Wbg.begin(), Wbg.end(), 0.0);
+        std::fill(res.begin(), res.end(), 0.0);
+        sweep(std::integral_constant<int, 0>()); reverse(std::integral_constant<int, 0>());
+        sweep(std::integral_constant<int, 1>()); reverse(std::integral_constant<int, 1>());
+        for (int i = -G; i < m.nx + G; ++i) ka_fold_y_body(m, Wbg.data(), i);
+        for (int j = 0; j < m.ny; ++j) ka_fold_x_body(m, Wbg.data(), j);
+        for (int j = 0; j < m.ny; ++j) for (int i = 0; i < m.nx; ++i) ka_accumulate_body(m, Wbg.data(), res.data(), i, j);
+    };
+    adjoint(out);
+    // the same with the reconstructions' and the GKS flux's intermediates taped by the forward sweep
+    std::vector<double> tape0(TG_COUNT * B.flux_stride[0], -7.0), tape1(TG_COUNT * B.flux_stride[1], -7.0), out2(4 * N, 0.0);
+    std::vector<double> ltape(8 * AT_COUNT * B.line_stride, -7.0), ftape(4 * AT_COUNT * B.gp_stride, -7.0);
+    B.tape[0] = tape0.data(); B.tape[1] = tape1.data();
+    B.ltape = ltape.data(); B.ftape = ftape.data();
+    adjoint(out2);
     f = fopen(argv[2], "wb");
     if (!f) return 2;
-    fwrite(L.data(), 8, 4 * N, f); fwrite(dL.data(), 8, 4 * N, f); fwrite(dLt.data(), 8, 4 * N, f); fwrite(out.data(), 8, 4 * N, f);
+    fwrite(L.data(), 8, 4 * N, f); fwrite(dL.data(), 8, 4 * N, f); fwrite(dLt.data(), 8, 4 * N, f); fwrite(out.data(), 8, 4 * N, f); fwrite(out2.data(), 8, 4 * N, f);
     fclose(f);
     return 0;
 }

@@ -41,7 +41,7 @@ def emu(tmp_path_factory):
         r = subprocess.run([exe, fin, fout], capture_output=True, text=True, timeout=300,
                            env=dict(os.environ, ASAN_OPTIONS="detect_leaks=0"))
         assert r.returncode == 0, r.stderr[-2000:]
-        return np.fromfile(fout).reshape(4, 4, s.ny, s.nx)
+        return np.fromfile(fout).reshape(5, 4, s.ny, s.nx)
     return run
 
 
@@ -78,3 +78,4 @@ def test_host_build_matches_oracle(emu, name, make, akind):
     assert rel(out[0], L) <= 1e-12 and rel(out[1], dL) <= 1e-11 and rel(out[2], dLt) <= 1e-7
     ref = oracle.residual_vjp(s, w.W0, alpha, dt, Lb, dLb, dLtb)
     assert rel(out[3], ref) <= 1e-12, rel(out[3], ref)
+    assert rel(out[4], ref) <= 1e-12, rel(out[4], ref)        # GKS reverse from the forward's tape
