@@ -41,11 +41,11 @@ FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
 # FP64 flops the Gauss-point flux kernel executes per Gauss point (GKS): ncu instruction counts
 # 2*DFMA + DADD + DMUL of one launch divided by its 2*(n+1)*n Gauss points
 # (profiles/k_flux_gks_fp64_counts_quadrants128.md).  Valid for the kernel source it was measured on.
-FLUX_GKS_FLOPS_PER_GP = 1866.0
+FLUX_GKS_FLOPS_PER_GP = 1773.0
 # DRAM bytes (read + write) per launch of that kernel on this workload, mean of the x and y launches
 # of one ncu capture at 400 x 400 (profiles/k_flux_gks_traffic_quadrants400.md); None once the
 # kernel has changed since the capture.
-FLUX_GKS_TRAFFIC_BYTES = 65.1e6
+FLUX_GKS_TRAFFIC_BYTES = 64.75e6
 # steps of the oracle's timed sample (about 0.9 s each at 400 x 400 on 16 Arm cores)
 CPU_SAMPLE_STEPS = 12
 
