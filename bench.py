@@ -57,9 +57,12 @@ def parse():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--n", type=int, default=400, help="mesh side of the four-quadrant workload")
-    p.add_argument("--workload", default="quadrants", choices=["quadrants", "batch", "adjoint"],
+    p.add_argument("--workload", default="quadrants", choices=["quadrants", "batch", "adjoint", "blast"],
                    help="quadrants: the 400x400 GKS step (default); batch: the 64-problem uneven batch; "
-                        "adjoint: gradient / forward time on the 256x256 vortex, 100 steps")
+                        "adjoint: gradient / forward time on the 256x256 vortex, 100 steps; "
+                        "blast: the 1e6 pressure-ratio blast run to its end time")
+    p.add_argument("--blast-n", type=int, default=2048, help="mesh side of the blast workload")
+    p.add_argument("--blast-t", type=float, default=0.01, help="end time of the blast workload")
     p.add_argument("--no-adjoint", action="store_true", help="leave the adjoint summary out of the default line")
     p.add_argument("--adj-n", type=int, default=256, help="mesh side of the adjoint workload")
     p.add_argument("--adj-steps", type=int, default=100, help="S2O4 steps of the adjoint workload")
@@ -308,6 +311,48 @@ def bench_batch(args):
     print(json.dumps(line))
 
 
+def bench_blast(args):
+    """The extreme robustness run: 1e6 pressure ratio, reflecting walls, GKS, CFL 0.4, run to its end
+    time with positivity checked on the device every step.  Reports the whole run's throughput."""
+    import torch
+    from paper_2402_10914_gb300 import _lib, inputs as I
+    from paper_2402_10914_gb300.solver import Solver
+    w = I.blast(args.blast_n, t_end=args.blast_t)
+    s = w.settings
+    sol = Solver(s)
+    sol.set_ic(w.W0)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(0)
+    torch.cuda.synchronize()
+    clocks.start()
+    a.record(sol.stream)
+    status = "reached t_end"
+    try:
+        sol.run(t_end=w.t_end, chunk=256)
+    except _lib.DfgksError as e:
+        status = "stopped: %s" % e
+    b.record(sol.stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = a.elapsed_time(b)
+    W, alpha, t, steps = sol.get_state()
+    cnt = sol.counters()
+    p = (s.gamma - 1.0) * (W[3] - 0.5 * (W[1] ** 2 + W[2] ** 2) / W[0])
+    sol.close()
+    units = 2.0 * s.nx * s.ny * steps
+    line = {"metric": "FP64 cell-stage updates/s (1e6 pressure-ratio blast, %dx%d, to t=%g)" % (s.nx, s.ny, w.t_end),
+            "value": units / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": int(steps), "warmup": 0,
+            "ms_per_step": ms / max(steps, 1), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "blast_%dx%d_t%g" % (s.nx, s.ny, w.t_end), "flux": "GKS", "cfl": s.cfl,
+                       "bc": "reflecting", "time_limiter": 1},
+            "blast": {"status": status, "t": t, "min_rho": float(W[0].min()), "min_p": float(p.min()),
+                      "gauss_point_fallbacks": cnt["fallbacks"], "df_normal": cnt["df_normal"],
+                      "df_tangential": cnt["df_tangential"], "wall_ms": ms},
+            "clocks": clk}
+    print(json.dumps(line))
+
+
 def adj_workload(n: int, nsteps: int, ckpt: int = 10) -> str:
     return "vortex_%dx%d_gks_%dsteps_ckpt%d" % (n, n, nsteps, ckpt)
 
@@ -418,6 +463,10 @@ def main():
     if args.workload == "batch":
         if rank == 0:
             bench_batch(args)
+        return
+    if args.workload == "blast":
+        if rank == 0:
+            bench_blast(args)
         return
     if args.workload == "adjoint":
         if rank == 0:

@@ -56,7 +56,7 @@ typedef struct dfgks_config {
     int nx, ny;                    /* interior cells, each >= 1 (>= 3 along a periodic direction) */
     double x0, x1, y0, y1;         /* domain [x0,x1] x [y0,y1] */
     double gamma;                  /* specific heat ratio; K = (4 - 2 gamma)/(gamma - 1) (Sect. 2.2) */
-    double cfl;                    /* dt = cfl * min over cells of min(dx/(|U|+c), dy/(|V|+c)) */
+    double cfl;                    /* dt = cfl * min over cells of the dt_rule bound */
     int bc_xlo, bc_xhi, bc_ylo, bc_yhi;   /* dfgks_bc */
     double alpha_thres;            /* DF threshold of Eq. 34 (paper: 0.5) */
     double dH, dL;                 /* WENO-AO linear-weight parameters (paper: 0.85, 0.85) */
@@ -66,6 +66,8 @@ typedef struct dfgks_config {
     int tau_reading;               /* 0: physical tau = 0 outside the exponentials; 1: tau = tau_n */
     int gp_fallback;               /* 1: Gauss-point states with rho <= 0 or p <= 0 use the cell average */
     int time_scheme;               /* dfgks_time_scheme */
+    int dt_rule;                   /* CFL bound per cell (Alg. 1 gives no formula): 0 min(dx/(|U|+c), dy/(|V|+c)),
+                                      1 1/((|U|+c)/dx + (|V|+c)/dy) */
 } dfgks_config;
 
 typedef struct dfgks dfgks;        /* opaque; owns every device buffer it uses */

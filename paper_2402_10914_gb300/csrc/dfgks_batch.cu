@@ -305,7 +305,7 @@ static bool batch_config_ok(const dfgks_config* c) {
     if ((c->bc_xlo == 0) != (c->bc_xhi == 0) || (c->bc_ylo == 0) != (c->bc_yhi == 0)) return false;
     if (c->bc_xlo == 0 && c->nx < G) return false;
     if (c->bc_ylo == 0 && c->ny < G) return false;
-    return c->time_scheme == 0 && (c->tau_reading == 0 || c->tau_reading == 1);
+    return c->time_scheme == 0 && (c->tau_reading == 0 || c->tau_reading == 1) && (c->dt_rule == 0 || c->dt_rule == 1);
 }
 
 extern "C" DFGKS_API dfgks_status dfgks_batch_create(const dfgks_config* cfgs, const int* flux, int np, void* stream,
@@ -345,6 +345,7 @@ extern "C" DFGKS_API dfgks_status dfgks_batch_create(const dfgks_config* cfgs, c
         m.dx = (c->x1 - c->x0) / c->nx;
         m.dy = (c->y1 - c->y0) / c->ny;
         m.bc[0] = c->bc_xlo; m.bc[1] = c->bc_xhi; m.bc[2] = c->bc_ylo; m.bc[3] = c->bc_yhi;
+        m.dt_rule = c->dt_rule;
         SchemeConsts& S = q.S;
         S.gamma = c->gamma; S.gm1 = c->gamma - 1.0; S.K = (4.0 - 2.0 * c->gamma) / (c->gamma - 1.0);
         S.inv_K2 = 1.0 / (S.K + 2.0);

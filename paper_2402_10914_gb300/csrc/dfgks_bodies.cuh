@@ -70,13 +70,14 @@ DFK_HD bool state_ok(const double W[4], double gm1) {
     return fin && physical_state(W, gm1);
 }
 
-// CFL bound of one interior cell: min(dx/(|U|+c), dy/(|V|+c))
+// CFL bound of one interior cell: min(dx/(|U|+c), dy/(|V|+c)), or 1/((|U|+c)/dx + (|V|+c)/dy)
 __device__ __forceinline__ double cfl_cell(const Mesh& m, const double* W, double gamma, int c) {
     int i = c % m.nx, j = c / m.nx;
     long long g = gid(m, i, j);
     double r = W[g], U = W[m.plane + g] / r, V = W[2 * m.plane + g] / r;
     double p = (gamma - 1.0) * (W[3 * m.plane + g] - 0.5 * r * (U * U + V * V));
     double cs = sqrt(gamma * p / r);
+    if (m.dt_rule) return 1.0 / ((fabs(U) + cs) / m.dx + (fabs(V) + cs) / m.dy);
     return fmin(m.dx / (fabs(U) + cs), m.dy / (fabs(V) + cs));
 }
 

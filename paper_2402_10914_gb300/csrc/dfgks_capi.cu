@@ -89,6 +89,7 @@ extern "C" dfgks_status dfgks_config_default(dfgks_config* c, int nx, int ny) {
     c->bc_xlo = c->bc_xhi = c->bc_ylo = c->bc_yhi = DFGKS_BC_OUTFLOW;
     c->alpha_thres = 0.5; c->dH = 0.85; c->dL = 0.85; c->eps = 1e-6; c->C1 = 0.01; c->C2 = 5.0;
     c->time_limiter = 1; c->tau_reading = 0; c->gp_fallback = 1; c->time_scheme = DFGKS_TIME_S2O4;
+    c->dt_rule = 0;
     return DFGKS_OK;
 }
 
@@ -106,6 +107,7 @@ static bool config_ok(const dfgks_config* c) {
     if (c->bc_ylo == 0 && c->ny < G) return false;
     if (c->time_scheme != 0 && c->time_scheme != 1) return false;
     if (c->tau_reading != 0 && c->tau_reading != 1) return false;
+    if (c->dt_rule != 0 && c->dt_rule != 1) return false;
     return true;
 }
 
@@ -172,6 +174,7 @@ extern "C" dfgks_status dfgks_create(const dfgks_config* cfg, void* stream, dfgk
     m.dx = (cfg->x1 - cfg->x0) / cfg->nx;
     m.dy = (cfg->y1 - cfg->y0) / cfg->ny;
     m.bc[0] = cfg->bc_xlo; m.bc[1] = cfg->bc_xhi; m.bc[2] = cfg->bc_ylo; m.bc[3] = cfg->bc_yhi;
+    m.dt_rule = cfg->dt_rule;
     SchemeConsts& S = h->S;
     S.gamma = cfg->gamma; S.gm1 = cfg->gamma - 1.0; S.K = (4.0 - 2.0 * cfg->gamma) / (cfg->gamma - 1.0);
     S.inv_K2 = 1.0 / (S.K + 2.0);

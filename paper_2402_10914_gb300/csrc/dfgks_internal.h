@@ -57,6 +57,7 @@ struct Mesh {
     long long plane;    // P * NYg
     double dx, dy;
     int bc[4];          // x-low, x-high, y-low, y-high
+    int dt_rule;        // CFL bound per cell: 0 per-direction minimum, 1 summed inverse
 };
 
 __host__ __device__ __forceinline__ long long gid(const Mesh& m, int i, int j) {

@@ -103,7 +103,7 @@ def run_both(w, nsteps, t_end=0.0, dt_fixed=0.0):
 
 
 @pytest.mark.parametrize("name", ["c1", "quadrants", "rough_periodic", "rough_reflect", "blast", "vortex", "ssprk3",
-                                  "tau_reading_a", "no_limiter_gks"])
+                                  "tau_reading_a", "no_limiter_gks", "dt_rule_sum"])
 def test_one_step_parity(name):
     if name == "c1":
         w = I.sine_c1(40)
@@ -123,6 +123,9 @@ def test_one_step_parity(name):
     elif name == "tau_reading_a":
         w = rough(20, 18, seed=10, flux=I.GKS)
         w.settings = w.settings.with_(tau_reading=1)
+    elif name == "dt_rule_sum":
+        w = rough(20, 18, seed=13, flux=I.GKS)
+        w.settings = w.settings.with_(dt_rule=1)
     else:
         w = rough(20, 18, seed=12, flux=I.GKS)
         w.settings = w.settings.with_(time_limiter=0)

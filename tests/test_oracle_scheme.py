@@ -256,3 +256,16 @@ def test_blast_positivity_small():
     # reflecting walls conserve mass exactly and the blast is symmetric under x <-> y
     assert abs(W[0].sum() - w.W0[0].sum()) <= 1e-13 * w.W0[0].sum()
     assert np.allclose(W[0], W[0].T, rtol=1e-12)
+
+
+@pytest.mark.parametrize("rule", [0, 1])
+def test_cfl_step_closed_forms(rule):
+    # a uniform moving state on a non-square mesh: dt = CFL * min(dx/(|U|+c), dy/(|V|+c)) (rule 0)
+    # or CFL / ((|U|+c)/dx + (|V|+c)/dy) (rule 1), with c = sqrt(gamma p / rho)
+    s = I.Settings(nx=12, ny=7, x1=2.0, y1=0.5, cfl=0.45, dt_rule=rule)
+    rho, u, v, p = 1.3, -0.7, 0.4, 2.1
+    W = np.broadcast_to(I.conserved(rho, u, v, p, s.gamma)[:, None, None], (4, s.ny, s.nx)).copy()
+    c = np.sqrt(s.gamma * p / rho)
+    dx, dy = 2.0 / 12, 0.5 / 7
+    want = min(dx / (abs(u) + c), dy / (abs(v) + c)) if rule == 0 else 1.0 / ((abs(u) + c) / dx + (abs(v) + c) / dy)
+    assert oracle.cfl_dt(s, W) == pytest.approx(s.cfl * want, rel=1e-14)
