@@ -677,58 +677,63 @@ static dfgks_status backward_checkpointed(dfgks* h, const double* WT_bar, double
     if (r) { cleanup(); return r; }
     r = ensure_adjoint_buffers(h);
     if (r) { cleanup(); return r; }
-    CK(cudaMemcpyAsync(h->st_host, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
-    CK(cudaStreamSynchronize(h->stream));
-    const DevState stT = *h->st_host;
-    launch_ghosted_to_dense(m, h->W[h->cur], 4, WTs, h->stream);
-    launch_ghosted_to_dense(m, h->A[h->cur], 1, ATs, h->stream);
-    CK(cudaMemcpyAsync(Wb, WT_bar, (size_t)N4 * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
-    for (int seg = nseg - 1; seg >= 0 && r == DFGKS_OK; --seg) {
-        const int s0 = seg * k, s1 = (s0 + k < n) ? s0 + k : n;
-        if (!(kept && seg == nseg - 1)) {
-            // recompute the segment from its checkpoint, keeping W^s, alpha^s, W* and the records
-            launch_dense_to_ghosted(m, h->ck_W + (long long)seg * N4, 4, h->W[h->cur], h->stream);
-            launch_dense_to_ghosted(m, h->ck_A + (long long)seg * N, 1, h->A[h->cur], h->stream);
-            for (int s = s0; s < s1; ++s) {
-                launch_ghosted_to_dense(m, h->W[h->cur], 4, a.W + (s - s0) * N4, h->stream);
-                launch_ghosted_to_dense(m, h->A[h->cur], 1, a.A + (s - s0) * N, h->stream);
+    // the passes; a CUDA error returns from this lambda, and the scratch is freed either way
+    auto passes = [&]() -> dfgks_status {
+        CK(cudaMemcpyAsync(h->st_host, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        const DevState stT = *h->st_host;
+        launch_ghosted_to_dense(m, h->W[h->cur], 4, WTs, h->stream);
+        launch_ghosted_to_dense(m, h->A[h->cur], 1, ATs, h->stream);
+        CK(cudaMemcpyAsync(Wb, WT_bar, (size_t)N4 * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+        for (int seg = nseg - 1; seg >= 0 && r == DFGKS_OK; --seg) {
+            const int s0 = seg * k, s1 = (s0 + k < n) ? s0 + k : n;
+            if (!(kept && seg == nseg - 1)) {
+                // recompute the segment from its checkpoint, keeping W^s, alpha^s, W* and the records
+                launch_dense_to_ghosted(m, h->ck_W + (long long)seg * N4, 4, h->W[h->cur], h->stream);
+                launch_dense_to_ghosted(m, h->ck_A + (long long)seg * N, 1, h->A[h->cur], h->stream);
+                for (int s = s0; s < s1; ++s) {
+                    launch_ghosted_to_dense(m, h->W[h->cur], 4, a.W + (s - s0) * N4, h->stream);
+                    launch_ghosted_to_dense(m, h->A[h->cur], 1, a.A + (s - s0) * N, h->stream);
+                    SweepBuffers rec[4];
+                    if (a.recs) record_sets(h, a.recs + (long long)(s - s0) * a.rec_step, a.tape, a.gks, rec);
+                    enqueue_step(h, 0, dts[s], flux, 0.0, h->cur, a.Ws + (s - s0) * N4, a.recs ? rec : nullptr);
+                    h->cur ^= 1;
+                }
+            }
+            // reverse through the segment: Eq. 24 with the time limiter,
+            //   W* = W + dt/2 L + dt^2/8 dL,  W' = W + dt L + dt^2/2 dL - dt^2/3 dLt + dt^2/3 dLt(W*)
+            for (int s = s1 - 1; s >= s0 && r == DFGKS_OK; --s) {
+                const double dt = dts[s], dt2 = dt * dt;
+                const double* Wn = a.W + (s - s0) * N4;
+                const double* An = a.A + (s - s0) * N;
+                const double* Wst = a.Ws + (s - s0) * N4;
                 SweepBuffers rec[4];
                 if (a.recs) record_sets(h, a.recs + (long long)(s - s0) * a.rec_step, a.tape, a.gks, rec);
-                enqueue_step(h, 0, dts[s], flux, 0.0, h->cur, a.Ws + (s - s0) * N4, a.recs ? rec : nullptr);
-                h->cur ^= 1;
+                CK(cudaMemsetAsync(Wsb, 0, (size_t)N4 * sizeof(double), h->stream));
+                launch_axpby(N4, dt2 / 3.0, Wb, 0.0, bdLt, h->stream);
+                r = adjoint_stage(h, Wst, An, dt, flux, nullptr, nullptr, bdLt, Wsb, a.recs ? rec + 2 : nullptr);
+                if (r) break;
+                launch_axpby(N4, dt, Wb, 0.0, bL, h->stream);
+                launch_axpby(N4, 0.5 * dt, Wsb, 1.0, bL, h->stream);
+                launch_axpby(N4, 0.5 * dt2, Wb, 0.0, bdL, h->stream);
+                launch_axpby(N4, 0.125 * dt2, Wsb, 1.0, bdL, h->stream);
+                launch_axpby(N4, -dt2 / 3.0, Wb, 0.0, bdLt, h->stream);
+                launch_axpby(N4, 1.0, Wsb, 1.0, Wb, h->stream);
+                r = adjoint_stage(h, Wn, An, dt, flux, bL, bdL, bdLt, Wb, a.recs ? rec : nullptr);
             }
         }
-        // reverse through the segment: Eq. 24 with the time limiter,
-        //   W* = W + dt/2 L + dt^2/8 dL,  W' = W + dt L + dt^2/2 dL - dt^2/3 dLt + dt^2/3 dLt(W*)
-        for (int s = s1 - 1; s >= s0 && r == DFGKS_OK; --s) {
-            const double dt = dts[s], dt2 = dt * dt;
-            const double* Wn = a.W + (s - s0) * N4;
-            const double* An = a.A + (s - s0) * N;
-            const double* Wst = a.Ws + (s - s0) * N4;
-            SweepBuffers rec[4];
-            if (a.recs) record_sets(h, a.recs + (long long)(s - s0) * a.rec_step, a.tape, a.gks, rec);
-            CK(cudaMemsetAsync(Wsb, 0, (size_t)N4 * sizeof(double), h->stream));
-            launch_axpby(N4, dt2 / 3.0, Wb, 0.0, bdLt, h->stream);
-            r = adjoint_stage(h, Wst, An, dt, flux, nullptr, nullptr, bdLt, Wsb, a.recs ? rec + 2 : nullptr);
-            if (r) break;
-            launch_axpby(N4, dt, Wb, 0.0, bL, h->stream);
-            launch_axpby(N4, 0.5 * dt, Wsb, 1.0, bL, h->stream);
-            launch_axpby(N4, 0.5 * dt2, Wb, 0.0, bdL, h->stream);
-            launch_axpby(N4, 0.125 * dt2, Wsb, 1.0, bdL, h->stream);
-            launch_axpby(N4, -dt2 / 3.0, Wb, 0.0, bdLt, h->stream);
-            launch_axpby(N4, 1.0, Wsb, 1.0, Wb, h->stream);
-            r = adjoint_stage(h, Wn, An, dt, flux, bL, bdL, bdLt, Wb, a.recs ? rec : nullptr);
-        }
-    }
-    if (r == DFGKS_OK) CK(cudaMemcpyAsync(W0_bar, Wb, (size_t)N4 * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
-    // leave the handle at the forward solution W^n (state, alpha, time and step count)
-    launch_dense_to_ghosted(m, WTs, 4, h->W[h->cur], h->stream);
-    launch_dense_to_ghosted(m, ATs, 1, h->A[h->cur], h->stream);
-    *h->st_host = stT;
-    CK(cudaMemcpyAsync(h->st, h->st_host, sizeof(DevState), cudaMemcpyHostToDevice, h->stream));
+        if (r == DFGKS_OK) CK(cudaMemcpyAsync(W0_bar, Wb, (size_t)N4 * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+        // leave the handle at the forward solution W^n (state, alpha, time and step count)
+        launch_dense_to_ghosted(m, WTs, 4, h->W[h->cur], h->stream);
+        launch_dense_to_ghosted(m, ATs, 1, h->A[h->cur], h->stream);
+        *h->st_host = stT;
+        CK(cudaMemcpyAsync(h->st, h->st_host, sizeof(DevState), cudaMemcpyHostToDevice, h->stream));
+        CK_LAUNCH();
+        return r;
+    };
+    r = passes();
     cleanup();
     h->timer->harvest();
-    CK_LAUNCH();
     return r;
 }
 
