@@ -160,8 +160,10 @@ DFK_HD int lines_body(const Mesh& m, const SchemeConsts& S, const double* __rest
         const double idn = 1.0 / g.dn;
         const long long li = g.line(f, t);
         double qL[4], qLn[4], qR[4], qRn[4];
-        double tl = 1.0;
-        int tlk = -1;                                     // the reconstruction that set tl
+        // the limiter weight so far as tn / td (1 until a reconstruction gives less); fractions are
+        // compared by cross-multiplication (denominators >= 2), one division at the end
+        double tn = 1.0, td = 1.0;
+        int tlk = -1;                                     // the reconstruction that set it
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             double sL[5] = {Q[0][k], Q[1][k], Q[2][k], Q[3][k], Q[4][k]};
@@ -169,14 +171,22 @@ DFK_HD int lines_body(const Mesh& m, const SchemeConsts& S, const double* __rest
             double v, sl;
             if (!dfL || S.time_limiter) {
                 AO o = TAPE ? weno_ao_t(sL, S, PlaneTape{ltape + li, ls}, 2 * k * AT_COUNT) : weno_ao(sL, S);
-                if (S.time_limiter) { double la = limiter_alpha(o); if (la < tl) { tl = la; tlk = 2 * k; } }
+                if (S.time_limiter) {
+                    double n, d;
+                    limiter_fraction(o, n, d);
+                    if (n * td < tn * d) { tn = n; td = d; tlk = 2 * k; }
+                }
                 if (!dfL) ao_at_right_edge(o, sL[2], v, sl);
             }
             if (dfL) df_at_right_edge(sL, al[2], v, sl);
             qL[k] = v; qLn[k] = sl * idn;
             if (!dfR || S.time_limiter) {
                 AO o = TAPE ? weno_ao_t(sR, S, PlaneTape{ltape + li, ls}, (2 * k + 1) * AT_COUNT) : weno_ao(sR, S);
-                if (S.time_limiter) { double la = limiter_alpha(o); if (la < tl) { tl = la; tlk = 2 * k + 1; } }
+                if (S.time_limiter) {
+                    double n, d;
+                    limiter_fraction(o, n, d);
+                    if (n * td < tn * d) { tn = n; td = d; tlk = 2 * k + 1; }
+                }
                 if (!dfR) ao_at_right_edge(o, sR[2], v, sl);
             }
             if (dfR) df_at_right_edge(sR, al[3], v, sl);
@@ -189,7 +199,7 @@ DFK_HD int lines_body(const Mesh& m, const SchemeConsts& S, const double* __rest
         back_project(B, qRn, out + LR_WRN);
 #pragma unroll
         for (int q = 0; q < 16; ++q) lines[q * ls + li] = out[q];
-        lines[LR_TL * ls + li] = tl;
+        lines[LR_TL * ls + li] = tn / td;
         lines[LR_TLK * ls + li] = (double)tlk;
         lines[LR_U * ls + li] = B.u;
         lines[LR_V * ls + li] = B.v;

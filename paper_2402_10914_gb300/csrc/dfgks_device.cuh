@@ -197,10 +197,18 @@ DFK_HD AO weno_ao_t(const double q[5], const SchemeConsts& S, const Tape& tp, in
 
 DFK_HD AO weno_ao(const double q[5], const SchemeConsts& S) { return weno_ao_t(q, S, NoTape{}, 0); }
 
-// time-limiter ingredient 2 at2 / (at1 + at2) of one reconstruction (Sect. 2.2)
-DFK_HD double limiter_alpha(const AO& o) {
+// time-limiter ingredient 2 at2 / (at1 + at2) of one reconstruction (Sect. 2.2), as numerator and
+// (positive) denominator, so that a minimum over several needs one division at the end
+DFK_HD void limiter_fraction(const AO& o, double& num, double& den) {
     double a1 = 1.0 + o.rmax * o.rmax, a2 = 1.0 + o.rmin * o.rmin;
-    return 2.0 * a2 / (a1 + a2);
+    num = 2.0 * a2;
+    den = a1 + a2;
+}
+
+DFK_HD double limiter_alpha(const AO& o) {
+    double n, d;
+    limiter_fraction(o, n, d);
+    return n / d;
 }
 
 // value and d/dxi of the AO polynomial at the right cell edge xi = +1/2
