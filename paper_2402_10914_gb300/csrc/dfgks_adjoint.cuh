@@ -138,6 +138,7 @@ DFK_HD AO ao_from_tape(const Tape& tp, int base, const SchemeConsts& S) {
     o.c3a4 = c3 * tp.get(base + AT_A4);
     o.rmax = tp.get(base + AT_R + (int)tp.get(base + AT_KMAX));
     o.rmin = tp.get(base + AT_R + (int)tp.get(base + AT_KMIN));
+    o.rs = 1.0;
     return o;
 }
 
@@ -185,6 +186,7 @@ DFK_HD void weno_ao_rev(const Tape& tp, int base, const SchemeConsts& S, const A
     qb[4] += -0.5 * a1b[2] + 0.5 * a2b[2] - (5.0 / 48.0) * a1b[3] - (1.0 / 16.0) * a2b[3] + (1.0 / 12.0) * a3b + (1.0 / 24.0) * a4b;
 }
 
+// o from a taped reconstruction (ratios unscaled, o.rs = 1)
 DFK_HD void limiter_alpha_vjp(const AO& o, double outb, AOBar& ob) {
     double a1 = 1.0 + o.rmax * o.rmax, a2 = 1.0 + o.rmin * o.rmin, D = a1 + a2;
     ob.rmax += outb * (-2.0 * a2 / (D * D)) * 2.0 * o.rmax;

@@ -100,19 +100,26 @@ DFK_HD void back_project(const CharBasis& B, const double Q[4], double W[4]) {
 struct AO {
     double A1, A2;          // sum_k c_k a1_k, sum_k c_k a2_k
     double c3a3, c3a4;      // c3 * a3, c3 * a4 of the quartic
-    double rmax, rmin;      // tau_Z/(beta_min+eps), tau_Z/(beta_max+eps): the time limiter's ratios
+    // the time limiter's ratios tau_Z/(beta_min+eps), tau_Z/(beta_max+eps), both multiplied by rs
+    // (1 whenever the reconstruction was taped; the product of the four beta_k+eps otherwise)
+    double rmax, rmin, rs;
 };
 
 // Optional record of a reconstruction's intermediates for its reverse (a "tape"): a sink with
 // put(index, value).  NoTape discards everything, so the plain forward compiles to the arithmetic
 // alone; ArrayTape writes a local array, PlaneTape one element of SoA planes in global memory.
-struct NoTape { DFK_HD void put(int, double) const {} };
+struct NoTape {
+    static constexpr bool active = false;
+    DFK_HD void put(int, double) const {}
+};
 struct ArrayTape {
+    static constexpr bool active = true;
     double* t;
     DFK_HD void put(int i, double v) const { t[i] = v; }
     DFK_HD double get(int i) const { return t[i]; }
 };
 struct PlaneTape {
+    static constexpr bool active = true;
     double* p;
     long long s;
     DFK_HD void put(int i, double v) const { p[(long long)i * s] = v; }
@@ -147,51 +154,72 @@ DFK_HD AO weno_ao_t(const double q[5], const SchemeConsts& S, const Tape& tp, in
     double b2 = a1_2 * a1_2 + c13_3 * a2_2 * a2_2;
     double b3 = a1_3 * (a1_3 + 0.5 * a3_3) + c13_3 * a2_3 * a2_3 + (21.0 / 5.0) * a2_3 * a4_3
               + (3129.0 / 80.0) * a3_3 * a3_3 + (87617.0 / 140.0) * a4_3 * a4_3;
-    // Eq. 37 and the WENO-Z weights.  The four ratios tau/(beta_k+eps) share one reciprocal of
-    // the product of their denominators (2 divisions per reconstruction instead of 5).
+    // Eq. 37 and the WENO-Z weights.  With P_k = prod_j (beta_j+eps) / (beta_k+eps) the ratios are
+    // r_k = tau P_k / prod; scaled by prod^2 the weights d_k (prod^2 + (tau P_k)^2) need one division
+    // (their normalisation) instead of two, and the limiter's ratios none (carried scaled by prod).
     double tau = (fabs(b3 - b0) + fabs(b3 - b1) + fabs(b3 - b2)) * (1.0 / 3.0);
     double e0 = b0 + S.eps, e1 = b1 + S.eps, e2 = b2 + S.eps, e3 = b3 + S.eps;
     double p01 = e0 * e1, p23 = e2 * e3, prod = p01 * p23;
-    double r0, r1, r2, r3;
-    if (prod < 1e300) {                              // beta+eps >= eps, so prod >= eps^4 > 0
-        double ti = tau / prod;
-        r0 = ti * (e1 * p23); r1 = ti * (e0 * p23); r2 = ti * (p01 * e3); r3 = ti * (p01 * e2);
-        const double ip = 1.0 / prod;                // the reciprocals, for the tape only
-        tp.put(base + AT_IE, (e1 * p23) * ip); tp.put(base + AT_IE + 1, (e0 * p23) * ip);
-        tp.put(base + AT_IE + 2, (p01 * e3) * ip); tp.put(base + AT_IE + 3, (p01 * e2) * ip);
+    const double P0 = e1 * p23, P1 = e0 * p23, P2 = p01 * e3, P3 = p01 * e2;
+    const double t0 = tau * P0, t1 = tau * P1, t2 = tau * P2, t3 = tau * P3;     // prod * r_k
+    const double tmax = fmax(fmax(t0, t1), fmax(t2, t3)), tmin = fmin(fmin(t0, t1), fmin(t2, t3));
+    AO o;
+    double c0, c1, c2, c3;
+    double r0, r1, r2, r3;                           // the ratios themselves: tape and fallback only
+    if (prod < 1e150 && tmax < 1e150) {              // beta+eps >= eps, so prod >= eps^4 > 0
+        const double p2 = prod * prod;
+        const double v0 = S.d[0] * (p2 + t0 * t0), v1 = S.d[1] * (p2 + t1 * t1);
+        const double v2 = S.d[2] * (p2 + t2 * t2), v3 = S.d[3] * (p2 + t3 * t3);
+        const double iv = 1.0 / (v0 + v1 + v2 + v3);
+        c3 = v3 * iv * S.inv_d3;
+        c0 = v0 * iv - c3 * S.d[0]; c1 = v1 * iv - c3 * S.d[1]; c2 = v2 * iv - c3 * S.d[2];
+        o.rmax = tmax; o.rmin = tmin; o.rs = prod;
+        if constexpr (Tape::active) {                // unscaled quantities for the reverse
+            const double ip = 1.0 / prod;
+            r0 = t0 * ip; r1 = t1 * ip; r2 = t2 * ip; r3 = t3 * ip;
+            tp.put(base + AT_IE, P0 * ip); tp.put(base + AT_IE + 1, P1 * ip);
+            tp.put(base + AT_IE + 2, P2 * ip); tp.put(base + AT_IE + 3, P3 * ip);
+            o.rmax = tmax * ip; o.rmin = tmin * ip; o.rs = 1.0;
+        }
     } else {
         r0 = tau / e0; r1 = tau / e1; r2 = tau / e2; r3 = tau / e3;
         tp.put(base + AT_IE, 1.0 / e0); tp.put(base + AT_IE + 1, 1.0 / e1);
         tp.put(base + AT_IE + 2, 1.0 / e2); tp.put(base + AT_IE + 3, 1.0 / e3);
+        const double w0 = S.d[0] * (1.0 + r0 * r0), w1 = S.d[1] * (1.0 + r1 * r1);
+        const double w2 = S.d[2] * (1.0 + r2 * r2), w3 = S.d[3] * (1.0 + r3 * r3);
+        const double iw = 1.0 / (w0 + w1 + w2 + w3);
+        c3 = w3 * iw * S.inv_d3;
+        c0 = w0 * iw - c3 * S.d[0]; c1 = w1 * iw - c3 * S.d[1]; c2 = w2 * iw - c3 * S.d[2];
+        // tau >= 0, so the ratio is largest at beta_min and smallest at beta_max
+        o.rmax = fmax(fmax(r0, r1), fmax(r2, r3)); o.rmin = fmin(fmin(r0, r1), fmin(r2, r3)); o.rs = 1.0;
     }
-    double w0 = S.d[0] * (1.0 + r0 * r0), w1 = S.d[1] * (1.0 + r1 * r1);
-    double w2 = S.d[2] * (1.0 + r2 * r2), w3 = S.d[3] * (1.0 + r3 * r3);
-    double iw = 1.0 / (w0 + w1 + w2 + w3);
-    double c3 = w3 * iw * S.inv_d3;
-    double c0 = w0 * iw - c3 * S.d[0], c1 = w1 * iw - c3 * S.d[1], c2 = w2 * iw - c3 * S.d[2];
-    AO o;
+    if constexpr (Tape::active) {
+        // the reverse differentiates w_k = d_k (1 + r_k^2) and c_k = w_k / sum w - c_3 d_k
+        const double w0 = S.d[0] * (1.0 + r0 * r0), w1 = S.d[1] * (1.0 + r1 * r1);
+        const double w2 = S.d[2] * (1.0 + r2 * r2), w3 = S.d[3] * (1.0 + r3 * r3);
+        const double iw = 1.0 / (w0 + w1 + w2 + w3);
+        c3 = w3 * iw * S.inv_d3;
+        c0 = w0 * iw - c3 * S.d[0]; c1 = w1 * iw - c3 * S.d[1]; c2 = w2 * iw - c3 * S.d[2];
+        tp.put(base + AT_R, r0); tp.put(base + AT_R + 1, r1); tp.put(base + AT_R + 2, r2); tp.put(base + AT_R + 3, r3);
+        tp.put(base + AT_W, w0); tp.put(base + AT_W + 1, w1); tp.put(base + AT_W + 2, w2); tp.put(base + AT_W + 3, w3);
+        tp.put(base + AT_IW, iw); tp.put(base + AT_C3, c3);
+        int kmax = 0, kmin = 0;
+        const double rr[4] = {r0, r1, r2, r3};
+#pragma unroll
+        for (int k = 1; k < 4; ++k) { if (rr[k] > rr[kmax]) kmax = k; if (rr[k] < rr[kmin]) kmin = k; }
+        tp.put(base + AT_KMAX, (double)kmax);
+        tp.put(base + AT_KMIN, (double)kmin);
+    }
     o.A1 = c0 * a1_0 + c1 * a1_1 + c2 * a1_2 + c3 * a1_3;
     o.A2 = c0 * a2_0 + c1 * a2_1 + c2 * a2_2 + c3 * a2_3;
     o.c3a3 = c3 * a3_3;
     o.c3a4 = c3 * a4_3;
-    // tau >= 0, so the ratio is largest at beta_min and smallest at beta_max
-    o.rmax = fmax(fmax(r0, r1), fmax(r2, r3));
-    o.rmin = fmin(fmin(r0, r1), fmin(r2, r3));
     tp.put(base + AT_A1, a1_0); tp.put(base + AT_A1 + 1, a1_1); tp.put(base + AT_A1 + 2, a1_2); tp.put(base + AT_A1 + 3, a1_3);
     tp.put(base + AT_A2, a2_0); tp.put(base + AT_A2 + 1, a2_1); tp.put(base + AT_A2 + 2, a2_2); tp.put(base + AT_A2 + 3, a2_3);
     tp.put(base + AT_A3, a3_3); tp.put(base + AT_A4, a4_3);
-    tp.put(base + AT_R, r0); tp.put(base + AT_R + 1, r1); tp.put(base + AT_R + 2, r2); tp.put(base + AT_R + 3, r3);
-    tp.put(base + AT_W, w0); tp.put(base + AT_W + 1, w1); tp.put(base + AT_W + 2, w2); tp.put(base + AT_W + 3, w3);
-    tp.put(base + AT_IW, iw); tp.put(base + AT_C3, c3);
     tp.put(base + AT_SG, (b3 - b0) >= 0.0 ? 1.0 : -1.0);
     tp.put(base + AT_SG + 1, (b3 - b1) >= 0.0 ? 1.0 : -1.0);
     tp.put(base + AT_SG + 2, (b3 - b2) >= 0.0 ? 1.0 : -1.0);
-    int kmax = 0, kmin = 0;
-    const double rr[4] = {r0, r1, r2, r3};
-#pragma unroll
-    for (int k = 1; k < 4; ++k) { if (rr[k] > rr[kmax]) kmax = k; if (rr[k] < rr[kmin]) kmin = k; }
-    tp.put(base + AT_KMAX, (double)kmax);
-    tp.put(base + AT_KMIN, (double)kmin);
     return o;
 }
 
@@ -200,7 +228,9 @@ DFK_HD AO weno_ao(const double q[5], const SchemeConsts& S) { return weno_ao_t(q
 // time-limiter ingredient 2 at2 / (at1 + at2) of one reconstruction (Sect. 2.2), as numerator and
 // (positive) denominator, so that a minimum over several needs one division at the end
 DFK_HD void limiter_fraction(const AO& o, double& num, double& den) {
-    double a1 = 1.0 + o.rmax * o.rmax, a2 = 1.0 + o.rmin * o.rmin;
+    // 1 + r^2 scaled by rs^2, which cancels in the ratio
+    const double s2 = o.rs * o.rs;
+    double a1 = s2 + o.rmax * o.rmax, a2 = s2 + o.rmin * o.rmin;
     num = 2.0 * a2;
     den = a1 + a2;
 }
