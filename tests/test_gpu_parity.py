@@ -242,6 +242,28 @@ def test_full_size_quadrants_run_sampled_steps():
     assert W[0].min() > 0 and p.min() > 0
 
 
+@pytest.mark.parametrize("limiter", [0, 1])
+def test_full_run_parity_vortex_c4_forward(limiter):
+    # the adjoint workload's forward run at full size: isentropic vortex 256 x 256, 100 GKS steps,
+    # the DF branch never firing.  With the time limiter off the step map is well conditioned and
+    # the strict bar holds; with it on (the workload's setting) the limiter amplifies rounding over
+    # the 100 steps, so the bar is ten times the oracle's own spread under 1e-15 input noise
+    w = I.vortex(256, steps=100)
+    w.settings = w.settings.with_(time_limiter=limiter)
+    oracle.set_threads(oracle.max_threads())
+    (rc, Wo, ao, to, dts_o, st), (done, W, a, t, dts, cnt) = run_both(w, 100)
+    assert rc == 0 and done == 100
+    assert cnt["df_normal"] == st.df_normal == 0 and cnt["df_tangential"] == st.df_tangential == 0
+    err = l1_rel(W, Wo)
+    if limiter == 0:
+        assert err <= 1e-9 and comp_rel_err(W, Wo) <= 1e-9, (err, comp_rel_err(W, Wo))
+    else:
+        _, env_max, env_l1 = oracle_envelope(w.settings, w.W0, 100)
+        print("vortex 256^2 limiter on: rel L1 %.3e (oracle's own spread %.3e)" % (err, env_l1))
+        assert err <= max(1e-9, 10.0 * env_l1), (err, env_l1)
+    assert np.allclose(dts, dts_o, rtol=1e-9, atol=0)
+
+
 def test_full_run_parity_blast_steps():
     w = I.blast(96)
     (rc, Wo, ao, to, dts_o, st), (done, W, a, t, dts, cnt) = run_both(w, 30)
