@@ -361,6 +361,7 @@ DFK_HD void update_body(const Mesh& m, const SchemeConsts& S, const UpdateArgs& 
         return;
     }
     double L[4], dL[4], dLt[4];
+    const double idx = 1.0 / m.dx, idy = 1.0 / m.dy;     // two divisions per cell instead of twelve
     const double ow = frx[FR_OMEGA * fsx + fw], oe = frx[FR_OMEGA * fsx + fe];
     const double os = fry[FR_OMEGA * fsy + fsf], on = fry[FR_OMEGA * fsy + fn];
 #pragma unroll
@@ -373,9 +374,9 @@ DFK_HD void update_body(const Mesh& m, const SchemeConsts& S, const UpdateArgs& 
         double DE = 0.5 * frx[(FR_DF + k) * fsx + fe] + 0.5 * frx[(FR_DF + k) * fsx + nfx + fe];
         double DS = 0.5 * fry[(FR_DF + k) * fsy + fsf] + 0.5 * fry[(FR_DF + k) * fsy + nfy + fsf];
         double DN = 0.5 * fry[(FR_DF + k) * fsy + fn] + 0.5 * fry[(FR_DF + k) * fsy + nfy + fn];
-        L[k] = -(FE - FW) / m.dx - (FN - FS) / m.dy;
-        dL[k] = -(DE - DW) / m.dx - (DN - DS) / m.dy;
-        dLt[k] = -(oe * DE - ow * DW) / m.dx - (on * DN - os * DS) / m.dy;
+        L[k] = -(FE - FW) * idx - (FN - FS) * idy;
+        dL[k] = -(DE - DW) * idx - (DN - DS) * idy;
+        dLt[k] = -(oe * DE - ow * DW) * idx - (on * DN - os * DS) * idy;
     }
     if (MODE == UM_RESIDUAL) {
 #pragma unroll

@@ -261,7 +261,8 @@ def test_full_run_parity_vortex_c4_forward(limiter):
         _, env_max, env_l1 = oracle_envelope(w.settings, w.W0, 100)
         print("vortex 256^2 limiter on: rel L1 %.3e (oracle's own spread %.3e)" % (err, env_l1))
         assert err <= max(1e-9, 10.0 * env_l1), (err, env_l1)
-    assert np.allclose(dts, dts_o, rtol=1e-9, atol=0)
+    # the CFL step follows the state: to rounding without the limiter, to its spread with it
+    assert np.allclose(dts, dts_o, rtol=1e-9 if limiter == 0 else 1e-5, atol=0)
 
 
 def test_full_run_parity_blast_steps():
