@@ -385,6 +385,89 @@ DFK_HD void a_mom_vjp(const Mom& m, const double a[4], const double ob[4], MomBa
     ab[3] += 0.5 * hb;
 }
 
+// The reverse of several a_mom of one (m, a) at once (the factorised form of a_mom): the output
+// adjoints of each out<k, l> are accumulated into the adjoints of the shared P_k, Q_l, Qp_l terms
+// (out_vjp), whose own reverse runs once (finish).  Needs KLO <= k, k + 2 <= KHI, LLO <= l,
+// l + 2 <= LHI for every output.
+template <int KLO, int KHI, int LLO, int LHI>
+struct AMomRev {
+    double P[KHI - KLO + 1], Q[LHI - LLO + 1], Qp[LHI - LLO + 1], h, x1, x2;
+    double Pb[KHI - KLO + 1], Qb[LHI - LLO + 1], Qpb[LHI - LLO + 1], hb;
+    DFK_HD AMomRev(const Mom& m, const double a[4]) {
+        h = 0.5 * a[3];
+        x1 = m.mx[1];
+        x2 = m.mx[2];
+        const double hx1 = h * x1;
+        for (int j = KLO; j <= KHI; ++j) {
+            P[j - KLO] = a[0] * m.mu[j] + a[1] * m.mu[j + 1] + h * m.mu[j + 2];
+            Pb[j - KLO] = 0.0;
+        }
+        for (int j = LLO; j <= LHI; ++j) {
+            Q[j - LLO] = a[2] * m.mv[j + 1] + h * m.mv[j + 2];
+            Qp[j - LLO] = Q[j - LLO] + hx1 * m.mv[j];
+            Qb[j - LLO] = 0.0;
+            Qpb[j - LLO] = 0.0;
+        }
+        hb = 0.0;
+    }
+    template <int k, int l>
+    DFK_HD void out_vjp(const Mom& m, const double ob[4], MomBar& mb) {
+        const double* mu = m.mu;
+        const double* mv = m.mv;
+        const double g0 = ob[0], g1 = ob[1], g2 = ob[2], g3 = 0.5 * ob[3];
+        const int pk = k - KLO, ql = l - LLO;
+        // out0 = mv_l P_k + mu_k Qp_l, out1 = mv_l P_{k+1} + mu_{k+1} Qp_l, out2 = mv_{l+1} P_k + mu_k Qp_{l+1},
+        // out3 / 2 = G(k+2,l,0) + G(k,l+2,0) + G(k,l,1)
+        mb.mv[l] += g0 * P[pk] + g1 * P[pk + 1] + g3 * P[pk + 2];
+        mb.mu[k] += g0 * Qp[ql] + g2 * Qp[ql + 1] + g3 * Qp[ql + 2];
+        mb.mu[k + 1] += g1 * Qp[ql];
+        mb.mv[l + 1] += g2 * P[pk];
+        mb.mu[k + 2] += g3 * Qp[ql];
+        mb.mv[l + 2] += g3 * P[pk];
+        Pb[pk] += g0 * mv[l] + g2 * mv[l + 1] + g3 * mv[l + 2];
+        Pb[pk + 1] += g1 * mv[l];
+        Pb[pk + 2] += g3 * mv[l];
+        Qpb[ql] += g0 * mu[k] + g1 * mu[k + 1] + g3 * mu[k + 2];
+        Qpb[ql + 1] += g2 * mu[k];
+        Qpb[ql + 2] += g3 * mu[k];
+        // G(k,l,1) = x1 (mv_l P_k + mu_k Q_l) + h mu_k mv_l x2
+        const double gi = g3 * x1, t = g3 * h * x2;
+        mb.mx[1] += g3 * (mv[l] * P[pk] + mu[k] * Q[ql]);
+        mb.mv[l] += gi * P[pk] + t * mu[k];
+        mb.mu[k] += gi * Q[ql] + t * mv[l];
+        mb.mx[2] += g3 * h * mu[k] * mv[l];
+        Pb[pk] += gi * mv[l];
+        Qb[ql] += gi * mu[k];
+        hb += g3 * mu[k] * mv[l] * x2;
+    }
+    DFK_HD void finish(const Mom& m, const double a[4], MomBar& mb, double ab[4]) {
+        const double* mu = m.mu;
+        const double* mv = m.mv;
+        const double hx1 = h * x1;
+        for (int j = LLO; j <= LHI; ++j) {
+            const int q = j - LLO;
+            // Qp_j = Q_j + h x1 mv_j, Q_j = a2 mv_{j+1} + h mv_{j+2}
+            const double qb = Qb[q] + Qpb[q];
+            hb += Qpb[q] * x1 * mv[j] + qb * mv[j + 2];
+            mb.mx[1] += Qpb[q] * h * mv[j];
+            mb.mv[j] += Qpb[q] * hx1;
+            ab[2] += qb * mv[j + 1];
+            mb.mv[j + 1] += qb * a[2];
+            mb.mv[j + 2] += qb * h;
+        }
+        for (int j = KLO; j <= KHI; ++j) {
+            const double pb = Pb[j - KLO];
+            ab[0] += pb * mu[j];
+            ab[1] += pb * mu[j + 1];
+            hb += pb * mu[j + 2];
+            mb.mu[j] += pb * a[0];
+            mb.mu[j + 1] += pb * a[1];
+            mb.mu[j + 2] += pb * h;
+        }
+        ab[3] += 0.5 * hb;
+    }
+};
+
 // adjoint of slope_solve: bb += S^T ab, state adjoints accumulated
 DFK_HD void slope_solve_vjp(const Maxw& s, const double b[4], const double abin[4], double bb[4], MaxwBar& sb) {
     double R2 = b[1] - s.U * b[0], R3 = b[2] - s.V * b[0], R4 = 2.0 * b[3] - s.qK * b[0];
@@ -588,24 +671,26 @@ DFK_HD void gks_flux_reverse(const Tape& tp, const GPState& L, const GPState& R,
         fill_moments_vjp<0>(sl, K, mlF, mlFb, slb);
         fill_moments_vjp<0>(sr, K, mrF, mrFb, srb);
     }
-    // flux moments
+    // flux moments and the compatibility condition of A^c: the equilibrium's moment sums of a_x
+    // and of a_y are reversed together (their outputs share P, Q terms)
     psi_mom_vjp<1, 0, 0>(mc, Mc0b, mcb);
-    a_mom_vjp<2, 0>(mc, acx, Mc1b, mcb, acxb);
-    a_mom_vjp<1, 1>(mc, acy, Mc1b, mcb, acyb);
     a_mom_vjp<1, 0>(mc, Ac, Mc2b, mcb, Acb);
     psi_mom_vjp<1, 0, 0>(ml, Ml0b, mlb);
     psi_mom_vjp<1, 0, 0>(mr, Mr0b, mrb);
-    a_mom_vjp<2, 0>(ml, alx, Ml1b, mlb, alxb);
-    a_mom_vjp<1, 1>(ml, aly, Ml1b, mlb, alyb);
-    a_mom_vjp<2, 0>(mr, arx, Mr1b, mrb, arxb);
-    a_mom_vjp<1, 1>(mr, ary, Mr1b, mrb, aryb);
-    // A^c from the compatibility condition
     double bctb[4] = {0, 0, 0, 0};
     slope_solve_vjp(sc, bct, Acb, bctb, scb);
-    double nb[4];
-    for (int i = 0; i < 4; ++i) nb[i] = -bctb[i];
-    a_mom_vjp<1, 0>(mc, acx, nb, mcb, acxb);
-    a_mom_vjp<0, 1>(mc, acy, nb, mcb, acyb);
+    {
+        double nb[4];
+        for (int i = 0; i < 4; ++i) nb[i] = -bctb[i];
+        AMomRev<1, 4, 0, 2> Cx(mc, acx);
+        AMomRev<0, 3, 0, 3> Cy(mc, acy);
+        Cx.out_vjp<2, 0>(mc, Mc1b, mcb);
+        Cx.out_vjp<1, 0>(mc, nb, mcb);
+        Cx.finish(mc, acx, mcb, acxb);
+        Cy.out_vjp<1, 1>(mc, Mc1b, mcb);
+        Cy.out_vjp<0, 1>(mc, nb, mcb);
+        Cy.finish(mc, acy, mcb, acyb);
+    }
     // equilibrium slopes
     double bcxb[4] = {0, 0, 0, 0}, bcyb[4] = {0, 0, 0, 0};
     slope_solve_vjp(sc, bcx, acxb, bcxb, scb);
@@ -628,15 +713,36 @@ DFK_HD void gks_flux_reverse(const Tape& tp, const GPState& L, const GPState& R,
     }
     psi_mom_vjp<0, 0, 0>(ml, plb, mlb);
     psi_mom_vjp<0, 0, 0>(mr, prb, mrb);
+    // each side's moment sums of a_x (kinetic weighting, flux moment) and of a_y, reversed together
     double tb[4];
-    for (int i = 0; i < 4; ++i) tb[i] = Wcxb[i] * sl.rho;
-    a_mom_vjp<0, 0>(ml, alx, tb, mlb, alxb);
-    for (int i = 0; i < 4; ++i) tb[i] = Wcxb[i] * sr.rho;
-    a_mom_vjp<0, 0>(mr, arx, tb, mrb, arxb);
-    for (int i = 0; i < 4; ++i) tb[i] = Wcyb[i] * sl.rho;
-    a_mom_vjp<0, 0>(ml, aly, tb, mlb, alyb);
-    for (int i = 0; i < 4; ++i) tb[i] = Wcyb[i] * sr.rho;
-    a_mom_vjp<0, 0>(mr, ary, tb, mrb, aryb);
+    {
+        AMomRev<0, 4, 0, 2> X(ml, alx);
+        for (int i = 0; i < 4; ++i) tb[i] = Wcxb[i] * sl.rho;
+        X.out_vjp<0, 0>(ml, tb, mlb);
+        X.out_vjp<2, 0>(ml, Ml1b, mlb);
+        X.finish(ml, alx, mlb, alxb);
+    }
+    {
+        AMomRev<0, 4, 0, 2> X(mr, arx);
+        for (int i = 0; i < 4; ++i) tb[i] = Wcxb[i] * sr.rho;
+        X.out_vjp<0, 0>(mr, tb, mrb);
+        X.out_vjp<2, 0>(mr, Mr1b, mrb);
+        X.finish(mr, arx, mrb, arxb);
+    }
+    {
+        AMomRev<0, 3, 0, 3> Y(ml, aly);
+        for (int i = 0; i < 4; ++i) tb[i] = Wcyb[i] * sl.rho;
+        Y.out_vjp<0, 0>(ml, tb, mlb);
+        Y.out_vjp<1, 1>(ml, Ml1b, mlb);
+        Y.finish(ml, aly, mlb, alyb);
+    }
+    {
+        AMomRev<0, 3, 0, 3> Y(mr, ary);
+        for (int i = 0; i < 4; ++i) tb[i] = Wcyb[i] * sr.rho;
+        Y.out_vjp<0, 0>(mr, tb, mrb);
+        Y.out_vjp<1, 1>(mr, Mr1b, mrb);
+        Y.finish(mr, ary, mrb, aryb);
+    }
     // side slope coefficients
     double bb[4];
     for (int i = 0; i < 4; ++i) bb[i] = 0.0;
