@@ -40,7 +40,7 @@ typedef enum {
     DFGKS_ENONPHYS = 4,    /* initial/state data with rho <= 0, p <= 0 or a non-finite value */
     DFGKS_ENONPOS = 5,     /* positivity (rho > 0, p > 0, finite) lost during a step */
     DFGKS_ENAN = 6,        /* reserved: non-finite value outside the positivity check */
-    DFGKS_ETIMEOUT = 7,    /* a bounded device-side wait expired (batched persistent launch) */
+    DFGKS_ETIMEOUT = 7,    /* reserved: a bounded device-side wait expired (no kernel here waits) */
     DFGKS_ENOTSUP = 8      /* the requested combination is not implemented */
 } dfgks_status;
 
