@@ -57,10 +57,11 @@ def parse():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--n", type=int, default=400, help="mesh side of the four-quadrant workload")
-    p.add_argument("--workload", default="quadrants", choices=["quadrants", "batch", "adjoint", "blast"],
+    p.add_argument("--workload", default="quadrants", choices=["quadrants", "batch", "adjoint", "blast", "robustness"],
                    help="quadrants: the 400x400 GKS step (default); batch: the 64-problem uneven batch; "
                         "adjoint: gradient / forward time on the 256x256 vortex, 100 steps; "
-                        "blast: the 1e6 pressure-ratio blast run to its end time")
+                        "blast: the 1e6 pressure-ratio blast run to its end time; "
+                        "robustness: maximum Mach numbers of the 123 problem and the hurricane-like flow")
     p.add_argument("--blast-n", type=int, default=2048, help="mesh side of the blast workload")
     p.add_argument("--blast-t", type=float, default=0.01, help="end time of the blast workload")
     p.add_argument("--no-adjoint", action="store_true", help="leave the adjoint summary out of the default line")
@@ -353,6 +354,61 @@ def bench_blast(args):
     print(json.dumps(line))
 
 
+def bench_robustness(args):
+    """Sect. 4.3 robustness measure: the largest Mach number at which a run keeps positivity, for
+    the hybrid (DF + WENO-AO) and the plain WENO-AO reconstruction (alpha_thres = 0: the DF branch
+    never fires), GKS (S2O4) and L-F (SSP-RK3), with and without the Gauss-point fallback.  Found by
+    bisection in log Mach between 1 and 256 (12 halvings)."""
+    import torch
+    from paper_2402_10914_gb300 import _lib, inputs as I
+    from paper_2402_10914_gb300.solver import Solver
+
+    def survives(make, ma, flux, thres, fb):
+        w = make(ma, flux=flux)
+        s = w.settings.with_(alpha_thres=thres, gp_fallback=fb)
+        with Solver(s) as sol:
+            try:
+                sol.set_ic(w.W0)
+                if w.t_end:
+                    sol.run(t_end=w.t_end, chunk=512)
+                else:
+                    sol.step(w.steps)
+            except _lib.DfgksError:
+                return False
+            W = sol.get_state()[0]
+        return bool(np.isfinite(W).all())
+
+    t0 = time.perf_counter()
+    rows = []
+    for name, make in (("123 problem (100 cells, t = 0.14)", I.problem_123),
+                       ("hurricane-like (400 x 400, 50 steps)", I.hurricane)):
+        for flux, fname in ((I.GKS, "GKS S2O4"), (I.LF, "L-F SSP-RK3")):
+            for thres, rname in ((0.5, "hybrid"), (0.0, "WENO-AO")):
+                for fb in (0, 1):
+                    lo, hi = 1.0, 256.0
+                    if not survives(make, lo, flux, thres, fb):
+                        res = "< 1"
+                    elif survives(make, hi, flux, thres, fb):
+                        res = ">= 256"
+                    else:
+                        for _ in range(12):
+                            mid = math.sqrt(lo * hi)
+                            if survives(make, mid, flux, thres, fb):
+                                lo = mid
+                            else:
+                                hi = mid
+                        res = round(lo, 2)
+                    rows.append({"problem": name, "solver": fname, "reconstruction": rname,
+                                 "gauss_point_fallback": fb, "max_mach": res})
+                    print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+    torch.cuda.synchronize()
+    line = {"metric": "maximum Mach number keeping positivity (Sect. 4.3 robustness measure)", "value": None,
+            "unit": "Mach", "n_gpus": 1, "steps": None, "warmup": 0, "higher_is_better": True,
+            "dtype": "f64", "data": "synthetic", "config": {"workload": "robustness_123_hurricane"},
+            "robustness": rows, "wall_s": time.perf_counter() - t0}
+    print(json.dumps(line))
+
+
 def adj_workload(n: int, nsteps: int, ckpt: int = 10) -> str:
     return "vortex_%dx%d_gks_%dsteps_ckpt%d" % (n, n, nsteps, ckpt)
 
@@ -467,6 +523,10 @@ def main():
     if args.workload == "blast":
         if rank == 0:
             bench_blast(args)
+        return
+    if args.workload == "robustness":
+        if rank == 0:
+            bench_robustness(args)
         return
     if args.workload == "adjoint":
         if rank == 0:

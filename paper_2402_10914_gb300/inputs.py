@@ -20,6 +20,10 @@ Workloads (all FP64, gamma = 1.4):
   blast          pressure ratio 1e6 blast (p = 1e4 inside r < 0.1 of (0.5,0.5), 0.01 outside)
                  on [0,1]^2 with reflecting walls, GKS, CFL 0.4, t = 0.01.
   riemann_cfg3   Sect. 4.2 planar-shock interaction (four constant states split at (0.7,0.7)).
+  problem_123    Sect. 4.3 "123 problem": two receding rarefactions on [0,1] (a y-uniform strip),
+                 rho = 1, u = -2 / +2, p0 set by the Mach number u / c, free boundaries, t = 0.14.
+  hurricane      Sect. 4.3 hurricane-like flow: rho = 1, p = 25 (entropy A = 25), rotation speed v0
+                 set by the Mach number v0 / c0, [-2,2]^2 at dx = 1/100, 50 steps.
 """
 from __future__ import annotations
 
@@ -218,6 +222,37 @@ def riemann_cfg3(n: int = 500, t_end: float = 0.6, flux: int = GKS) -> Workload:
     s = Settings(nx=n, ny=n, cfl=0.5, bc=(OUTFLOW,) * 4, flux=flux, time_limiter=1 if flux == GKS else 0)
     states = [(0.138, 1.206, 1.206, 0.129), (0.5323, 0.0, 1.206, 0.3), (1.5, 0.0, 0.0, 1.5), (0.5323, 1.206, 0.0, 0.3)]
     return Workload("riemann3_%dx%d" % (n, n), s, _four_states(s, states, 0.7, 0.7), t_end=t_end)
+
+
+def problem_123(ma: float, n: int = 100, flux: int = GKS, ny: int = 4) -> Workload:
+    """Sect. 4.3, 123 problem: (rho, u, p) = (1, -2, p0) for x < 0.5 and (1, 2, p0) beyond, with p0
+    from Ma = |u| / sqrt(gamma p0 / rho); free (outflow) boundaries in x, periodic in y; GKS with
+    S2O4 or L-F with SSP-RK3, as the paper pairs them; t = 0.14."""
+    dx = 1.0 / n
+    s = Settings(nx=n, ny=ny, x0=0.0, x1=1.0, y0=0.0, y1=ny * dx, cfl=0.5,
+                 bc=(OUTFLOW, OUTFLOW, PERIODIC, PERIODIC), flux=flux, time_scheme=S2O4 if flux == GKS else SSPRK3)
+    xc, yc, _, _ = cell_centres(s)
+    X, _ = np.meshgrid(xc, yc)
+    p0 = 2.0 ** 2 / (s.gamma * ma * ma)
+    u = np.where(X < 0.5, -2.0, 2.0)
+    W = conserved(np.ones_like(X), u, np.zeros_like(X), np.full_like(X, p0), s.gamma)
+    return Workload("p123_ma%g_%d" % (ma, n), s, W, t_end=0.14, meta={"mach": ma, "p0": p0})
+
+
+def hurricane(ma: float, n: int = 400, flux: int = GKS, steps: int = 50) -> Workload:
+    """Sect. 4.3, hurricane-like flow: (rho, u, v, p) = (1, v0 sin(theta), -v0 cos(theta), A rho^gamma)
+    with theta the polar angle, A = 25 and v0 from Ma = v0 / c0, c0 = sqrt(gamma A); [-2,2]^2 with
+    dx = 1/100 (n = 400) and non-reflecting (outflow) boundaries; 50 steps."""
+    s = Settings(nx=n, ny=n, x0=-2.0, x1=2.0, y0=-2.0, y1=2.0, cfl=0.5, bc=(OUTFLOW,) * 4, flux=flux,
+                 time_scheme=S2O4 if flux == GKS else SSPRK3)
+    xc, yc, _, _ = cell_centres(s)
+    X, Y = np.meshgrid(xc, yc)
+    A, rho0 = 25.0, 1.0
+    p0 = A * rho0 ** s.gamma
+    v0 = ma * math.sqrt(s.gamma * p0 / rho0)
+    th = np.arctan2(Y, X)
+    W = conserved(np.full_like(X, rho0), v0 * np.sin(th), -v0 * np.cos(th), np.full_like(X, p0), s.gamma)
+    return Workload("hurricane_ma%g_%d" % (ma, n), s, W, steps=steps, meta={"mach": ma, "v0": v0})
 
 
 def random_smooth(nx: int, ny: int, seed: int, amp: float = 0.1, bc=(PERIODIC,) * 4, **kw) -> Workload:

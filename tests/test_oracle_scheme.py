@@ -269,3 +269,22 @@ def test_cfl_step_closed_forms(rule):
     dx, dy = 2.0 / 12, 0.5 / 7
     want = min(dx / (abs(u) + c), dy / (abs(v) + c)) if rule == 0 else 1.0 / ((abs(u) + c) / dx + (abs(v) + c) / dy)
     assert oracle.cfl_dt(s, W) == pytest.approx(s.cfl * want, rel=1e-14)
+
+
+def test_robustness_inputs_have_their_mach_numbers():
+    # the 123 problem and the hurricane-like flow are parametrised by a Mach number (Sect. 4.3)
+    g = 1.4
+    for ma in (2.0, 31.5):
+        w = I.problem_123(ma)
+        rho, u = w.W0[0], w.W0[1] / w.W0[0]
+        p = (g - 1) * (w.W0[3] - 0.5 * rho * u * u)
+        assert np.allclose(np.abs(u) / np.sqrt(g * p / rho), ma, rtol=1e-12)
+        assert np.all(u[:, : w.settings.nx // 2] == -2.0) and np.all(u[:, w.settings.nx // 2:] == 2.0)
+        h = I.hurricane(ma, n=40)
+        rho, u, v = h.W0[0], h.W0[1] / h.W0[0], h.W0[2] / h.W0[0]
+        p = (g - 1) * (h.W0[3] - 0.5 * rho * (u * u + v * v))
+        assert np.allclose(np.hypot(u, v) / np.sqrt(g * p / rho), ma, rtol=1e-12)
+        xc, yc, _, _ = I.cell_centres(h.settings)
+        X, Y = np.meshgrid(xc, yc)
+        assert np.allclose(u * X + v * Y, 0.0, atol=1e-9 * ma)        # purely azimuthal
+        assert np.all(u * Y - v * X > 0)                              # rotating clockwise: (u, v) = v0 (sin, -cos)
