@@ -57,11 +57,13 @@ def parse():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--n", type=int, default=400, help="mesh side of the four-quadrant workload")
-    p.add_argument("--workload", default="quadrants", choices=["quadrants", "batch", "adjoint", "blast", "robustness"],
+    p.add_argument("--workload", default="quadrants",
+                   choices=["quadrants", "batch", "adjoint", "blast", "robustness", "resolution"],
                    help="quadrants: the 400x400 GKS step (default); batch: the 64-problem uneven batch; "
                         "adjoint: gradient / forward time on the 256x256 vortex, 100 steps; "
                         "blast: the 1e6 pressure-ratio blast run to its end time; "
-                        "robustness: maximum Mach numbers of the 123 problem and the hurricane-like flow")
+                        "robustness: maximum Mach numbers of the 123 problem and the hurricane-like flow; "
+                        "resolution: the planar-shock (500^2) and planar-contact (800^2) Riemann problems")
     p.add_argument("--blast-n", type=int, default=2048, help="mesh side of the blast workload")
     p.add_argument("--blast-t", type=float, default=0.01, help="end time of the blast workload")
     p.add_argument("--no-adjoint", action="store_true", help="leave the adjoint summary out of the default line")
@@ -409,6 +411,51 @@ def bench_robustness(args):
     print(json.dumps(line))
 
 
+def bench_resolution(args):
+    """Sect. 4.2 resolution workloads run to their end times as throughput and regression runs: the
+    planar-shock interaction (500 x 500, t = 0.6) and the planar-contact interaction (800 x 800 on
+    [0,2]^2, t = 1.6), GKS/S2O4 and L-F/SSP-RK3, hybrid and plain WENO-AO (alpha_thres = 0).  Per run:
+    steps, throughput, density extrema, and the density along the horizontal mid line summarised by
+    its total variation (more resolved structure, more variation) and its L1 distance to the
+    hybrid run's cut."""
+    import torch
+    from paper_2402_10914_gb300 import inputs as I
+    from paper_2402_10914_gb300.solver import Solver
+    rows = []
+    for make, name in ((I.riemann_cfg3, "planar shocks 500x500 t=0.6"), (I.riemann_cfg6, "planar contacts 800x800 t=1.6")):
+        for flux, fname in ((I.GKS, "GKS S2O4"), (I.LF, "L-F SSP-RK3")):
+            cut_h = None
+            for thres, rname in ((0.5, "hybrid"), (0.0, "WENO-AO")):
+                w = make(flux=flux)
+                s = w.settings.with_(alpha_thres=thres)
+                with Solver(s) as sol:
+                    sol.set_ic(w.W0)
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    torch.cuda.synchronize()
+                    a.record(sol.stream)
+                    steps, _ = sol.run(t_end=w.t_end, chunk=512)
+                    b.record(sol.stream)
+                    torch.cuda.synchronize()
+                    ms = a.elapsed_time(b)
+                    W, alpha, t, _ = sol.get_state()
+                    cnt = sol.counters()
+                rho = W[0]
+                cut = rho[s.ny // 2]
+                if cut_h is None:
+                    cut_h = cut
+                rows.append({"problem": name, "solver": fname, "reconstruction": rname, "steps": int(steps),
+                             "t": t, "cell_stage_per_s": 2.0 * s.nx * s.ny * steps / (ms * 1e-3), "wall_s": ms * 1e-3,
+                             "rho_min": float(rho.min()), "rho_max": float(rho.max()),
+                             "midline_total_variation": float(np.abs(np.diff(cut)).sum()),
+                             "midline_l1_to_hybrid": float(np.abs(cut - cut_h).mean()),
+                             "df_cells_normal": cnt["df_normal"], "fallbacks": cnt["fallbacks"]})
+                print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+    line = {"metric": "Sect. 4.2 resolution runs (throughput and mid-line density statistics)", "value": None,
+            "unit": "cell-stage/s", "n_gpus": 1, "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "riemann_cfg3_500_cfg6_800"}, "resolution": rows}
+    print(json.dumps(line))
+
+
 def adj_workload(n: int, nsteps: int, ckpt: int = 10) -> str:
     return "vortex_%dx%d_gks_%dsteps_ckpt%d" % (n, n, nsteps, ckpt)
 
@@ -527,6 +574,10 @@ def main():
     if args.workload == "robustness":
         if rank == 0:
             bench_robustness(args)
+        return
+    if args.workload == "resolution":
+        if rank == 0:
+            bench_resolution(args)
         return
     if args.workload == "adjoint":
         if rank == 0:

@@ -20,6 +20,7 @@ Workloads (all FP64, gamma = 1.4):
   blast          pressure ratio 1e6 blast (p = 1e4 inside r < 0.1 of (0.5,0.5), 0.01 outside)
                  on [0,1]^2 with reflecting walls, GKS, CFL 0.4, t = 0.01.
   riemann_cfg3   Sect. 4.2 planar-shock interaction (four constant states split at (0.7,0.7)).
+  riemann_cfg6   Sect. 4.2 planar contact interaction on [0,2]^2 (four constant states split at (1,1)).
   problem_123    Sect. 4.3 "123 problem": two receding rarefactions on [0,1] (a y-uniform strip),
                  rho = 1, u = -2 / +2, p0 set by the Mach number u / c, free boundaries, t = 0.14.
   hurricane      Sect. 4.3 hurricane-like flow: rho = 1, p = 25 (entropy A = 25), rotation speed v0
@@ -219,9 +220,20 @@ def blast(n: int = 2048, t_end: float = 0.01) -> Workload:
 
 
 def riemann_cfg3(n: int = 500, t_end: float = 0.6, flux: int = GKS) -> Workload:
-    s = Settings(nx=n, ny=n, cfl=0.5, bc=(OUTFLOW,) * 4, flux=flux, time_limiter=1 if flux == GKS else 0)
+    """Sect. 4.2 interaction of planar shocks on [0,1]^2; GKS with S2O4 (time limiter on) or L-F
+    with SSP-RK3; outflow boundaries."""
+    s = Settings(nx=n, ny=n, cfl=0.5, bc=(OUTFLOW,) * 4, flux=flux, time_scheme=S2O4 if flux == GKS else SSPRK3)
     states = [(0.138, 1.206, 1.206, 0.129), (0.5323, 0.0, 1.206, 0.3), (1.5, 0.0, 0.0, 1.5), (0.5323, 1.206, 0.0, 0.3)]
     return Workload("riemann3_%dx%d" % (n, n), s, _four_states(s, states, 0.7, 0.7), t_end=t_end)
+
+
+def riemann_cfg6(n: int = 800, t_end: float = 1.6, flux: int = GKS) -> Workload:
+    """Sect. 4.2 interaction of planar contact discontinuities on [0,2]^2 (four constant states split
+    at (1,1)); GKS with S2O4 (time limiter on) or L-F with SSP-RK3; outflow boundaries."""
+    s = Settings(nx=n, ny=n, x0=0.0, x1=2.0, y0=0.0, y1=2.0, cfl=0.5, bc=(OUTFLOW,) * 4, flux=flux,
+                 time_scheme=S2O4 if flux == GKS else SSPRK3)
+    states = [(1.0, -0.75, 0.5, 1.0), (3.0, -0.75, -0.5, 1.0), (1.0, 0.75, -0.5, 1.0), (2.0, 0.75, 0.5, 1.0)]
+    return Workload("riemann6_%dx%d" % (n, n), s, _four_states(s, states, 1.0, 1.0), t_end=t_end)
 
 
 def problem_123(ma: float, n: int = 100, flux: int = GKS, ny: int = 4) -> Workload:
