@@ -74,6 +74,25 @@ def parse():
     return p.parse_args()
 
 
+def max_over_ranks(x: float, ws: int) -> float:
+    """The maximum of x over all ranks (x itself on one rank).  NCCL reduces a device tensor, gloo
+    (the CPU test backend) a host one."""
+    if ws <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(units_per_rank: float, ws: int, max_ms: float) -> float:
+    """Whole-job throughput of ws independent replicas (weak scaling): every rank processes the
+    same units, and the job takes as long as its slowest rank."""
+    return units_per_rank * ws / (max_ms * 1e-3)
+
+
 def dist_init():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -177,15 +196,11 @@ def bench_ours(args, ws, rank, local):
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
     total_ms = sum(step_ms)
-    if ws > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, ws)
     timing = sol.timing()
     sol.set_timing(False)
     launches = sum(v["launches"] for v in timing.values())
-    units = 2.0 * cells * args.steps * ws            # cell-stages processed by all ranks
-    value = units / (total_ms * 1e-3)
+    value = replica_throughput(2.0 * cells * args.steps, ws, total_ms)
 
     # roofline of the dominant kernel (the Gauss-point flux kernel)
     share = {k: v["ms"] for k, v in timing.items()}
@@ -236,9 +251,9 @@ def bench_ours(args, ws, rank, local):
             Wh[...] = Wr
             ah[...] = ar
         torch.cuda.synchronize()
-        e_ms = (time.perf_counter() - e0) * 1e3
+        e_ms = max_over_ranks((time.perf_counter() - e0) * 1e3, ws)
         nbytes = Wh.nbytes + ah.nbytes
-        e2e = {"value": 2.0 * cells * ke / (e_ms * 1e-3) * ws, "unit": UNIT, "steps": ke,
+        e2e = {"value": replica_throughput(2.0 * cells * ke, ws, e_ms), "unit": UNIT, "steps": ke,
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
     counters = sol.counters()
     sol.close()
