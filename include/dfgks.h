@@ -53,7 +53,8 @@ typedef enum { DFGKS_BC_PERIODIC = 0, DFGKS_BC_OUTFLOW = 1, DFGKS_BC_REFLECT = 2
 typedef enum { DFGKS_TIME_S2O4 = 0, DFGKS_TIME_SSPRK3 = 1 } dfgks_time_scheme;
 
 typedef struct dfgks_config {
-    int nx, ny;                    /* interior cells, each >= 1 (>= 3 along a periodic direction) */
+    int nx, ny;                    /* interior cells, each >= 1 (>= 3 along a direction with a periodic or
+                                      reflecting boundary: the ghost layers copy 3 interior cells) */
     double x0, x1, y0, y1;         /* domain [x0,x1] x [y0,y1] */
     double gamma;                  /* specific heat ratio; K = (4 - 2 gamma)/(gamma - 1) (Sect. 2.2) */
     double cfl;                    /* dt = cfl * min over cells of the dt_rule bound */

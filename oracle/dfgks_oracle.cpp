@@ -994,9 +994,9 @@ static bool make_ctx(const oracle_cfg* cfg, Ctx& C) {
     C.dx = (cfg->x1 - cfg->x0) / cfg->nx;
     C.dy = (cfg->y1 - cfg->y0) / cfg->ny;
     C.K = (4.0 - 2.0 * cfg->gamma) / (cfg->gamma - 1.0);      // internal degrees of freedom, 2-D
-    // periodic wrap needs at least G interior cells to copy from
-    if ((cfg->bc[0] == 0 || cfg->bc[1] == 0) && cfg->nx < G) return false;
-    if ((cfg->bc[2] == 0 || cfg->bc[3] == 0) && cfg->ny < G) return false;
+    // periodic wrap and wall mirror both need G interior cells to copy from (outflow copies one)
+    if ((cfg->bc[0] != 1 || cfg->bc[1] != 1) && cfg->nx < G) return false;
+    if ((cfg->bc[2] != 1 || cfg->bc[3] != 1) && cfg->ny < G) return false;
     return true;
 }
 

@@ -303,8 +303,9 @@ static bool batch_config_ok(const dfgks_config* c) {
     const int bcs[4] = {c->bc_xlo, c->bc_xhi, c->bc_ylo, c->bc_yhi};
     for (int k = 0; k < 4; ++k) if (bcs[k] < 0 || bcs[k] > 2) return false;
     if ((c->bc_xlo == 0) != (c->bc_xhi == 0) || (c->bc_ylo == 0) != (c->bc_yhi == 0)) return false;
-    if (c->bc_xlo == 0 && c->nx < G) return false;
-    if (c->bc_ylo == 0 && c->ny < G) return false;
+    // periodic wrap and wall mirror both copy G interior cells into the ghost layers
+    if ((c->bc_xlo != 1 || c->bc_xhi != 1) && c->nx < G) return false;
+    if ((c->bc_ylo != 1 || c->bc_yhi != 1) && c->ny < G) return false;
     return c->time_scheme == 0 && (c->tau_reading == 0 || c->tau_reading == 1) && (c->dt_rule == 0 || c->dt_rule == 1);
 }
 

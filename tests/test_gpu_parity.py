@@ -381,3 +381,66 @@ def test_stage_operator_argument_errors():
             sol.residual(Wd, ad, 0.0)
         with pytest.raises(_lib.DfgksError):
             sol.residual(Wd, ad, 1e-3, flux=7)
+
+
+# ---------------------------------------------------------------- degenerate meshes
+
+O_, P_, R_ = I.OUTFLOW, I.PERIODIC, I.REFLECT
+DEGENERATE = {
+    # name: (generator, nx, ny, boundaries, flux, seed)
+    "1x1_outflow_gks": (I.random_rough, 1, 1, (O_,) * 4, I.GKS, 5),
+    "1x7_outflow_gks": (I.random_rough, 1, 7, (O_,) * 4, I.GKS, 5),
+    "7x1_outflow_lf_fallbacks": (I.random_rough, 7, 1, (O_,) * 4, I.LF, 5),
+    "3x3_periodic_gks": (I.random_rough, 3, 3, (P_,) * 4, I.GKS, 5),
+    "3x5_reflect_gks": (I.random_rough, 3, 5, (R_,) * 4, I.GKS, 7),
+    "35x2_periodic_x_lf": (I.random_rough, 35, 2, (P_, P_, O_, O_), I.LF, 5),
+    "2x33_walls_in_y_gks": (I.random_smooth, 2, 33, (O_, O_, R_, R_), I.GKS, 5),
+}
+
+
+@pytest.mark.parametrize("name", list(DEGENERATE))
+def test_degenerate_meshes_three_steps(name):
+    # one cell, one row or column, and the smallest periodic and walled meshes: every stencil
+    # reaches into ghost layers that hold copies (or mirrors) of the same few cells
+    gen, nx, ny, bc, flux, seed = DEGENERATE[name]
+    w = gen(nx, ny, seed, bc=bc, flux=flux, time_limiter=1 if flux == I.GKS else 0)
+    (rc, Wo, ao, to, dts_o, st), (done, W, a, t, dts, cnt) = run_both(w, 3)
+    assert rc == 0 and done == 3
+    err = comp_rel_err(W, Wo)
+    if err > 1e-12:
+        _, env, _ = oracle_envelope(w.settings, w.W0, 3)
+        assert err <= 2.0 * env, (err, env)
+    assert np.allclose(dts, dts_o, rtol=1e-11, atol=0.0)
+    assert cnt["fallbacks"] == st.fallbacks
+    assert cnt["df_normal"] == st.df_normal and cnt["df_tangential"] == st.df_tangential
+
+
+def test_degenerate_row_positivity_failure_matches_oracle():
+    # a 7 x 1 rough row on which the first GKS step loses positivity: same step and cell as the
+    # oracle, the initial state kept
+    from paper_2402_10914_gb300 import _lib
+    w = I.random_rough(7, 1, 5, bc=(O_,) * 4, flux=I.GKS, time_limiter=1)
+    a0 = oracle.alpha0(w.settings, w.W0)
+    rc, Wo, ao, to, dts_o, st = oracle.run(w.settings, w.W0, a0, 3)
+    assert rc == 5 and len(dts_o) == 0
+    with Solver(w.settings) as sol:
+        sol.set_ic(w.W0)
+        with pytest.raises(_lib.DfgksError) as e:
+            sol.step(3)
+        assert e.value.status == _lib.ENONPOS
+        W, a, t, step = sol.get_state()
+        fstep, fi, fj = sol.last_error()
+    assert step == 0 and t == 0.0 and np.array_equal(W, w.W0)
+    assert (fstep, fi, fj) == (st.fail_step, st.fail_i, st.fail_j)
+
+
+@pytest.mark.parametrize("nx,ny,bc", [(2, 6, (R_, R_, O_, O_)), (6, 2, (O_, O_, R_, R_)), (2, 6, (P_,) * 4),
+                                      (0, 6, (O_,) * 4), (6, 0, (O_,) * 4), (1 << 16, 1 << 16, (O_,) * 4)])
+def test_create_rejects_meshes_the_ghost_layers_cannot_fill(nx, ny, bc):
+    # periodic wrap and wall mirror copy 3 interior cells per side; zero sizes and meshes above
+    # 2^28 cells are refused before anything is allocated
+    from paper_2402_10914_gb300 import _lib
+    s = I.random_smooth(8, 8, 1, bc=(O_,) * 4, flux=I.GKS).settings.with_(nx=nx, ny=ny, bc=bc)
+    with pytest.raises(_lib.DfgksError) as e:
+        Solver(s)
+    assert e.value.status == _lib.EINVAL

@@ -288,3 +288,16 @@ def test_robustness_inputs_have_their_mach_numbers():
         X, Y = np.meshgrid(xc, yc)
         assert np.allclose(u * X + v * Y, 0.0, atol=1e-9 * ma)        # purely azimuthal
         assert np.all(u * Y - v * X > 0)                              # rotating clockwise: (u, v) = v0 (sin, -cos)
+
+
+@pytest.mark.parametrize("nx,ny,bc", [(2, 6, (I.REFLECT, I.REFLECT, I.OUTFLOW, I.OUTFLOW)),
+                                      (6, 2, (I.OUTFLOW, I.OUTFLOW, I.REFLECT, I.REFLECT)),
+                                      (2, 6, (I.PERIODIC,) * 4)])
+def test_oracle_refuses_walls_and_wraps_on_fewer_than_three_cells(nx, ny, bc):
+    # a reflecting wall mirrors ghost k onto interior cell k (k < 3), a periodic wrap copies the
+    # opposite 3 cells: with fewer interior cells the map would read other ghost cells
+    w = I.random_smooth(nx, ny, 1, bc=bc, flux=I.GKS)
+    with pytest.raises(AssertionError):
+        oracle.alpha0(w.settings, w.W0)
+    ok = I.random_smooth(3 if nx == 2 else nx, 3 if ny == 2 else ny, 1, bc=bc, flux=I.GKS)
+    assert np.all(np.isfinite(oracle.alpha0(ok.settings, ok.W0)))
