@@ -45,8 +45,8 @@ def emu(tmp_path_factory):
     return run
 
 
-def rel(a, b):
-    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+def rel(a, b, floor=1e-300):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), floor))
 
 
 CASES = [
@@ -60,6 +60,14 @@ CASES = [
     ("lf_rough_periodic", lambda: I.random_rough(14, 11, seed=44, bc=(I.PERIODIC,) * 4, flux=I.LF,
                                                  time_limiter=0), "rand"),
     ("quadrants", lambda: I.quadrants(24, seed=2), "ones"),
+    # degenerate meshes: one cell, one row, one column, the smallest periodic and walled meshes
+    ("gks_one_cell", lambda: I.random_rough(1, 1, seed=5, flux=I.GKS, time_limiter=1), "rand"),
+    ("lf_one_row", lambda: I.random_rough(7, 1, seed=6, flux=I.LF, time_limiter=0), "rand"),
+    ("gks_one_column", lambda: I.random_rough(1, 7, seed=5, flux=I.GKS, time_limiter=1), "rand"),
+    ("gks_3x3_periodic", lambda: I.random_rough(3, 3, seed=5, bc=(I.PERIODIC,) * 4, flux=I.GKS,
+                                                time_limiter=1), "rand"),
+    ("gks_3x5_reflect", lambda: I.random_smooth(3, 5, seed=7, bc=(I.REFLECT,) * 4, flux=I.GKS,
+                                                time_limiter=1), "ones"),
 ]
 
 
@@ -77,5 +85,7 @@ def test_host_build_matches_oracle(emu, name, make, akind):
     # differences in the smoothness indicators move it by up to ~3e-8 there
     assert rel(out[0], L) <= 1e-12 and rel(out[1], dL) <= 1e-11 and rel(out[2], dLt) <= 1e-7
     ref = oracle.residual_vjp(s, w.W0, alpha, dt, Lb, dLb, dLtb)
-    assert rel(out[3], ref) <= 1e-12, rel(out[3], ref)
-    assert rel(out[4], ref) <= 1e-12, rel(out[4], ref)        # GKS reverse from the forward's tape
+    # floor 1: the cotangents are N(0, 1); on one cell with outflow ghosts the state is uniform
+    # for every W, L is identically zero and both sides return rounding noise (~1e-16)
+    assert rel(out[3], ref, 1.0) <= 1e-12, rel(out[3], ref, 1.0)
+    assert rel(out[4], ref, 1.0) <= 1e-12, rel(out[4], ref, 1.0)     # GKS reverse from the forward's tape
