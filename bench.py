@@ -42,6 +42,10 @@ FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
 # 2*DFMA + DADD + DMUL of one launch divided by its 2*(n+1)*n Gauss points
 # (profiles/k_flux_gks_fp64_counts_quadrants128.md).  Valid for the kernel source it was measured on.
 FLUX_GKS_FLOPS_PER_GP = 1773.0
+# FP64-pipe thread instructions (DFMA + DADD + DMUL) per Gauss point from the same capture.  Each
+# occupies one issue slot of the FP64 units whether it does 2 flops (DFMA) or 1, so the issue rate
+# against 152 SM x 2 per clock x 2.07 GHz says how busy the pipe the kernel is bound by is.
+FLUX_GKS_FP64_INST_PER_GP = 1130.0
 # DRAM bytes (read + write) per launch of that kernel on this workload, mean of the x and y launches
 # of one ncu capture at 400 x 400 (profiles/k_flux_gks_traffic_quadrants400.md); None once the
 # kernel has changed since the capture.
@@ -219,6 +223,9 @@ def bench_ours(args, ws, rank, local):
         roof.update({"achieved": round(achieved, 2), "frac": round(achieved / FP64_PEAK_GFLOPS, 4),
                      "flops_per_unit": FLUX_GKS_FLOPS_PER_GP, "unit_of_work": "Gauss point",
                      "units_per_launch": gps_per_launch})
+        if FLUX_GKS_FP64_INST_PER_GP is not None:
+            issue = FLUX_GKS_FP64_INST_PER_GP * gps_per_launch / (avg_flux_ms * 1e-3)
+            roof["fp64_issue_frac"] = round(issue / (FP64_PEAK_GFLOPS / 2.0 * 1e9), 4)
     else:
         roof.update({"achieved": None, "frac": None})
     # FP64 probe as a cross-check of the denominator
