@@ -569,65 +569,131 @@ DFK_HD void tape_get_vec(const Tape& tp, int b, double v[4]) {
     for (int i = 0; i < 4; ++i) v[i] = tp.get(b + i);
 }
 
+// under the tau = tau_n reading, one side's slope coefficients A of the time derivative of its
+// Maxwellian (from the compatibility condition over the full velocity space) and <u A psi> over the
+// side's half space, recomputed from the tape.  SIGN +1: left side, -1: right side.
+template <int SIGN, class Tape>
+DFK_HD void tau_side_terms(const Tape& tp, const Maxw& s, double K, Mom& mF, double bA[4], double A[4]) {
+    double ax[4], ay[4], t1[4], t2[4];
+    tape_get_vec(tp, SIGN > 0 ? TG_ALX : TG_ARX, ax);
+    tape_get_vec(tp, SIGN > 0 ? TG_ALY : TG_ARY, ay);
+    fill_moments<0>(s, K, mF);
+    a_mom<1, 0>(mF, ax, t1);
+    a_mom<0, 1>(mF, ay, t2);
+    for (int i = 0; i < 4; ++i) bA[i] = -(t1[i] + t2[i]);
+    slope_solve(s, bA, A);
+}
+
+// reverse of one side's share of gks_flux (SIGN +1 left, -1 right): its half-space moment sums in
+// the flux, in the kinetic weighting of the equilibrium state and in its slopes, its slope
+// coefficients and (tau = tau_n) its extra terms; accumulates into the side's Maxwellian adjoint sb
+// and the Gauss-point state adjoint Pb.  The sides are reversed one after the other so that only
+// one side's moments and their adjoints are live at a time.
+template <int SIGN, class Tape>
+DFK_HD void gks_side_reverse(const Tape& tp, const GPState& P, const Maxw& s, const SchemeConsts& S,
+                             const double Wcb[4], const double Wcxb[4], const double Wcyb[4], const double M0b[4],
+                             const double M1b[4], const double M2b[4], MaxwBar& sb, GPStateBar& Pb) {
+    constexpr bool left = SIGN > 0;
+    Mom m;
+    tape_get_mom(tp, left ? TG_ML : TG_MR, m);
+    MomBar mb;
+    zero(mb);
+    double axb[4] = {0, 0, 0, 0}, ayb[4] = {0, 0, 0, 0};
+    if (S.tau_reading == 1) {
+        Mom mF;
+        double bA[4], A[4], Ab[4] = {0, 0, 0, 0}, bAb[4] = {0, 0, 0, 0}, nb[4], ax[4], ay[4];
+        tau_side_terms<SIGN>(tp, s, S.K, mF, bA, A);
+        a_mom_vjp<1, 0>(m, A, M2b, mb, Ab);
+        slope_solve_vjp(s, bA, Ab, bAb, sb);
+        for (int i = 0; i < 4; ++i) nb[i] = -bAb[i];
+        tape_get_vec(tp, left ? TG_ALX : TG_ARX, ax);
+        tape_get_vec(tp, left ? TG_ALY : TG_ARY, ay);
+        MomBar mFb;
+        zero(mFb);
+        a_mom_vjp<1, 0>(mF, ax, nb, mFb, axb);
+        a_mom_vjp<0, 1>(mF, ay, nb, mFb, ayb);
+        fill_moments_vjp<0>(s, S.K, mF, mFb, sb);
+    }
+    // flux moments <u psi> of the side's initial distribution
+    psi_mom_vjp<1, 0, 0>(m, M0b, mb);
+    // kinetic weighting of the equilibrium state and its slopes
+    double pb[4], tb[4];
+    const int tp0 = left ? TG_PL0 : TG_PR0, tx0 = left ? TG_LX0 : TG_RX0, ty0 = left ? TG_LY0 : TG_RY0;
+    for (int i = 0; i < 4; ++i) {
+        sb.rho += Wcb[i] * tp.get(tp0 + i) + Wcxb[i] * tp.get(tx0 + i) + Wcyb[i] * tp.get(ty0 + i);
+        pb[i] = Wcb[i] * s.rho;
+    }
+    psi_mom_vjp<0, 0, 0>(m, pb, mb);
+    // the side's moment sums of a_x (kinetic weighting, flux moment) and of a_y, each reversed as one
+    {
+        double ax[4];
+        tape_get_vec(tp, left ? TG_ALX : TG_ARX, ax);
+        AMomRev<0, 4, 0, 2> X(m, ax);
+        for (int i = 0; i < 4; ++i) tb[i] = Wcxb[i] * s.rho;
+        X.out_vjp<0, 0>(m, tb, mb);
+        X.out_vjp<2, 0>(m, M1b, mb);
+        X.finish(m, ax, mb, axb);
+    }
+    {
+        double ay[4];
+        tape_get_vec(tp, left ? TG_ALY : TG_ARY, ay);
+        AMomRev<0, 3, 0, 3> Y(m, ay);
+        for (int i = 0; i < 4; ++i) tb[i] = Wcyb[i] * s.rho;
+        Y.out_vjp<0, 0>(m, tb, mb);
+        Y.out_vjp<1, 1>(m, M1b, mb);
+        Y.finish(m, ay, mb, ayb);
+    }
+    // slope coefficients from the side's normal and tangential slopes (b = W_n / rho, W_t / rho)
+    double b[4], bb[4] = {0, 0, 0, 0};
+    for (int i = 0; i < 4; ++i) b[i] = P.Wn[i] * s.ir;
+    slope_solve_vjp(s, b, axb, bb, sb);
+    for (int i = 0; i < 4; ++i) {
+        Pb.Wn[i] += bb[i] * s.ir;
+        sb.ir += bb[i] * P.Wn[i];
+        bb[i] = 0.0;
+        b[i] = P.Wt[i] * s.ir;
+    }
+    slope_solve_vjp(s, b, ayb, bb, sb);
+    for (int i = 0; i < 4; ++i) { Pb.Wt[i] += bb[i] * s.ir; sb.ir += bb[i] * P.Wt[i]; }
+    fill_moments_vjp<SIGN>(s, S.K, m, mb, sb);
+    maxw_of_vjp(P.W, S, s, sb, Pb.W);
+}
+
 // reverse of gks_flux from its taped forward intermediates: given Fb, dFb (local frame) accumulates
-// into Lb, Rb.  The tau = tau_n reading's extra terms are recomputed from the tape.
+// into Lb, Rb.  The tau = tau_n reading's extra terms are recomputed from the tape.  Taped values
+// are read where they are used: the reverse holds many adjoint accumulators at once, and values
+// kept live from the start would spill.
 template <class Tape>
 DFK_HD void gks_flux_reverse(const Tape& tp, const GPState& L, const GPState& R, double dt, const SchemeConsts& S,
                              const double Fb[4], const double dFb[4], GPStateBar& Lb, GPStateBar& Rb) {
     const double K = S.K;
     const Maxw sl = tape_get_maxw(tp, TG_SL), sr = tape_get_maxw(tp, TG_SR), sc = tape_get_maxw(tp, TG_SC);
-    Mom ml, mr, mc;
-    tape_get_mom(tp, TG_ML, ml);
-    tape_get_mom(tp, TG_MR, mr);
-    tape_get_mom(tp, TG_MC, mc);
-    double alx[4], aly[4], arx[4], ary[4], acx[4], acy[4], Ac[4], bct[4];
-    tape_get_vec(tp, TG_ALX, alx); tape_get_vec(tp, TG_ALY, aly);
-    tape_get_vec(tp, TG_ARX, arx); tape_get_vec(tp, TG_ARY, ary);
-    tape_get_vec(tp, TG_ACX, acx); tape_get_vec(tp, TG_ACY, acy);
-    tape_get_vec(tp, TG_AC, Ac); tape_get_vec(tp, TG_BCT, bct);
-    double Wc[4], Wcx[4], Wcy[4], pl0[4], pr0[4], lx0[4], rx0[4], ly0[4], ry0[4];
-    tape_get_vec(tp, TG_WC, Wc); tape_get_vec(tp, TG_WCX, Wcx); tape_get_vec(tp, TG_WCY, Wcy);
-    tape_get_vec(tp, TG_PL0, pl0); tape_get_vec(tp, TG_PR0, pr0);
-    tape_get_vec(tp, TG_LX0, lx0); tape_get_vec(tp, TG_RX0, rx0);
-    tape_get_vec(tp, TG_LY0, ly0); tape_get_vec(tp, TG_RY0, ry0);
-    double Mc0[4], Mc1[4], Mc2[4], Ml0[4], Mr0[4], Ml1[4], Mr1[4];
-    tape_get_vec(tp, TG_MC0, Mc0); tape_get_vec(tp, TG_MC1, Mc1); tape_get_vec(tp, TG_MC2, Mc2);
-    tape_get_vec(tp, TG_ML0, Ml0); tape_get_vec(tp, TG_MR0, Mr0);
-    tape_get_vec(tp, TG_ML1, Ml1); tape_get_vec(tp, TG_MR1, Mr1);
     const double q = tp.get(TG_Q);
-    double bLx[4], bLy[4], bRx[4], bRy[4], bcx[4], bcy[4], t1[4], t2[4];
-    for (int i = 0; i < 4; ++i) {
-        bLx[i] = L.Wn[i] * sl.ir; bLy[i] = L.Wt[i] * sl.ir; bRx[i] = R.Wn[i] * sr.ir; bRy[i] = R.Wt[i] * sr.ir;
-        bcx[i] = Wcx[i] * sc.ir; bcy[i] = Wcy[i] * sc.ir;
-    }
     double rT = S.C1 + S.C2 * fabs(q);
     TimeCoeffs tc = time_coeffs(rT, dt, S.tau_reading);
-    double Ml2[4] = {0, 0, 0, 0}, Mr2[4] = {0, 0, 0, 0}, Al[4] = {0, 0, 0, 0}, Ar[4] = {0, 0, 0, 0};
-    double bAl[4] = {0, 0, 0, 0}, bAr[4] = {0, 0, 0, 0};
-    Mom mlF, mrF;
+    double Ml2[4] = {0, 0, 0, 0}, Mr2[4] = {0, 0, 0, 0};
     if (S.tau_reading == 1) {
-        fill_moments<0>(sl, K, mlF);
-        fill_moments<0>(sr, K, mrF);
-        a_mom<1, 0>(mlF, alx, t1); a_mom<0, 1>(mlF, aly, t2);
-        for (int i = 0; i < 4; ++i) bAl[i] = -(t1[i] + t2[i]);
-        slope_solve(sl, bAl, Al);
-        a_mom<1, 0>(mrF, arx, t1); a_mom<0, 1>(mrF, ary, t2);
-        for (int i = 0; i < 4; ++i) bAr[i] = -(t1[i] + t2[i]);
-        slope_solve(sr, bAr, Ar);
-        a_mom<1, 0>(ml, Al, Ml2);
-        a_mom<1, 0>(mr, Ar, Mr2);
+        Mom m, mF;
+        double bA[4], A[4];
+        tau_side_terms<+1>(tp, sl, K, mF, bA, A);
+        tape_get_mom(tp, TG_ML, m);
+        a_mom<1, 0>(m, A, Ml2);
+        tau_side_terms<-1>(tp, sr, K, mF, bA, A);
+        tape_get_mom(tp, TG_MR, m);
+        a_mom<1, 0>(m, A, Mr2);
     }
     // ---- reverse of the final combination
     MaxwBar slb, srb, scb;
     zero(slb); zero(srb); zero(scb);
-    MomBar mlb, mrb, mcb;
-    zero(mlb); zero(mrb); zero(mcb);
     double Mc0b[4], Mc1b[4], Mc2b[4], Ml0b[4], Mr0b[4], Ml1b[4], Mr1b[4], Ml2b[4], Mr2b[4];
     double rTb = 0.0;
     for (int i = 0; i < 4; ++i) {
-        double c0 = sc.rho * Mc0[i], c1 = sc.rho * Mc1[i], c2 = sc.rho * Mc2[i];
-        double g0 = sl.rho * Ml0[i] + sr.rho * Mr0[i];
-        double g1 = sl.rho * Ml1[i] + sr.rho * Mr1[i];
+        const double Mc0 = tp.get(TG_MC0 + i), Mc1 = tp.get(TG_MC1 + i), Mc2 = tp.get(TG_MC2 + i);
+        const double Ml0 = tp.get(TG_ML0 + i), Mr0 = tp.get(TG_MR0 + i);
+        const double Ml1 = tp.get(TG_ML1 + i), Mr1 = tp.get(TG_MR1 + i);
+        double c0 = sc.rho * Mc0, c1 = sc.rho * Mc1, c2 = sc.rho * Mc2;
+        double g0 = sl.rho * Ml0 + sr.rho * Mr0;
+        double g1 = sl.rho * Ml1 + sr.rho * Mr1;
         double g2 = sl.rho * Ml2[i] + sr.rho * Mr2[i];
         double c0b = Fb[i] * tc.gcF.v + dFb[i] * tc.gcD.v;
         double c1b = Fb[i] * tc.acF.v + dFb[i] * tc.acD.v;
@@ -637,10 +703,10 @@ DFK_HD void gks_flux_reverse(const Tape& tp, const GPState& L, const GPState& R,
         double g2b = Fb[i] * tc.AlrF.v + dFb[i] * tc.AlrD.v;
         rTb += Fb[i] * (tc.gcF.d * c0 + tc.acF.d * c1 + tc.AcF.d * c2 + tc.glrF.d * g0 + tc.alrF.d * g1 + tc.AlrF.d * g2)
              + dFb[i] * (tc.gcD.d * c0 + tc.acD.d * c1 + tc.AcD.d * c2 + tc.glrD.d * g0 + tc.alrD.d * g1 + tc.AlrD.d * g2);
-        scb.rho += c0b * Mc0[i] + c1b * Mc1[i] + c2b * Mc2[i];
+        scb.rho += c0b * Mc0 + c1b * Mc1 + c2b * Mc2;
         Mc0b[i] = c0b * sc.rho; Mc1b[i] = c1b * sc.rho; Mc2b[i] = c2b * sc.rho;
-        slb.rho += g0b * Ml0[i] + g1b * Ml1[i] + g2b * Ml2[i];
-        srb.rho += g0b * Mr0[i] + g1b * Mr1[i] + g2b * Mr2[i];
+        slb.rho += g0b * Ml0 + g1b * Ml1 + g2b * Ml2[i];
+        srb.rho += g0b * Mr0 + g1b * Mr1 + g2b * Mr2[i];
         Ml0b[i] = g0b * sl.rho; Ml1b[i] = g1b * sl.rho; Ml2b[i] = g2b * sl.rho;
         Mr0b[i] = g0b * sr.rho; Mr1b[i] = g1b * sr.rho; Mr2b[i] = g2b * sr.rho;
     }
@@ -651,113 +717,62 @@ DFK_HD void gks_flux_reverse(const Tape& tp, const GPState& L, const GPState& R,
         slb.p += rTb * S.C2 * sg * 2.0 * sr.p / den;
         srb.p += rTb * S.C2 * sg * (-2.0) * sl.p / den;
     }
-    double alxb[4] = {0, 0, 0, 0}, alyb[4] = {0, 0, 0, 0}, arxb[4] = {0, 0, 0, 0}, aryb[4] = {0, 0, 0, 0};
-    double acxb[4] = {0, 0, 0, 0}, acyb[4] = {0, 0, 0, 0}, Acb[4] = {0, 0, 0, 0};
-    if (S.tau_reading == 1) {
-        double Alb[4] = {0, 0, 0, 0}, Arb[4] = {0, 0, 0, 0}, bAlb[4] = {0, 0, 0, 0}, bArb[4] = {0, 0, 0, 0};
-        MomBar mlFb, mrFb;
-        zero(mlFb); zero(mrFb);
-        a_mom_vjp<1, 0>(ml, Al, Ml2b, mlb, Alb);
-        a_mom_vjp<1, 0>(mr, Ar, Mr2b, mrb, Arb);
-        slope_solve_vjp(sl, bAl, Alb, bAlb, slb);
-        slope_solve_vjp(sr, bAr, Arb, bArb, srb);
-        double nb[4];
-        for (int i = 0; i < 4; ++i) nb[i] = -bAlb[i];
-        a_mom_vjp<1, 0>(mlF, alx, nb, mlFb, alxb);
-        a_mom_vjp<0, 1>(mlF, aly, nb, mlFb, alyb);
-        for (int i = 0; i < 4; ++i) nb[i] = -bArb[i];
-        a_mom_vjp<1, 0>(mrF, arx, nb, mrFb, arxb);
-        a_mom_vjp<0, 1>(mrF, ary, nb, mrFb, aryb);
-        fill_moments_vjp<0>(sl, K, mlF, mlFb, slb);
-        fill_moments_vjp<0>(sr, K, mrF, mrFb, srb);
-    }
-    // flux moments and the compatibility condition of A^c: the equilibrium's moment sums of a_x
-    // and of a_y are reversed together (their outputs share P, Q terms)
-    psi_mom_vjp<1, 0, 0>(mc, Mc0b, mcb);
-    a_mom_vjp<1, 0>(mc, Ac, Mc2b, mcb, Acb);
-    psi_mom_vjp<1, 0, 0>(ml, Ml0b, mlb);
-    psi_mom_vjp<1, 0, 0>(mr, Mr0b, mrb);
-    double bctb[4] = {0, 0, 0, 0};
-    slope_solve_vjp(sc, bct, Acb, bctb, scb);
-    {
-        double nb[4];
-        for (int i = 0; i < 4; ++i) nb[i] = -bctb[i];
-        AMomRev<1, 4, 0, 2> Cx(mc, acx);
-        AMomRev<0, 3, 0, 3> Cy(mc, acy);
-        Cx.out_vjp<2, 0>(mc, Mc1b, mcb);
-        Cx.out_vjp<1, 0>(mc, nb, mcb);
-        Cx.finish(mc, acx, mcb, acxb);
-        Cy.out_vjp<1, 1>(mc, Mc1b, mcb);
-        Cy.out_vjp<0, 1>(mc, nb, mcb);
-        Cy.finish(mc, acy, mcb, acyb);
-    }
-    // equilibrium slopes
-    double bcxb[4] = {0, 0, 0, 0}, bcyb[4] = {0, 0, 0, 0};
-    slope_solve_vjp(sc, bcx, acxb, bcxb, scb);
-    slope_solve_vjp(sc, bcy, acyb, bcyb, scb);
+    // ---- the equilibrium state's part: its flux moments and the compatibility condition of A^c
+    // (the moment sums of a_x and of a_y reversed together: their outputs share P, Q terms), its
+    // slopes and its Maxwellian
     double Wcb[4] = {0, 0, 0, 0}, Wcxb[4], Wcyb[4];
-    for (int i = 0; i < 4; ++i) {
-        Wcxb[i] = bcxb[i] * sc.ir;
-        Wcyb[i] = bcyb[i] * sc.ir;
-        scb.ir += bcxb[i] * Wcx[i] + bcyb[i] * Wcy[i];
-    }
-    fill_moments_vjp<0>(sc, K, mc, mcb, scb);
-    maxw_of_vjp(Wc, S, sc, scb, Wcb);
-    // kinetic weighting of the equilibrium state and its slopes
-    double plb[4], prb[4];
-    for (int i = 0; i < 4; ++i) {
-        slb.rho += Wcb[i] * pl0[i] + Wcxb[i] * lx0[i] + Wcyb[i] * ly0[i];
-        srb.rho += Wcb[i] * pr0[i] + Wcxb[i] * rx0[i] + Wcyb[i] * ry0[i];
-        plb[i] = Wcb[i] * sl.rho;
-        prb[i] = Wcb[i] * sr.rho;
-    }
-    psi_mom_vjp<0, 0, 0>(ml, plb, mlb);
-    psi_mom_vjp<0, 0, 0>(mr, prb, mrb);
-    // each side's moment sums of a_x (kinetic weighting, flux moment) and of a_y, reversed together
-    double tb[4];
     {
-        AMomRev<0, 4, 0, 2> X(ml, alx);
-        for (int i = 0; i < 4; ++i) tb[i] = Wcxb[i] * sl.rho;
-        X.out_vjp<0, 0>(ml, tb, mlb);
-        X.out_vjp<2, 0>(ml, Ml1b, mlb);
-        X.finish(ml, alx, mlb, alxb);
+        Mom mc;
+        tape_get_mom(tp, TG_MC, mc);
+        MomBar mcb;
+        zero(mcb);
+        double Acb[4] = {0, 0, 0, 0}, bctb[4] = {0, 0, 0, 0}, acxb[4] = {0, 0, 0, 0}, acyb[4] = {0, 0, 0, 0};
+        psi_mom_vjp<1, 0, 0>(mc, Mc0b, mcb);
+        {
+            double Ac[4];
+            tape_get_vec(tp, TG_AC, Ac);
+            a_mom_vjp<1, 0>(mc, Ac, Mc2b, mcb, Acb);
+        }
+        {
+            double bct[4];
+            tape_get_vec(tp, TG_BCT, bct);
+            slope_solve_vjp(sc, bct, Acb, bctb, scb);
+        }
+        {
+            double acx[4], acy[4], nb[4];
+            tape_get_vec(tp, TG_ACX, acx);
+            tape_get_vec(tp, TG_ACY, acy);
+            for (int i = 0; i < 4; ++i) nb[i] = -bctb[i];
+            AMomRev<1, 4, 0, 2> Cx(mc, acx);
+            AMomRev<0, 3, 0, 3> Cy(mc, acy);
+            Cx.out_vjp<2, 0>(mc, Mc1b, mcb);
+            Cx.out_vjp<1, 0>(mc, nb, mcb);
+            Cx.finish(mc, acx, mcb, acxb);
+            Cy.out_vjp<1, 1>(mc, Mc1b, mcb);
+            Cy.out_vjp<0, 1>(mc, nb, mcb);
+            Cy.finish(mc, acy, mcb, acyb);
+        }
+        {
+            double Wcx[4], Wcy[4], bcx[4], bcy[4], bcxb[4] = {0, 0, 0, 0}, bcyb[4] = {0, 0, 0, 0};
+            tape_get_vec(tp, TG_WCX, Wcx);
+            tape_get_vec(tp, TG_WCY, Wcy);
+            for (int i = 0; i < 4; ++i) { bcx[i] = Wcx[i] * sc.ir; bcy[i] = Wcy[i] * sc.ir; }
+            slope_solve_vjp(sc, bcx, acxb, bcxb, scb);
+            slope_solve_vjp(sc, bcy, acyb, bcyb, scb);
+            for (int i = 0; i < 4; ++i) {
+                Wcxb[i] = bcxb[i] * sc.ir;
+                Wcyb[i] = bcyb[i] * sc.ir;
+                scb.ir += bcxb[i] * Wcx[i] + bcyb[i] * Wcy[i];
+            }
+        }
+        fill_moments_vjp<0>(sc, K, mc, mcb, scb);
+        double Wc[4];
+        tape_get_vec(tp, TG_WC, Wc);
+        maxw_of_vjp(Wc, S, sc, scb, Wcb);
     }
-    {
-        AMomRev<0, 4, 0, 2> X(mr, arx);
-        for (int i = 0; i < 4; ++i) tb[i] = Wcxb[i] * sr.rho;
-        X.out_vjp<0, 0>(mr, tb, mrb);
-        X.out_vjp<2, 0>(mr, Mr1b, mrb);
-        X.finish(mr, arx, mrb, arxb);
-    }
-    {
-        AMomRev<0, 3, 0, 3> Y(ml, aly);
-        for (int i = 0; i < 4; ++i) tb[i] = Wcyb[i] * sl.rho;
-        Y.out_vjp<0, 0>(ml, tb, mlb);
-        Y.out_vjp<1, 1>(ml, Ml1b, mlb);
-        Y.finish(ml, aly, mlb, alyb);
-    }
-    {
-        AMomRev<0, 3, 0, 3> Y(mr, ary);
-        for (int i = 0; i < 4; ++i) tb[i] = Wcyb[i] * sr.rho;
-        Y.out_vjp<0, 0>(mr, tb, mrb);
-        Y.out_vjp<1, 1>(mr, Mr1b, mrb);
-        Y.finish(mr, ary, mrb, aryb);
-    }
-    // side slope coefficients
-    double bb[4];
-    for (int i = 0; i < 4; ++i) bb[i] = 0.0;
-    slope_solve_vjp(sl, bLx, alxb, bb, slb);
-    for (int i = 0; i < 4; ++i) { Lb.Wn[i] += bb[i] * sl.ir; slb.ir += bb[i] * L.Wn[i]; bb[i] = 0.0; }
-    slope_solve_vjp(sl, bLy, alyb, bb, slb);
-    for (int i = 0; i < 4; ++i) { Lb.Wt[i] += bb[i] * sl.ir; slb.ir += bb[i] * L.Wt[i]; bb[i] = 0.0; }
-    slope_solve_vjp(sr, bRx, arxb, bb, srb);
-    for (int i = 0; i < 4; ++i) { Rb.Wn[i] += bb[i] * sr.ir; srb.ir += bb[i] * R.Wn[i]; bb[i] = 0.0; }
-    slope_solve_vjp(sr, bRy, aryb, bb, srb);
-    for (int i = 0; i < 4; ++i) { Rb.Wt[i] += bb[i] * sr.ir; srb.ir += bb[i] * R.Wt[i]; }
-    fill_moments_vjp<+1>(sl, K, ml, mlb, slb);
-    fill_moments_vjp<-1>(sr, K, mr, mrb, srb);
-    maxw_of_vjp(L.W, S, sl, slb, Lb.W);
-    maxw_of_vjp(R.W, S, sr, srb, Rb.W);
+    // ---- the two sides
+    gks_side_reverse<+1>(tp, L, sl, S, Wcb, Wcxb, Wcyb, Ml0b, Ml1b, Ml2b, slb, Lb);
+    gks_side_reverse<-1>(tp, R, sr, S, Wcb, Wcxb, Wcyb, Mr0b, Mr1b, Mr2b, srb, Rb);
 }
 
 // adjoint of gks_flux: the forward recomputed into a local tape, then its reverse
