@@ -226,6 +226,8 @@ def bench_ours(args, ws, rank, local):
         if FLUX_GKS_FP64_INST_PER_GP is not None:
             issue = FLUX_GKS_FP64_INST_PER_GP * gps_per_launch / (avg_flux_ms * 1e-3)
             roof["fp64_issue_frac"] = round(issue / (FP64_PEAK_GFLOPS / 2.0 * 1e9), 4)
+    if FLUX_GKS_TRAFFIC_BYTES is not None:
+        roof["dram_gbs"] = round(FLUX_GKS_TRAFFIC_BYTES / (avg_flux_ms * 1e-3) / 1e9, 1)
     else:
         roof.update({"achieved": None, "frac": None})
     # FP64 probe as a cross-check of the denominator
@@ -532,10 +534,39 @@ def bench_adjoint(reps: int, warmup: int = 1, n: int = 256, nsteps: int = 100, c
     tf = statistics.median([g[0] for g in G])
     tb = statistics.median([g[1] for g in G])
     rev = G[-1][2]
-    return {"workload": adj_workload(n, nsteps, ckpt), "ratio": (tf + tb) / fwd, "forward_ms": fwd, "forward_checkpointed_ms": tf,
+    return {"workload": adj_workload(n, nsteps, ckpt), "ratio": (tf + tb) / fwd,
+            "gradient_cell_stage_per_s": 2.0 * n * n * nsteps / ((tf + tb) * 1e-3), "forward_ms": fwd, "forward_checkpointed_ms": tf,
             "backward_ms": tb, "backward_over_forward": tb / fwd, "reps": reps,
             "backward_kernel_ms": {k: round(v["ms"], 3) for k, v in rev.items()},
             "definition": "(checkpointed forward + backward) / plain forward, same %d steps" % nsteps}
+
+
+def oracle_adjoint_sample(n=32, steps=1):
+    """The CPU oracle as it stands on the gradient of the vortex workload, on a bounded sample: its
+    reverse sweep (a recorded forward pass, then the adjoints of every stage from the operation
+    tape of its residual) over `steps` steps of the isentropic vortex on an n x n mesh.  That tape
+    holds every operation of a stage (about 2 GB per step at 32 x 32), which puts the 256 x 256
+    workload itself out of its reach."""
+    import numpy as np
+    import oracle
+    from paper_2402_10914_gb300 import inputs as I
+    w = I.vortex(n, steps=steps)
+    s = w.settings
+    cores = oracle.max_threads()
+    dt = oracle.cfl_dt(s, w.W0)
+    a0 = oracle.alpha0(s, w.W0)
+    t0 = time.perf_counter()
+    rc, W, _, _, _, _ = oracle.run(s, w.W0, a0, steps, dt_fixed=dt)
+    t_fwd = time.perf_counter() - t0
+    assert rc == 0
+    WTb = np.zeros_like(W)
+    WTb[0] = 2.0 * W[0]
+    t0 = time.perf_counter()
+    oracle.run_vjp(s, w.W0, [dt] * steps, WTb)
+    t_grad = time.perf_counter() - t0
+    return {"value": 2.0 * n * n * steps / t_grad, "unit": "cell-stage/s (gradient)", "cores": cores,
+            "kind": "oracle", "sample": "gradient of J = sum rho^2 over %d step(s) of the %dx%d vortex" % (steps, n, n),
+            "forward_s": t_fwd, "gradient_s": t_grad, "gradient_over_forward": t_grad / t_fwd}
 
 
 def oracle_sample(n_threads=None, steps=1, n=400):
@@ -613,6 +644,8 @@ def main():
                                                     "flux": "GKS", "time_limiter": 1, "ckpt_every": 10,
                                                     "l2": "flushed before each timed region"},
                     "adjoint": a}
+            if not args.no_cpu:
+                line["cpu_baseline"] = oracle_adjoint_sample()
             print(json.dumps(line))
         return
     r = bench_ours(args, ws, rank, local)
@@ -642,6 +675,11 @@ def main():
             line["adjoint"] = bench_adjoint(1, 1)
         except Exception as e:  # the benchmark line must still be printed
             line["adjoint"] = {"workload": adj_workload(256, 100), "ratio": None, "error": str(e)}
+        if not args.no_cpu:
+            try:
+                line["adjoint"]["cpu_baseline"] = oracle_adjoint_sample()
+            except Exception as e:
+                line["adjoint"]["cpu_baseline"] = {"value": None, "kind": "oracle", "sample": "failed: %s" % e}
     print(json.dumps(line))
 
 
