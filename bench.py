@@ -334,8 +334,32 @@ def bench_batch(args):
                        "sides": sorted(set(w.settings.nx for w in ws)), "shapes": shapes, "status": rc,
                        "problems_lost_positivity": failed, "l2": "one 256 MiB flush before each timed region"},
             "per_problem_sequential": {"value": units_seq / t_seq, "ms_per_step": t_seq / args.steps * 1e3},
-            "speedup_vs_per_problem": (units / t_batch) / (units_seq / t_seq)}
+            "speedup_vs_per_problem": (units / t_batch) / (units_seq / t_seq),
+            "timing": "host clock around each call, which returns after a device synchronisation (the batch "
+                      "runs on the handle's private stream, where its graph is captured)"}
+    if not args.no_cpu:
+        try:
+            line["cpu_baseline"] = oracle_batch_sample(ws[:16])
+        except Exception as e:
+            line["cpu_baseline"] = {"value": None, "kind": "oracle", "sample": "failed: %s" % e}
     print(json.dumps(line))
+
+
+def oracle_batch_sample(ws):
+    """The CPU oracle as it stands on a bounded sample of the batch: one S2O4 step of each given
+    problem, one after another, on all host cores."""
+    import oracle
+    cores = oracle.max_threads()
+    units, t = 0.0, 0.0
+    for w in ws:
+        a0 = oracle.alpha0(w.settings, w.W0)
+        t0 = time.perf_counter()
+        rc, *_ = oracle.run(w.settings, w.W0, a0, 1)
+        t += time.perf_counter() - t0
+        if rc == 0:
+            units += 2.0 * w.settings.nx * w.settings.ny
+    return {"value": units / t, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "one S2O4 step of each of the first %d problems (%.1f s)" % (len(ws), t)}
 
 
 def bench_blast(args):
