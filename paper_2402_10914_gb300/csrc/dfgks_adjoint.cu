@@ -154,6 +154,7 @@ DFK_HD void ka_faces_body(const Mesh& m, const SchemeConsts& S, const double* __
     }
     // per characteristic component: the reconstruction once, then its reverse
     double qv[2][4], qt[2][4], Qb[5][4];
+#pragma unroll
     for (int k = 0; k < 4; ++k) {
         double sq[5] = {Q[0][k], Q[1][k], Q[2][k], Q[3][k], Q[4][k]};
         double vb[2] = {qvb[0][k], qvb[1][k]}, sb[2] = {slb[0][k], slb[1][k]};
@@ -244,7 +245,9 @@ DFK_HD void ka_lines_body(const Mesh& m, const SchemeConsts& S, const double* __
     back_project_T(B, WRnb, qRnb);
     double qL[4], qLn[4], qR[4], qRn[4], Qb[6][4];
     for (int s = 0; s < 6; ++s) for (int k = 0; k < 4; ++k) Qb[s][k] = 0.0;
+#pragma unroll
     for (int k = 0; k < 4; ++k) {
+#pragma unroll
         for (int sd = 0; sd < 2; ++sd) {
             // side 0: cell f-1, value at xi = +1/2; side 1: cell f, mirrored stencil, slope sign reversed
             double sq[5];
