@@ -89,8 +89,18 @@ class Solver:
         _lib.check(_lib.lib().dfgks_set_state(self._h, _ptr(W), _ptr(alpha), float(t), int(step), int(on_dev)),
                    "dfgks_set_state")
 
-    def get_state(self, device: bool = False):
-        if device:
+    def get_state(self, device: bool = False, out=None):
+        """(W, alpha, t, step).  out: optional (W, alpha) to fill instead of new arrays, both host
+        arrays (numpy, ideally views of pinned memory: the copy then needs no staging) or both CUDA
+        tensors, float64, C-contiguous, shaped (4, ny, nx) and (ny, nx)."""
+        if out is not None:
+            W, a = out
+            device = isinstance(W, torch.Tensor) and W.is_cuda
+            if tuple(W.shape) != self.shape or tuple(a.shape) != self.shape[1:] or \
+                    device != (isinstance(a, torch.Tensor) and a.is_cuda):
+                raise ValueError("get_state: out must be (W, alpha) of shapes %s and %s, both on the host or "
+                                 "both on the device" % (self.shape, self.shape[1:]))
+        elif device:
             W = torch.empty(self.shape, dtype=torch.float64, device="cuda")
             a = torch.empty(self.shape[1:], dtype=torch.float64, device="cuda")
         else:

@@ -444,3 +444,26 @@ def test_create_rejects_meshes_the_ghost_layers_cannot_fill(nx, ny, bc):
     with pytest.raises(_lib.DfgksError) as e:
         Solver(s)
     assert e.value.status == _lib.EINVAL
+
+
+def test_get_state_into_caller_buffers():
+    # pinned host buffers and device tensors receive the same bytes as freshly allocated arrays;
+    # mismatched shapes or a host/device mix are refused before the library is called
+    w = rough(20, 18, seed=14, flux=I.GKS)
+    with Solver(w.settings) as sol:
+        sol.set_ic(w.W0)
+        sol.step(2)
+        W, a, t, step = sol.get_state()
+        Wp = torch.empty((4, 18, 20), dtype=torch.float64, pin_memory=True).numpy()
+        ap = torch.empty((18, 20), dtype=torch.float64, pin_memory=True).numpy()
+        W2, a2, t2, step2 = sol.get_state(out=(Wp, ap))
+        Wd = torch.empty((4, 18, 20), dtype=torch.float64, device="cuda")
+        ad = torch.empty((18, 20), dtype=torch.float64, device="cuda")
+        sol.get_state(out=(Wd, ad))
+        with pytest.raises(ValueError):
+            sol.get_state(out=(Wp, ad))
+        with pytest.raises(ValueError):
+            sol.get_state(out=(Wp[:, :, :10].copy(), ap))
+    assert W2 is Wp and a2 is ap and (t2, step2) == (t, step) == (t, 2)
+    assert np.array_equal(Wp, W) and np.array_equal(ap, a)
+    assert np.array_equal(host(Wd), W) and np.array_equal(host(ad), a)
