@@ -344,8 +344,9 @@ __global__ void __launch_bounds__(128) ka_flux(Mesh m, SchemeConsts S, AdjointAr
                                                long long gs, const double* __restrict__ fr, long long fs,
                                                const double* dtp, double* __restrict__ lb, long long ls,
                                                double* __restrict__ gb, double* __restrict__ tape = nullptr) {
-    ka_flux_body<DIR, FLUX, TAPED>(m, S, a, gp, gs, fr, fs, *dtp, lb, ls, gb, blockIdx.x * blockDim.x + threadIdx.x,
-                                   blockIdx.y * blockDim.y + threadIdx.y, blockIdx.z, tape);
+    int ax, ay;
+    sweep_xy(faces_lx<DIR>(m), ax, ay);
+    ka_flux_body<DIR, FLUX, TAPED>(m, S, a, gp, gs, fr, fs, *dtp, lb, ls, gb, ax, ay, blockIdx.y, tape);
 }
 
 template <int DIR, bool TAPED>
@@ -354,8 +355,9 @@ __global__ void __launch_bounds__(128) ka_faces(Mesh m, SchemeConsts S, const do
                                                 const double* __restrict__ gp, const double* __restrict__ gb,
                                                 long long gs, double* __restrict__ lb, double* __restrict__ Wb,
                                                 double* __restrict__ ftape) {
-    ka_faces_body<DIR, TAPED>(m, S, alpha, lines, ls, gp, gb, gs, lb, Wb, blockIdx.x * blockDim.x + threadIdx.x,
-                              blockIdx.y * blockDim.y + threadIdx.y, blockIdx.z, ftape);
+    int ax, ay;
+    sweep_xy(faces_lx<DIR>(m), ax, ay);
+    ka_faces_body<DIR, TAPED>(m, S, alpha, lines, ls, gp, gb, gs, lb, Wb, ax, ay, blockIdx.y, ftape);
 }
 
 template <int DIR, bool TAPED>
@@ -363,8 +365,9 @@ __global__ void __launch_bounds__(128) ka_lines(Mesh m, SchemeConsts S, const do
                                                 const double* __restrict__ alpha, const double* __restrict__ lines,
                                                 const double* __restrict__ lb, long long ls, double* __restrict__ Wb,
                                                 double* __restrict__ ltape) {
-    ka_lines_body<DIR, TAPED>(m, S, W, alpha, lines, lb, ls, Wb, blockIdx.x * blockDim.x + threadIdx.x,
-                              blockIdx.y * blockDim.y + threadIdx.y, ltape);
+    int ax, ay;
+    sweep_xy(lines_lx<DIR>(m), ax, ay);
+    ka_lines_body<DIR, TAPED>(m, S, W, alpha, lines, lb, ls, Wb, ax, ay, ltape);
 }
 
 __global__ void ka_fold_y(Mesh m, double* Wb) { ka_fold_y_body(m, Wb, blockIdx.x * blockDim.x + threadIdx.x - G); }
@@ -377,12 +380,10 @@ template <int DIR>
 static void adjoint_dir(const Mesh& m, const SchemeConsts& S, int flux, const AdjointArgs& a, const double* W,
                         const double* alpha, const double* dtp, const SweepBuffers& B, double* lb, double* gbuf,
                         double* Wb, cudaStream_t s, KernelTimer* T) {
-    const int nn = DIR == 0 ? m.nx : m.ny, nt = DIR == 0 ? m.ny : m.nx;
-    dim3 blk(32, 4);
-    int fx = DIR == 0 ? nn + 1 : nt, fy = DIR == 0 ? nt : nn + 1;
-    dim3 gf((fx + 31) / 32, (fy + 3) / 4, 2);
-    int lx = DIR == 0 ? nn + 1 : nt + 4, ly = DIR == 0 ? nt + 4 : nn + 1;
-    dim3 gl((lx + 31) / 32, (ly + 3) / 4);
+    // the forward sweep's 1-D grids (sweep_xy)
+    const dim3 blk(128);
+    const dim3 gf(sweep_blocks(faces_lx<DIR>(m), faces_ly<DIR>(m)), 2);
+    const dim3 gl(sweep_blocks(lines_lx<DIR>(m), lines_ly<DIR>(m)));
     cudaMemsetAsync(lb, 0, sizeof(double) * LR_COUNT * B.line_stride, s);
     if (T) T->begin(KK_FLUX);
     if (flux == 0 && B.tape[DIR])

@@ -48,6 +48,25 @@ struct Geo {
     DFK_HD long long nfaces() const { return (long long)(nn + 1) * nt; }
 };
 
+// Index spaces of the sweep kernels, row-major, rows lx wide (the thread-x direction of the bodies):
+// face lines (f, t+2) and face sides / Gauss points (f, t), with f the normal and t the tangential
+// index, f along the rows for x-faces and t along the rows for y-faces.
+template <int DIR> DFK_HD int lines_lx(const Mesh& m) { return DIR == 0 ? m.nx + 1 : m.nx + 4; }
+template <int DIR> DFK_HD int lines_ly(const Mesh& m) { return DIR == 0 ? m.ny + 4 : m.ny + 1; }
+template <int DIR> DFK_HD int faces_lx(const Mesh& m) { return DIR == 0 ? m.nx + 1 : m.nx; }
+template <int DIR> DFK_HD int faces_ly(const Mesh& m) { return DIR == 0 ? m.ny : m.ny + 1; }
+
+// The sweep kernels run on 1-D grids of 128-thread blocks over such a space: thread i takes
+// (i mod lx, i / lx), so only the grid's last warp is partly idle, where a 2-D grid of 32-wide rows
+// would idle part of every row's last warp (15 of 416 lanes on a 401-face row).  Threads past the
+// end get ay >= ly, which the bodies' bounds checks reject.
+inline unsigned sweep_blocks(int lx, int ly) { return (unsigned)(((long long)lx * ly + 127) / 128); }
+__device__ __forceinline__ void sweep_xy(int lx, int& ax, int& ay) {
+    const int i = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    ax = i % lx;
+    ay = i / lx;
+}
+
 __device__ __forceinline__ void warp_count_add(unsigned long long* dst, int v) {
     int s = __reduce_add_sync(0xffffffffu, v);
     if ((threadIdx.x & 31) == 0 && s) atomicAdd(dst, (unsigned long long)s);

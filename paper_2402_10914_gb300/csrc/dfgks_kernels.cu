@@ -98,13 +98,14 @@ void launch_end_step(DevState* st, double t_end, cudaStream_t s, KernelTimer* T)
 // tangential offset b maps to global column t - b.  Face f lies between normal cells f-1, f.
 // ---------------------------------------------------------------------------------------------
 template <int DIR, bool TAPE = false>
-__global__ void __launch_bounds__(128) k_lines(Mesh m, SchemeConsts S, const double* __restrict__ W,
+__global__ void __launch_bounds__(128, 3) k_lines(Mesh m, SchemeConsts S, const double* __restrict__ W,
                                                const double* __restrict__ alpha, double* __restrict__ lines,
                                                long long ls, DevState* st, const int* halt,
                                                double* __restrict__ ltape = nullptr) {
     if (halted(halt)) return;
-    int ndf = lines_body<DIR, TAPE>(m, S, W, alpha, lines, ls, blockIdx.x * blockDim.x + threadIdx.x,
-                                    blockIdx.y * blockDim.y + threadIdx.y, ltape);
+    int ax, ay;
+    sweep_xy(lines_lx<DIR>(m), ax, ay);
+    int ndf = lines_body<DIR, TAPE>(m, S, W, alpha, lines, ls, ax, ay, ltape);
     if (st) warp_count_add(&st->df_normal, ndf);
 }
 
@@ -114,9 +115,9 @@ __global__ void __launch_bounds__(128) k_faces(Mesh m, SchemeConsts S, const dou
                                                long long ls, double* __restrict__ gp, long long gs,
                                                DevState* st, const int* halt, double* __restrict__ ftape = nullptr) {
     if (halted(halt)) return;
-    int nfb;
-    int ndf = faces_body<DIR, TAPE>(m, S, W, alpha, lines, ls, gp, gs, blockIdx.x * blockDim.x + threadIdx.x,
-                                    blockIdx.y * blockDim.y + threadIdx.y, blockIdx.z, nfb, ftape);
+    int nfb, ax, ay;
+    sweep_xy(faces_lx<DIR>(m), ax, ay);
+    int ndf = faces_body<DIR, TAPE>(m, S, W, alpha, lines, ls, gp, gs, ax, ay, blockIdx.y, nfb, ftape);
     if (st) { warp_count_add(&st->df_tangential, ndf); warp_count_add(&st->fallbacks, nfb); }
 }
 
@@ -126,26 +127,25 @@ __global__ void __launch_bounds__(128) k_flux(Mesh m, SchemeConsts S, const doub
                                               double* __restrict__ fr, long long fs, const double* dtp,
                                               const int* halt, double* __restrict__ tape = nullptr) {
     if (halted(halt)) return;
-    flux_body<DIR, FLUX, ALPHA_ONLY, TAPE>(m, S, lines, ls, gp, gs, fr, fs, ALPHA_ONLY ? 0.0 : *dtp,
-                                           blockIdx.x * blockDim.x + threadIdx.x,
-                                           blockIdx.y * blockDim.y + threadIdx.y, blockIdx.z, tape);
+    int ax, ay;
+    sweep_xy(faces_lx<DIR>(m), ax, ay);
+    flux_body<DIR, FLUX, ALPHA_ONLY, TAPE>(m, S, lines, ls, gp, gs, fr, fs, ALPHA_ONLY ? 0.0 : *dtp, ax, ay,
+                                           blockIdx.y, tape);
 }
 
 template <int DIR>
 static void sweep_dir(const Mesh& m, const SchemeConsts& S, int flux, bool alpha_only, const double* W,
                       const double* alpha, const double* dtp, const SweepBuffers& B, DevState* st,
                       const int* halt, cudaStream_t s, KernelTimer* T) {
-    const int nn = DIR == 0 ? m.nx : m.ny, nt = DIR == 0 ? m.ny : m.nx;
-    dim3 blk(32, 4);
-    // lines: (nn+1) x (nt+4); faces/flux: (nn+1) x nt; thread-x runs along the contiguous index
-    int lx = DIR == 0 ? nn + 1 : nt + 4, ly = DIR == 0 ? nt + 4 : nn + 1;
-    dim3 gl((lx + 31) / 32, (ly + 3) / 4);
+    // 1-D grids over the row-major index spaces of face lines ((nn+1) x (nt+4)) and of face sides /
+    // Gauss points ((nn+1) x nt, two of each per face: grid y); rows run along the contiguous index
+    const dim3 blk(128);
+    const dim3 gl(sweep_blocks(lines_lx<DIR>(m), lines_ly<DIR>(m)));
     if (T) T->begin(KK_LINES);
     if (B.ltape) k_lines<DIR, true><<<gl, blk, 0, s>>>(m, S, W, alpha, B.lines, B.line_stride, st, halt, B.ltape);
     else k_lines<DIR><<<gl, blk, 0, s>>>(m, S, W, alpha, B.lines, B.line_stride, st, halt);
     if (T) T->end(KK_LINES, 1);
-    int fx = DIR == 0 ? nn + 1 : nt, fy = DIR == 0 ? nt : nn + 1;
-    dim3 gf((fx + 31) / 32, (fy + 3) / 4, 2);
+    const dim3 gf(sweep_blocks(faces_lx<DIR>(m), faces_ly<DIR>(m)), 2);
     if (T) T->begin(KK_FACES);
     if (B.ftape)
         k_faces<DIR, true><<<gf, blk, 0, s>>>(m, S, W, alpha, B.lines, B.line_stride, B.gp, B.gp_stride, st, halt, B.ftape);

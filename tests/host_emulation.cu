@@ -59,48 +59,47 @@ int main(int argc, char** argv) {
     for (int j = 0; j < m.ny; ++j) for (int gc = 0; gc < 2 * G; ++gc) ghost_x_body(m, Wg.data(), Ag.data(), gc, j);
     for (int gr = 0; gr < 2 * G; ++gr) for (int i = -G; i < m.nx + G; ++i) ghost_y_body(m, Wg.data(), Ag.data(), i, gr);
     AdjointArgs a = {Lb.data(), dLb.data(), dLtb.data()};
+    // every thread of the kernels' 1-D grids, padded tail included (the bodies must reject it)
+    auto grid = [&](int lx, int ly, auto body) {
+        const long long n = (long long)sweep_blocks(lx, ly) * 128;
+        for (long long i = 0; i < n; ++i) body((int)(i % lx), (int)(i / lx));
+    };
     auto sweep = [&](auto dirc) {
         constexpr int DIR = decltype(dirc)::value;
-        const int nn = DIR == 0 ? m.nx : m.ny, nt = DIR == 0 ? m.ny : m.nx;
-        int lx = DIR == 0 ? nn + 1 : nt + 4, ly = DIR == 0 ? nt + 4 : nn + 1;
-        int fx = DIR == 0 ? nn + 1 : nt, fy = DIR == 0 ? nt : nn + 1;
-        for (int y = 0; y < ly; ++y) for (int x = 0; x < lx; ++x) {
+        const int lx = lines_lx<DIR>(m), ly = lines_ly<DIR>(m), fx = faces_lx<DIR>(m), fy = faces_ly<DIR>(m);
+        grid(lx, ly, [&](int x, int y) {
             if (B.ltape) lines_body<DIR, true>(m, S, Wg.data(), Ag.data(), B.lines, B.line_stride, x, y, B.ltape);
             else lines_body<DIR>(m, S, Wg.data(), Ag.data(), B.lines, B.line_stride, x, y);
-        }
-        for (int z = 0; z < 2; ++z) for (int y = 0; y < fy; ++y) for (int x = 0; x < fx; ++x) {
+        });
+        for (int z = 0; z < 2; ++z) grid(fx, fy, [&](int x, int y) {
             int nfb;
             if (B.ftape) faces_body<DIR, true>(m, S, Wg.data(), Ag.data(), B.lines, B.line_stride, B.gp, B.gp_stride, x, y, z, nfb, B.ftape);
             else faces_body<DIR>(m, S, Wg.data(), Ag.data(), B.lines, B.line_stride, B.gp, B.gp_stride, x, y, z, nfb);
-        }
-        for (int z = 0; z < 2; ++z) for (int y = 0; y < fy; ++y) for (int x = 0; x < fx; ++x) {
+        });
+        for (int z = 0; z < 2; ++z) grid(fx, fy, [&](int x, int y) {
             if (in.flux == 0 && B.tape[DIR]) flux_body<DIR, 0, false, true>(m, S, B.lines, B.line_stride, B.gp, B.gp_stride, B.flux[DIR], B.flux_stride[DIR], in.dt, x, y, z, B.tape[DIR]);
             else if (in.flux == 0) flux_body<DIR, 0, false>(m, S, B.lines, B.line_stride, B.gp, B.gp_stride, B.flux[DIR], B.flux_stride[DIR], in.dt, x, y, z);
             else flux_body<DIR, 1, false>(m, S, B.lines, B.line_stride, B.gp, B.gp_stride, B.flux[DIR], B.flux_stride[DIR], in.dt, x, y, z);
-        }
+        });
     };
     auto reverse = [&](auto dirc) {
         constexpr int DIR = decltype(dirc)::value;
-        const int nn = DIR == 0 ? m.nx : m.ny, nt = DIR == 0 ? m.ny : m.nx;
-        int lx = DIR == 0 ? nn + 1 : nt + 4, ly = DIR == 0 ? nt + 4 : nn + 1;
-        int fx = DIR == 0 ? nn + 1 : nt, fy = DIR == 0 ? nt : nn + 1;
+        const int lx = lines_lx<DIR>(m), ly = lines_ly<DIR>(m), fx = faces_lx<DIR>(m), fy = faces_ly<DIR>(m);
         std::fill(lb.begin(), lb.end(), 0.0);
         std::fill(gb.begin(), gb.end(), -9.0);
-        for (int z = 0; z < 2; ++z) for (int y = 0; y < fy; ++y) for (int x = 0; x < fx; ++x) {
+        for (int z = 0; z < 2; ++z) grid(fx, fy, [&](int x, int y) {
             if (in.flux == 0 && B.tape[DIR]) ka_flux_body<DIR, 0, true>(m, S, a, B.gp, B.gp_stride, B.flux[DIR], B.flux_stride[DIR], in.dt, lb.data(), B.line_stride, gb.data(), x, y, z, B.tape[DIR]);
             else if (in.flux == 0) ka_flux_body<DIR, 0>(m, S, a, B.gp, B.gp_stride, B.flux[DIR], B.flux_stride[DIR], in.dt, lb.data(), B.line_stride, gb.data(), x, y, z);
             else ka_flux_body<DIR, 1>(m, S, a, B.gp, B.gp_stride, B.flux[DIR], B.flux_stride[DIR], in.dt, lb.data(), B.line_stride, gb.data(), x, y, z);
-        }
-        for (int z = 0; z < 2; ++z) for (int y = 0; y < fy; ++y) for (int x = 0; x < fx; ++x)
-        {
+        });
+        for (int z = 0; z < 2; ++z) grid(fx, fy, [&](int x, int y) {
             if (B.ftape) ka_faces_body<DIR, true>(m, S, Ag.data(), B.lines, B.line_stride, B.gp, gb.data(), B.gp_stride, lb.data(), Wbg.data(), x, y, z, B.ftape);
             else ka_faces_body<DIR>(m, S, Ag.data(), B.lines, B.line_stride, B.gp, gb.data(), B.gp_stride, lb.data(), Wbg.data(), x, y, z);
-        }
-        for (int y = 0; y < ly; ++y) for (int x = 0; x < lx; ++x)
-        {
+        });
+        grid(lx, ly, [&](int x, int y) {
             if (B.ltape) ka_lines_body<DIR, true>(m, S, Wg.data(), Ag.data(), B.lines, lb.data(), B.line_stride, Wbg.data(), x, y, B.ltape);
             else ka_lines_body<DIR>(m, S, Wg.data(), Ag.data(), B.lines, lb.data(), B.line_stride, Wbg.data(), x, y);
-        }
+        });
     };
     // forward residual (both directions), for a sanity check of the emulation
     sweep(std::integral_constant<int, 0>());
