@@ -29,10 +29,17 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "FP64 cell-stage updates/s (GKS S2O4 step, four-quadrant 400x400)"
 UNIT = "cell-stage/s"
 SEED = 3
-WORKLOAD = "quadrants_400x400_gks_seed3"
+BENCH_N = 400          # mesh side of the benchmark workload; --n other than this is a scan, not the benchmark
+
+
+def metric_name(n: int) -> str:
+    return "FP64 cell-stage updates/s (GKS S2O4 step, four-quadrant %dx%d)" % (n, n)
+
+
+def workload_name(n: int) -> str:
+    return "quadrants_%dx%d_gks_seed%d" % (n, n, SEED)
 
 # FP64 roofline denominator of this GPU: 152 SMs x 2 FP64 FMA units per SM per clock x 2 flops
 # x 2070 MHz maximum SM clock = 1258.6 GFLOP/s (the recipe's nominal 1.25 TFLOP/s FP64 rate).
@@ -46,10 +53,10 @@ FLUX_GKS_FLOPS_PER_GP = 1773.0
 # occupies one issue slot of the FP64 units whether it does 2 flops (DFMA) or 1, so the issue rate
 # against 152 SM x 2 per clock x 2.07 GHz says how busy the pipe the kernel is bound by is.
 FLUX_GKS_FP64_INST_PER_GP = 1130.0
-# DRAM bytes (read + write) per launch of that kernel on this workload, mean of the x and y launches
-# of one ncu capture at 400 x 400 (profiles/k_flux_gks_traffic_quadrants400.md); None once the
-# kernel has changed since the capture.
-FLUX_GKS_TRAFFIC_BYTES = 64.75e6
+# DRAM bytes (read + write) per launch of that kernel on the 400 x 400 workload, mean of the x and
+# y launches of one ncu capture (profiles/k_flux_gks_traffic_quadrants400.md); None once the kernel
+# has changed since the capture, and not reported for other mesh sizes.
+FLUX_GKS_TRAFFIC_BYTES = 64.27e6
 # steps of the oracle's timed sample (about 0.9 s each at 400 x 400 on 16 Arm cores)
 CPU_SAMPLE_STEPS = 12
 
@@ -212,9 +219,10 @@ def bench_ours(args, ws, rank, local):
     fl = timing["flux"]
     avg_flux_ms = fl["ms"] / max(fl["timed"], 1)
     gps_per_launch = 2.0 * (s.nx + 1) * s.ny       # x- and y-sweeps have the same count on a square mesh
+    traffic = FLUX_GKS_TRAFFIC_BYTES if args.n == BENCH_N else None
     roof = {"kernel": "k_flux<GKS> (Gauss-point flux)", "bound": "alu", "unit": "GFLOP/s",
             "peak": round(FP64_PEAK_GFLOPS, 1), "peak_source": "derived: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz",
-            "avg_launch_ms": avg_flux_ms, "launches_timed": fl["timed"], "traffic": FLUX_GKS_TRAFFIC_BYTES,
+            "avg_launch_ms": avg_flux_ms, "launches_timed": fl["timed"], "traffic": traffic,
             "traffic_unit": "B per launch (ncu dram read+write)",
             "kernel_time_share": {k: round(v / max(sum(share.values()), 1e-30), 4) for k, v in share.items()},
             "dominant_kernel_class": dominant}
@@ -226,8 +234,8 @@ def bench_ours(args, ws, rank, local):
         if FLUX_GKS_FP64_INST_PER_GP is not None:
             issue = FLUX_GKS_FP64_INST_PER_GP * gps_per_launch / (avg_flux_ms * 1e-3)
             roof["fp64_issue_frac"] = round(issue / (FP64_PEAK_GFLOPS / 2.0 * 1e9), 4)
-    if FLUX_GKS_TRAFFIC_BYTES is not None:
-        roof["dram_gbs"] = round(FLUX_GKS_TRAFFIC_BYTES / (avg_flux_ms * 1e-3) / 1e9, 1)
+    if traffic is not None:
+        roof["dram_gbs"] = round(traffic / (avg_flux_ms * 1e-3) / 1e9, 1)
     else:
         roof.update({"achieved": None, "frac": None})
     # FP64 probe as a cross-check of the denominator
@@ -625,10 +633,10 @@ def main():
             times.append(dtw)
         total = sum(times)
         value = 2.0 * args.n * args.n * args.steps / total
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        line = {"metric": metric_name(args.n), "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-                "config": {"workload": WORKLOAD, "nx": args.n, "ny": args.n, "flux": "GKS", "time_limiter": 1,
+                "config": {"workload": workload_name(args.n), "nx": args.n, "ny": args.n, "flux": "GKS", "time_limiter": 1,
                            "cfl": 0.5, "bc": "outflow", "seed": SEED},
                 "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                                  "sample": "one full S2O4 step of the %dx%d workload per benchmark step" % (args.n, args.n)},
@@ -683,10 +691,10 @@ def main():
         except Exception as e:  # the benchmark line must still be printed
             cpu = {"value": None, "unit": UNIT, "cores": None, "kind": "oracle", "sample": "failed: %s" % e}
     line = {
-        "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "metric": metric_name(args.n), "value": r["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "nx": args.n, "ny": args.n, "flux": "GKS", "time_limiter": 1, "cfl": 0.5,
+        "config": {"workload": workload_name(args.n), "nx": args.n, "ny": args.n, "flux": "GKS", "time_limiter": 1, "cfl": 0.5,
                    "bc": "outflow", "seed": SEED, "l2": "flushed before every timed step (256 MiB write)",
                    "parallelism": "replica per GPU" if ws > 1 else "single GPU"},
         "roofline": r["roofline"], "cpu_baseline": cpu, "e2e": r["e2e"], "gpu_launches": r["launches"],
