@@ -62,3 +62,62 @@ def test_sm103a_cubin_only(libpath):
         pytest.skip("cuobjdump unavailable")
     elfs = [l for l in r.stdout.splitlines() if ".cubin" in l]
     assert elfs and all("sm_103a" in l for l in elfs), r.stdout
+
+
+def test_ctypes_structs_match_the_header(tmp_path):
+    # the binding's Config / Counters layouts against the C compiler's view of include/dfgks.h
+    import ctypes
+    from paper_2402_10914_gb300 import _lib
+    fields = [f for f, _ in _lib.Config._fields_]
+    cfields = [f for f, _ in _lib.Counters._fields_]
+    src = tmp_path / "layout.c"
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "dfgks.h"', 'int main(void) {',
+             '  printf("config %zu\\n", sizeof(dfgks_config));', '  printf("counters %zu\\n", sizeof(dfgks_counters));']
+    lines += ['  printf("%s %%zu\\n", offsetof(dfgks_config, %s));' % (f, f) for f in fields]
+    lines += ['  printf("c.%s %%zu\\n", offsetof(dfgks_counters, %s));' % (f, f) for f in cfields]
+    lines += ['  return 0;', '}']
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines())
+    assert int(out["config"]) == ctypes.sizeof(_lib.Config)
+    assert int(out["counters"]) == ctypes.sizeof(_lib.Counters)
+    for f in fields:
+        assert int(out[f]) == getattr(_lib.Config, f).offset, f
+    for f in cfields:
+        assert int(out["c." + f]) == getattr(_lib.Counters, f).offset, f
+
+
+INVALID = {
+    "nx_zero": dict(nx=0), "ny_negative": dict(ny=-4), "nx_above_2^20": dict(nx=(1 << 20) + 1),
+    "cells_above_2^28": dict(nx=1 << 15, ny=(1 << 13) + 1), "empty_domain": dict(x1=0.0),
+    "gamma_one": dict(gamma=1.0), "cfl_zero": dict(cfl=0.0), "eps_zero": dict(eps=0.0), "dH_zero": dict(dH=0.0),
+    "dL_above_one": dict(dL=1.5), "C2_negative": dict(C2=-1.0), "bc_unknown": dict(bc_yhi=3),
+    "periodic_one_side": dict(bc_xlo=0), "periodic_two_cells": dict(nx=2, bc_xlo=0, bc_xhi=0),
+    "wall_two_cells": dict(ny=2, bc_ylo=2), "tau_reading_2": dict(tau_reading=2), "time_scheme_5": dict(time_scheme=5),
+    "dt_rule_2": dict(dt_rule=2),
+}
+
+
+@pytest.mark.parametrize("name", list(INVALID))
+def test_create_refuses_invalid_configs_before_device_work(libpath, name):
+    # dfgks_create and dfgks_batch_create validate the whole configuration before any CUDA call,
+    # so this runs without a GPU
+    import ctypes
+    from paper_2402_10914_gb300 import _lib
+    L = _lib.lib()
+    cfg = _lib.Config()
+    assert L.dfgks_config_default(ctypes.byref(cfg), 16, 12) == 0
+    for k, v in INVALID[name].items():
+        setattr(cfg, k, v)
+    h = ctypes.c_void_p(1234)
+    assert L.dfgks_create(ctypes.byref(cfg), None, ctypes.byref(h)) == _lib.EINVAL
+    assert h.value is None                                   # *out cleared on failure
+    cfgs = (_lib.Config * 2)()
+    assert L.dfgks_config_default(ctypes.byref(cfgs[0]), 16, 16) == 0
+    cfgs[1] = cfg
+    flux = (ctypes.c_int * 2)(0, 1)
+    b = ctypes.c_void_p(1234)
+    assert L.dfgks_batch_create(ctypes.cast(cfgs, ctypes.c_void_p), ctypes.cast(flux, ctypes.c_void_p), 2, None,
+                                ctypes.byref(b)) == _lib.EINVAL
+    assert b.value is None
