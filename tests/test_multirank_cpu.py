@@ -51,3 +51,30 @@ def test_single_rank_needs_no_process_group():
     import bench
     assert bench.max_over_ranks(42.0, 1) == 42.0
     assert bench.replica_throughput(10.0, 1, 1000.0) == pytest.approx(10.0)
+
+
+REQUIRED = {"metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+            "vs_baseline", "dtype", "data", "config", "impl", "cpu_baseline", "e2e"}
+
+
+def test_reference_arm_two_ranks_prints_once():
+    # bench.py --impl reference under a 2-rank launch: rank 0 times the oracle and prints the one
+    # JSON line, rank 1 exits 0 without work or output
+    import json
+    import subprocess
+    port = free_port()
+    procs = []
+    for r in range(2):
+        env = dict(os.environ, MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(r), WORLD_SIZE="2",
+                   LOCAL_RANK=str(r), DFGKS_BENCH_GLOO="1")
+        procs.append(subprocess.Popen([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                                       "--gpus", "2", "--steps", "1", "--warmup", "0", "--n", "16"],
+                                      cwd=ROOT, env=env, stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True))
+    outs = [p.communicate(timeout=600) for p in procs]
+    assert [p.returncode for p in procs] == [0, 0], [o[1][-2000:] for o in outs]
+    lines0 = [l for l in outs[0][0].splitlines() if l.strip()]
+    assert len(lines0) == 1 and outs[1][0].strip() == ""
+    line = json.loads(lines0[0])
+    assert REQUIRED <= set(line) and line["impl"] == "reference" and line["value"] > 0
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["e2e"]["h2d_bytes_per_step"] == 0
+    assert line["config"]["workload"] == "quadrants_16x16_gks_seed3"
