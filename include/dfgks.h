@@ -139,7 +139,9 @@ DFGKS_API dfgks_status dfgks_residual(dfgks* h, const double* W, const double* a
  * memory, dense [4][ny][nx] / [ny][nx]; outputs may be NULL); work is ordered on `stream`
  * (a cudaStream_t, or NULL for the legacy default stream).  No cudaMalloc or cudaFree is called:
  * every intermediate lives in one file-scope 16 MiB device array that each GPU using the library
- * holds until exit.  Meshes above 128 x 128 = 16384 cells are rejected with DFGKS_EINVAL.
+ * holds until exit.  A mesh with a side above 128 cells (nx > 128 or ny > 128) is rejected with
+ * DFGKS_EINVAL, and so is every configuration dfgks_create refuses (for instance a periodic or
+ * reflecting direction with fewer than 3 cells); both checks run before any device work.
  * The first call on a device looks up that array's device address (cudaGetSymbolAddress) with the
  * device current; make that first call before any stream capture.  All calls share the array and
  * it keeps the last call's contents: calls that overlap on the GPU (different streams, concurrent

@@ -55,13 +55,44 @@ def test_library_loads_and_binds_without_gpu(libpath):
     assert L.dfgks_destroy(None) == 0
 
 
-def test_sm103a_cubin_only(libpath):
-    # the library carries sm_103a code only (no PTX for other architectures)
-    r = subprocess.run(["cuobjdump", "--list-elf", libpath], capture_output=True, text=True)
-    if r.returncode != 0:
-        pytest.skip("cuobjdump unavailable")
-    elfs = [l for l in r.stdout.splitlines() if ".cubin" in l]
-    assert elfs and all("sm_103a" in l for l in elfs), r.stdout
+def test_sm103a_only_build_flags():
+    # the library is compiled and linked for sm_103a alone: one -gencode, no PTX for other targets
+    from paper_2402_10914_gb300 import build
+    gencodes = [build.ARCH[i + 1] for i, a in enumerate(build.ARCH) if a == "-gencode"]
+    assert gencodes == ["arch=compute_103a,code=sm_103a"]
+    assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+    assert all("-arch" not in f and "compute_" not in f for f in build.flags() if f not in build.ARCH)
+
+
+def test_noalloc_refuses_what_create_refuses_before_device_work(libpath):
+    # dfgks_residual_noalloc validates its configuration before touching the device, so these
+    # refusals need no GPU; the pointers are never dereferenced
+    import ctypes
+    from paper_2402_10914_gb300 import _lib
+    L = _lib.lib()
+    buf = (ctypes.c_double * 64)()
+    p = ctypes.cast(buf, ctypes.c_void_p)
+
+    def call(nx, ny, bc):
+        cfg = _lib.Config()
+        assert L.dfgks_config_default(ctypes.byref(cfg), nx, ny) == 0
+        cfg.bc_xlo, cfg.bc_xhi, cfg.bc_ylo, cfg.bc_yhi = bc
+        h = ctypes.c_void_p()
+        created = L.dfgks_create(ctypes.byref(cfg), None, ctypes.byref(h)) if nx * ny <= 16 else None
+        rc = L.dfgks_residual_noalloc(ctypes.byref(cfg), None, p, p, ctypes.c_double(1e-3), 0, p, p, p, p)
+        return rc, created
+
+    REF, OUT, PER = 2, 1, 0
+    # a walled or periodic direction needs 3 cells (its ghost map copies or mirrors 3 cells)
+    for nx, ny, bc in [(2, 5, (REF, REF, OUT, OUT)), (2, 5, (REF, OUT, OUT, OUT)), (5, 2, (OUT, OUT, PER, PER)),
+                       (2, 5, (PER, PER, OUT, OUT)), (5, 2, (OUT, OUT, OUT, REF))]:
+        rc, created = call(nx, ny, bc)
+        assert rc == _lib.EINVAL, (nx, ny, bc)
+        assert created == _lib.EINVAL, (nx, ny, bc)
+    # a side above 128 cells is refused, also when the cell count is small (1024 x 16)
+    for nx, ny in [(129, 128), (1024, 16), (16, 129)]:
+        rc, _ = call(nx, ny, (OUT, OUT, OUT, OUT))
+        assert rc == _lib.EINVAL, (nx, ny)
 
 
 def test_ctypes_structs_match_the_header(tmp_path):

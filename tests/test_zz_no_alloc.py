@@ -53,9 +53,12 @@ def test_noalloc_stage_operator_matches_handle_twice_in_a_row():
         for g, r in zip(got[:3], ref[:3]):
             assert comp_rel_err(g.cpu().numpy(), r.cpu().numpy()) <= 1e-12
         assert comp_rel_err(got[3].cpu().numpy()[None], ref[3].cpu().numpy()[None], floor_frac=1e-12) <= 1e-12
-    # a mesh above the stated maximum is rejected before any device work
-    big = I.Settings(nx=129, ny=128)
-    Wb = torch.ones((4, 128, 129), dtype=torch.float64, device="cuda")
-    ab = torch.ones((128, 129), dtype=torch.float64, device="cuda")
-    rc, _ = _noalloc(big, Wb, ab, 1e-3, I.GKS)
-    assert rc == _lib.EINVAL
+    # refused before any device work: a side above 128 cells (also at a small cell count), and a
+    # walled direction with fewer than 3 cells, which dfgks_create refuses as well
+    for nx, ny, bc in [(129, 128, (I.OUTFLOW,) * 4), (1024, 16, (I.OUTFLOW,) * 4),
+                       (2, 5, (I.REFLECT, I.REFLECT, I.OUTFLOW, I.OUTFLOW))]:
+        bad = I.Settings(nx=nx, ny=ny, bc=bc)
+        Wb = torch.ones((4, ny, nx), dtype=torch.float64, device="cuda")
+        ab = torch.ones((ny, nx), dtype=torch.float64, device="cuda")
+        rc, _ = _noalloc(bad, Wb, ab, 1e-3, I.GKS)
+        assert rc == _lib.EINVAL, (nx, ny, bc)
