@@ -16,8 +16,26 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdfgks.so")
-SOURCES = ["dfgks_kernels.cu", "dfgks_capi.cu", "dfgks_probe.cu", "dfgks_noalloc.cu", "dfgks_batch.cu", "dfgks_adjoint.cu"]
+SOURCES = ["dfgks_kernels.cu", "dfgks_capi.cu", "dfgks_probe.cu", "dfgks_noalloc.cu", "dfgks_batch.cu", "dfgks_adjoint.cu",
+           "dfgks_decomp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+# the sources that define the single-problem forward kernels (the profiled ones)
+FORWARD_KERNEL_SOURCES = ["dfgks_device.cuh", "dfgks_bodies.cuh", "dfgks_kernels.cu", "dfgks_internal.h"]
+
+
+def kernel_source_hash() -> str:
+    """sha256 (first 16 hex digits) over the forward kernels' sources and the compile flags: a
+    profile summary records it, and counts measured on other sources are not used."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in FORWARD_KERNEL_SOURCES:
+        h.update(f.encode())
+        with open(os.path.join(CSRC, f), "rb") as fh:
+            h.update(fh.read())
+    h.update(" ".join(ARCH + ["-O3", "-std=c++17"]).encode())
+    return h.hexdigest()[:16]
 
 
 def nvcc() -> str:

@@ -72,7 +72,7 @@ __device__ __forceinline__ void warp_count_add(unsigned long long* dst, int v) {
     if ((threadIdx.x & 31) == 0 && s) atomicAdd(dst, (unsigned long long)s);
 }
 
-DFK_HD void report_fail(DevState* st, int key) {
+DFK_HD void report_fail(DevState* st, long long key) {
 #ifdef __CUDA_ARCH__
     atomicMin(&st->fail_key, (unsigned long long)key);
     if (atomicCAS(&st->err, 0, 5) == 0) st->fail_step = st->step;
@@ -82,6 +82,12 @@ DFK_HD void report_fail(DevState* st, int key) {
     if (st->err == 0) { st->err = 5; st->fail_step = st->step; }
     st->halt = 1;
 #endif
+}
+
+// linear index j*nx + i of cell (i, j) in the enclosing mesh (the mesh itself unless a block)
+DFK_HD long long fail_key(const Mesh& m, int i, int j) {
+    const long long gnx = m.gnx > 0 ? m.gnx : m.nx;
+    return (long long)(j + m.gj0) * gnx + (i + m.gi0);
 }
 
 DFK_HD bool state_ok(const double W[4], double gm1) {
@@ -116,9 +122,11 @@ __device__ __forceinline__ double block_min(double v) {
     return v;
 }
 
-// one ghost cell of the x pass: ghost column gc in [0, 2G), interior row j
+// one ghost cell of the x pass: ghost column gc in [0, 2G), interior row j (a side marked
+// BC_EXTERNAL is left to the halo copy)
 DFK_HD void ghost_x_body(const Mesh& m, double* W, double* alpha, int gc, int j) {
     if (gc >= 2 * G || j >= m.ny) return;
+    if (m.bc[gc < G ? 0 : 1] == BC_EXTERNAL) return;
     int i = gc < G ? gc - G : m.nx + gc - G;
     bool mir;
     int s = ghost_src(i, m.nx, m.bc[0], m.bc[1], mir);
@@ -134,6 +142,7 @@ DFK_HD void ghost_x_body(const Mesh& m, double* W, double* alpha, int gc, int j)
 // one ghost cell of the y pass: column i in [-G, nx+G), ghost row gr in [0, 2G)
 DFK_HD void ghost_y_body(const Mesh& m, double* W, double* alpha, int i, int gr) {
     if (i >= m.nx + G) return;
+    if (m.bc[gr < G ? 2 : 3] == BC_EXTERNAL) return;
     int j = gr < G ? gr - G : m.ny + gr - G;
     bool mir;
     int s = ghost_src(j, m.ny, m.bc[2], m.bc[3], mir);
@@ -188,6 +197,32 @@ DFK_HD int lines_body(const Mesh& m, const SchemeConsts& S, const double* __rest
             double sL[5] = {Q[0][k], Q[1][k], Q[2][k], Q[3][k], Q[4][k]};
             double sR[5] = {Q[5][k], Q[4][k], Q[3][k], Q[2][k], Q[1][k]};   // mirrored about cell f
             double v, sl;
+            if (!TAPE) {
+                // both reconstructions at once: the mirrored stencils share two of their three
+                // quadratic second differences, and the weights' normalisers one division
+                if (!dfL || !dfR || S.time_limiter) {
+                    const double h = 0.5 * kS13;
+                    const double d01 = h * (Q[0][k] - 2.0 * Q[1][k] + Q[2][k]);
+                    const double d12 = h * (Q[1][k] - 2.0 * Q[2][k] + Q[3][k]);
+                    const double d23 = h * (Q[2][k] - 2.0 * Q[3][k] + Q[4][k]);
+                    const double d34 = h * (Q[3][k] - 2.0 * Q[4][k] + Q[5][k]);
+                    const double aL[3] = {d01, d12, d23}, aR[3] = {d34, d23, d12};
+                    AO oL, oR;
+                    ao_finish_pair(ao_core(sL, aL, S), ao_core(sR, aR, S), S, oL, oR);
+                    if (S.time_limiter) {
+                        double n, d;
+                        limiter_fraction(oL, n, d);
+                        if (n * td < tn * d) { tn = n; td = d; tlk = 2 * k; }
+                        limiter_fraction(oR, n, d);
+                        if (n * td < tn * d) { tn = n; td = d; tlk = 2 * k + 1; }
+                    }
+                    if (!dfL) { ao_at_right_edge(oL, sL[2], v, sl); qL[k] = v; qLn[k] = sl * idn; }
+                    if (!dfR) { ao_at_right_edge(oR, sR[2], v, sl); qR[k] = v; qRn[k] = -sl * idn; }
+                }
+                if (dfL) { df_at_right_edge(sL, al[2], v, sl); qL[k] = v; qLn[k] = sl * idn; }
+                if (dfR) { df_at_right_edge(sR, al[3], v, sl); qR[k] = v; qRn[k] = -sl * idn; }
+                continue;
+            }
             if (!dfL || S.time_limiter) {
                 AO o = TAPE ? weno_ao_t(sL, S, PlaneTape{ltape + li, ls}, 2 * k * AT_COUNT) : weno_ao(sL, S);
                 if (S.time_limiter) {
@@ -272,17 +307,38 @@ DFK_HD int faces_body(const Mesh& m, const SchemeConsts& S, const double* __rest
         double qv[2][4], qt[2][4];
         const double idt = 1.0 / g.dtan;
         const long long e = (long long)side * g.nfaces() + g.face(f, t);
+        if (!TAPE && !df) {
+            // the four components' reconstructions in two pairs, one division per pair
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            double sq[5] = {Q[0][k], Q[1][k], Q[2][k], Q[3][k], Q[4][k]};
-            double v[2], s[2];
-            if (df) df_at_gauss(sq, al[1], v, s);
-            else {
-                AO o = TAPE ? weno_ao_t(sq, S, PlaneTape{ftape + e, gs}, k * AT_COUNT) : weno_ao(sq, S);
-                ao_at_gauss(o, sq[2], v, s);
+            for (int k = 0; k < 4; k += 2) {
+                const double sa[5] = {Q[0][k], Q[1][k], Q[2][k], Q[3][k], Q[4][k]};
+                const double sb[5] = {Q[0][k + 1], Q[1][k + 1], Q[2][k + 1], Q[3][k + 1], Q[4][k + 1]};
+                double da[3], db[3];
+                ao_second_differences(sa, da);
+                ao_second_differences(sb, db);
+                AO oa, ob;
+                ao_finish_pair(ao_core(sa, da, S), ao_core(sb, db, S), S, oa, ob);
+                double v[2], s[2];
+                ao_at_gauss(oa, sa[2], v, s);
+                qv[0][k] = v[0]; qv[1][k] = v[1];
+                qt[0][k] = s[0] * idt; qt[1][k] = s[1] * idt;
+                ao_at_gauss(ob, sb[2], v, s);
+                qv[0][k + 1] = v[0]; qv[1][k + 1] = v[1];
+                qt[0][k + 1] = s[0] * idt; qt[1][k + 1] = s[1] * idt;
             }
-            qv[0][k] = v[0]; qv[1][k] = v[1];
-            qt[0][k] = s[0] * idt; qt[1][k] = s[1] * idt;
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                double sq[5] = {Q[0][k], Q[1][k], Q[2][k], Q[3][k], Q[4][k]};
+                double v[2], s[2];
+                if (df) df_at_gauss(sq, al[1], v, s);
+                else {
+                    AO o = TAPE ? weno_ao_t(sq, S, PlaneTape{ftape + e, gs}, k * AT_COUNT) : weno_ao(sq, S);
+                    ao_at_gauss(o, sq[2], v, s);
+                }
+                qv[0][k] = v[0]; qv[1][k] = v[1];
+                qt[0][k] = s[0] * idt; qt[1][k] = s[1] * idt;
+            }
         }
         const int nbase = side == 0 ? LR_WLN : LR_WRN;
         int fbits = 0;
@@ -417,7 +473,7 @@ DFK_HD void update_body(const Mesh& m, const SchemeConsts& S, const UpdateArgs& 
             a.acc[k * dplane + dn] = w + dt * L[k] + 0.5 * dt * dt * dL[k] - (1.0 / 3.0) * dt * dt * dLt[k];
             a.Wout[k * m.plane + g] = Ws[k];
         }
-        if (!state_ok(Ws, S.gm1)) report_fail(st, (int)dn);
+        if (!state_ok(Ws, S.gm1)) report_fail(st, fail_key(m, i, j));
         return;
     }
     if (MODE == UM_S2O4_2) {
@@ -437,7 +493,7 @@ DFK_HD void update_body(const Mesh& m, const SchemeConsts& S, const UpdateArgs& 
 #pragma unroll
     for (int k = 0; k < 4; ++k) a.Wout[k * m.plane + g] = Wo[k];
     if ((MODE == UM_S2O4_2 || MODE == UM_RK_3) && a.alpha_out) a.alpha_out[a.alpha_dense ? dn : g] = an;
-    if (!state_ok(Wo, S.gm1)) report_fail(st, (int)dn);
+    if (!state_ok(Wo, S.gm1)) report_fail(st, fail_key(m, i, j));
 }
 
 }  // namespace dfk

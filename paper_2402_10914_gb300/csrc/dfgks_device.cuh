@@ -225,6 +225,98 @@ DFK_HD AO weno_ao_t(const double q[5], const SchemeConsts& S, const Tape& tp, in
 
 DFK_HD AO weno_ao(const double q[5], const SchemeConsts& S) { return weno_ao_t(q, S, NoTape{}, 0); }
 
+// The forward sweeps' WENO-AO without a tape, split in two so that two reconstructions can share
+// one division: ao_core does everything up to the weights' normaliser, ao_finish applies its
+// reciprocal.  Same formulas as weno_ao_t; the second differences are carried multiplied by
+// sqrt(13/3) (the smoothness indicators then need one multiply less each), and the AO coefficient
+// A2 is scaled back at the end.
+constexpr double kS13 = 2.0816659994661326;            // sqrt(13/3)
+constexpr double kIS13 = 0.48038446141526137;          // sqrt(3/13)
+
+struct AOCore {
+    double a1[4], a2s[4];   // first-derivative coefficients; second ones times sqrt(13/3)
+    double a3, a4;          // quartic's cubic and quartic coefficients
+    double v[4];            // unnormalised weights (scaled by prod^2 when `scaled`)
+    double sum;             // their sum
+    double rmax, rmin, rs;  // limiter ratios as in AO
+};
+
+// second differences of the three quadratic sub-stencils are shared between the left and right
+// reconstructions of a face line; the caller passes them (times sqrt(13/3)/2) in
+DFK_HD AOCore ao_core(const double q[5], const double a2s_q[3], const SchemeConsts& S) {
+    const double qm2 = q[0], qm1 = q[1], q0 = q[2], q1 = q[3], q2 = q[4];
+    AOCore c;
+    c.a1[0] = 0.5 * qm2 - 2.0 * qm1 + 1.5 * q0;
+    c.a1[1] = 0.5 * (q1 - qm1);
+    c.a1[2] = -1.5 * q0 + 2.0 * q1 - 0.5 * q2;
+    c.a1[3] = (5.0 * (qm2 - q2) - 34.0 * (qm1 - q1)) * (1.0 / 48.0);
+    c.a2s[0] = a2s_q[0]; c.a2s[1] = a2s_q[1]; c.a2s[2] = a2s_q[2];
+    c.a2s[3] = (-(qm2 + q2) + 12.0 * (qm1 + q1) - 22.0 * q0) * (kS13 / 16.0);
+    c.a3 = (-(qm2 - q2) + 2.0 * (qm1 - q1)) * (1.0 / 12.0);
+    c.a4 = ((qm2 + q2) - 4.0 * (qm1 + q1) + 6.0 * q0) * (1.0 / 24.0);
+    // Eq. 38 (cell-centred): beta_k = a1^2 + 13/3 a2^2 (+ the quartic's cross and higher terms)
+    const double b0 = c.a1[0] * c.a1[0] + c.a2s[0] * c.a2s[0];
+    const double b1 = c.a1[1] * c.a1[1] + c.a2s[1] * c.a2s[1];
+    const double b2 = c.a1[2] * c.a1[2] + c.a2s[2] * c.a2s[2];
+    const double b3 = c.a1[3] * (c.a1[3] + 0.5 * c.a3) + c.a2s[3] * (c.a2s[3] + (21.0 / 5.0) * kIS13 * c.a4)
+                    + (3129.0 / 80.0) * c.a3 * c.a3 + (87617.0 / 140.0) * c.a4 * c.a4;
+    // Eq. 37 and the WENO-Z weights d_k (1 + r_k^2), r_k = tau / (beta_k + eps), scaled by prod^2
+    const double tau = (fabs(b3 - b0) + fabs(b3 - b1) + fabs(b3 - b2)) * (1.0 / 3.0);
+    const double e0 = b0 + S.eps, e1 = b1 + S.eps, e2 = b2 + S.eps, e3 = b3 + S.eps;
+    const double p01 = e0 * e1, p23 = e2 * e3, prod = p01 * p23;
+    const double t0 = tau * (e1 * p23), t1 = tau * (e0 * p23), t2 = tau * (p01 * e3), t3 = tau * (p01 * e2);
+    const double tmax = fmax(fmax(t0, t1), fmax(t2, t3)), tmin = fmin(fmin(t0, t1), fmin(t2, t3));
+    if (prod < 1e150 && tmax < 1e150) {
+        const double p2 = prod * prod;
+        c.v[0] = S.d[0] * (p2 + t0 * t0); c.v[1] = S.d[1] * (p2 + t1 * t1);
+        c.v[2] = S.d[2] * (p2 + t2 * t2); c.v[3] = S.d[3] * (p2 + t3 * t3);
+        c.rmax = tmax; c.rmin = tmin; c.rs = prod;
+    } else {
+        const double r0 = tau / e0, r1 = tau / e1, r2 = tau / e2, r3 = tau / e3;
+        c.v[0] = S.d[0] * (1.0 + r0 * r0); c.v[1] = S.d[1] * (1.0 + r1 * r1);
+        c.v[2] = S.d[2] * (1.0 + r2 * r2); c.v[3] = S.d[3] * (1.0 + r3 * r3);
+        c.rmax = fmax(fmax(r0, r1), fmax(r2, r3)); c.rmin = fmin(fmin(r0, r1), fmin(r2, r3)); c.rs = 1.0;
+    }
+    c.sum = (c.v[0] + c.v[1]) + (c.v[2] + c.v[3]);
+    return c;
+}
+
+// second differences of q (times sqrt(13/3)/2) for the three quadratic sub-stencils
+DFK_HD void ao_second_differences(const double q[5], double a2s[3]) {
+    a2s[0] = (0.5 * kS13) * (q[0] - 2.0 * q[1] + q[2]);
+    a2s[1] = (0.5 * kS13) * (q[1] - 2.0 * q[2] + q[3]);
+    a2s[2] = (0.5 * kS13) * (q[2] - 2.0 * q[3] + q[4]);
+}
+
+// the AO polynomial's coefficients from a core and iv = 1 / c.sum
+DFK_HD AO ao_finish(const AOCore& c, double iv, const SchemeConsts& S) {
+    AO o;
+    const double c3 = c.v[3] * iv * S.inv_d3;
+    const double c0 = c.v[0] * iv - c3 * S.d[0], c1 = c.v[1] * iv - c3 * S.d[1], c2 = c.v[2] * iv - c3 * S.d[2];
+    o.A1 = c0 * c.a1[0] + c1 * c.a1[1] + c2 * c.a1[2] + c3 * c.a1[3];
+    o.A2 = (c0 * c.a2s[0] + c1 * c.a2s[1] + c2 * c.a2s[2] + c3 * c.a2s[3]) * kIS13;
+    o.c3a3 = c3 * c.a3;
+    o.c3a4 = c3 * c.a4;
+    o.rmax = c.rmax; o.rmin = c.rmin; o.rs = c.rs;
+    return o;
+}
+
+// two reconstructions finished with one division: 1/(sa sb) times sb and sa (both sums lie in
+// [1e-50, 1e150] on the scaled branch, so the product neither overflows nor underflows)
+DFK_HD void ao_finish_pair(const AOCore& a, const AOCore& b, const SchemeConsts& S, AO& oa, AO& ob) {
+    double ia, ib;
+    if (a.sum < 1e150 && b.sum < 1e150) {
+        const double r = 1.0 / (a.sum * b.sum);
+        ia = b.sum * r;
+        ib = a.sum * r;
+    } else {
+        ia = 1.0 / a.sum;
+        ib = 1.0 / b.sum;
+    }
+    oa = ao_finish(a, ia, S);
+    ob = ao_finish(b, ib, S);
+}
+
 // time-limiter ingredient 2 at2 / (at1 + at2) of one reconstruction (Sect. 2.2), as numerator and
 // (positive) denominator, so that a minimum over several needs one division at the end
 DFK_HD void limiter_fraction(const AO& o, double& num, double& den) {
@@ -595,13 +687,17 @@ DFK_HD void lf_flux(const GPState& L, const GPState& R, const SchemeConsts& S,
     }
 }
 
-// DF factor of one Gauss point (Sect. 3.2), local-frame states
+// DF factor of one Gauss point (Sect. 3.2), local-frame states: one division for both densities,
+// reciprocal square roots for the sound speeds, |dp|/p_l + |dp|/p_r as |dp| (p_l + p_r)/(p_l p_r)
 DFK_HD double df_alpha(const double WL[4], const double WR[4], const SchemeConsts& S) {
-    EulerPt l = euler_pt(WL, S), r = euler_pt(WR, S);
-    double jp = fabs(l.p - r.p);
-    double icl = 1.0 / l.c, icr = 1.0 / r.c;
-    double dn = l.u * icl - r.u * icr, dtg = l.v * icl - r.v * icr;
-    double D = jp / l.p + jp / r.p + dn * dn + dtg * dtg;
+    const double rr = 1.0 / (WL[0] * WR[0]);
+    const double irl = WR[0] * rr, irr = WL[0] * rr;
+    const double ul = WL[1] * irl, vl = WL[2] * irl, ur = WR[1] * irr, vr = WR[2] * irr;
+    const double pl = S.gm1 * (WL[3] - 0.5 * WL[0] * (ul * ul + vl * vl));
+    const double pr = S.gm1 * (WR[3] - 0.5 * WR[0] * (ur * ur + vr * vr));
+    const double icl = rsqrt(S.gamma * pl * irl), icr = rsqrt(S.gamma * pr * irr);
+    const double dn = ul * icl - ur * icr, dtg = vl * icl - vr * icr;
+    const double D = fabs(pl - pr) * (pl + pr) / (pl * pr) + dn * dn + dtg * dtg;
     return 1.0 / (1.0 + D * D);
 }
 

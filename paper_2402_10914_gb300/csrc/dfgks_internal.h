@@ -56,9 +56,14 @@ struct Mesh {
     int NYg;            // ny + 2G
     long long plane;    // P * NYg
     double dx, dy;
-    int bc[4];          // x-low, x-high, y-low, y-high
+    int bc[4];          // x-low, x-high, y-low, y-high; BC_EXTERNAL: ghosts written by a halo copy
     int dt_rule;        // CFL bound per cell: 0 per-direction minimum, 1 summed inverse
+    int gi0, gj0, gnx;  // a block of a larger mesh: its first cell there and that mesh's nx
+                        // (0, 0, nx for a whole mesh); positivity failures report that mesh's index
 };
+
+// boundary code of a block side whose ghost layers a neighbouring block's halo copy fills
+constexpr int BC_EXTERNAL = 3;
 
 __host__ __device__ __forceinline__ long long gid(const Mesh& m, int i, int j) {
     return (long long)(j + G) * m.P + (i + G);
@@ -125,6 +130,8 @@ struct AdjointArgs { const double* Lb; const double* dtLb; const double* dtLtb; 
 
 // ---- launchers (dfgks_kernels.cu) -----------------------------------------------------------
 void launch_fill_ghosts(const Mesh& m, double* W, double* alpha, const int* halt, cudaStream_t s, KernelTimer* T = nullptr);
+// one pass of the ghost fill: 0 = ghost columns of the interior rows, 1 = ghost rows of all columns
+void launch_ghost_pass(int dir, const Mesh& m, double* W, double* alpha, const int* halt, cudaStream_t s);
 void launch_cfl_min(const Mesh& m, const double* W, double gamma, DevState* st, cudaStream_t s, KernelTimer* T = nullptr);
 void launch_begin_step(DevState* st, double cfl, double dt_fixed, double t_end, double* dts, int idx, cudaStream_t s,
                        KernelTimer* T = nullptr);

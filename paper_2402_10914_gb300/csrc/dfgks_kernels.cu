@@ -29,12 +29,20 @@ __global__ void k_ghost_y(Mesh m, double* W, double* alpha, const int* halt) {
     ghost_y_body(m, W, alpha, blockIdx.x * blockDim.x + threadIdx.x - G, blockIdx.y);
 }
 
+void launch_ghost_pass(int dir, const Mesh& m, double* W, double* alpha, const int* halt, cudaStream_t s) {
+    if (dir == 0) {
+        dim3 bx(2 * G, 32), gx((m.ny + 31) / 32);
+        k_ghost_x<<<gx, bx, 0, s>>>(m, W, alpha, halt);
+    } else {
+        dim3 by(128), gy((m.nx + 2 * G + 127) / 128, 2 * G);
+        k_ghost_y<<<gy, by, 0, s>>>(m, W, alpha, halt);
+    }
+}
+
 void launch_fill_ghosts(const Mesh& m, double* W, double* alpha, const int* halt, cudaStream_t s, KernelTimer* T) {
     if (T) T->begin(KK_OTHER);
-    dim3 bx(2 * G, 32), gx((m.ny + 31) / 32);
-    k_ghost_x<<<gx, bx, 0, s>>>(m, W, alpha, halt);
-    dim3 by(128), gy((m.nx + 2 * G + 127) / 128, 2 * G);
-    k_ghost_y<<<gy, by, 0, s>>>(m, W, alpha, halt);
+    launch_ghost_pass(0, m, W, alpha, halt, s);
+    launch_ghost_pass(1, m, W, alpha, halt, s);
     if (T) T->end(KK_OTHER, 2);
 }
 

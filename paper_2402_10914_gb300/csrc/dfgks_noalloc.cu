@@ -81,6 +81,7 @@ extern "C" DFGKS_API dfgks_status dfgks_residual_noalloc(const dfgks_config* cfg
     m.dy = (cfg->y1 - cfg->y0) / cfg->ny;
     m.bc[0] = cfg->bc_xlo; m.bc[1] = cfg->bc_xhi; m.bc[2] = cfg->bc_ylo; m.bc[3] = cfg->bc_yhi;
     m.dt_rule = cfg->dt_rule;
+    m.gi0 = 0; m.gj0 = 0; m.gnx = cfg->nx;
     SchemeConsts S;
     memset(&S, 0, sizeof(S));
     S.gamma = cfg->gamma; S.gm1 = cfg->gamma - 1.0; S.K = (4.0 - 2.0 * cfg->gamma) / (cfg->gamma - 1.0);

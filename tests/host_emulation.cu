@@ -37,6 +37,7 @@ int main(int argc, char** argv) {
     m.nx = in.nx; m.ny = in.ny; m.P = (in.nx + 2 * G + 3) & ~3; m.NYg = in.ny + 2 * G; m.plane = (long long)m.P * m.NYg;
     m.dx = (in.x1 - in.x0) / in.nx; m.dy = (in.y1 - in.y0) / in.ny;
     for (int q = 0; q < 4; ++q) m.bc[q] = in.bc[q];
+    m.dt_rule = 0; m.gi0 = 0; m.gj0 = 0; m.gnx = in.nx;
     SchemeConsts S;
     S.gamma = in.gamma; S.gm1 = in.gamma - 1.0; S.K = (4.0 - 2.0 * in.gamma) / (in.gamma - 1.0); S.inv_K2 = 1.0 / (S.K + 2.0);
     S.d[3] = in.dH; S.d[0] = (1.0 - in.dH) * (1.0 - in.dL) / 2.0; S.d[1] = (1.0 - in.dH) * in.dL; S.d[2] = S.d[0];
