@@ -45,18 +45,29 @@ def workload_name(n: int) -> str:
 # x 2070 MHz maximum SM clock = 1258.6 GFLOP/s (the recipe's nominal 1.25 TFLOP/s FP64 rate).
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
 
-# FP64 flops the Gauss-point flux kernel executes per Gauss point (GKS): ncu instruction counts
-# 2*DFMA + DADD + DMUL of one launch divided by its 2*(n+1)*n Gauss points
-# (profiles/k_flux_gks_fp64_counts_quadrants128.md).  Valid for the kernel source it was measured on.
-FLUX_GKS_FLOPS_PER_GP = 1773.0
-# FP64-pipe thread instructions (DFMA + DADD + DMUL) per Gauss point from the same capture.  Each
-# occupies one issue slot of the FP64 units whether it does 2 flops (DFMA) or 1, so the issue rate
-# against 152 SM x 2 per clock x 2.07 GHz says how busy the pipe the kernel is bound by is.
-FLUX_GKS_FP64_INST_PER_GP = 1130.0
-# DRAM bytes (read + write) per launch of that kernel on the 400 x 400 workload, mean of the x and
-# y launches of one ncu capture (profiles/k_flux_gks_traffic_quadrants400.md); None once the kernel
-# has changed since the capture, and not reported for other mesh sizes.
-FLUX_GKS_TRAFFIC_BYTES = 64.27e6
+# Per-unit counts of the Gauss-point flux kernel (FP64 flops = 2*DFMA + DADD + DMUL per Gauss point,
+# FP64-pipe instructions per Gauss point, DRAM bytes per launch at 400 x 400) are read from the
+# machine-readable line of the committed ncu summary of that kernel, which also records a hash of
+# the kernel sources it was measured on; the counts are used only while that hash matches.
+FLUX_PROFILE = os.path.join(ROOT, "profiles", "k_flux_gks_counts.md")
+
+
+def profile_counts(path: str = FLUX_PROFILE):
+    """(counts, reason): the machine-readable `counts:` line of a kernel's ncu summary, a JSON object
+    with flops_per_unit, fp64_inst_per_unit, traffic_bytes_per_launch (at the benchmark size) and
+    source_hash; counts is None with the reason when the file or line is missing or the forward
+    kernels' sources have changed since the capture."""
+    from paper_2402_10914_gb300 import build
+    try:
+        lines = [l for l in open(path) if l.startswith("counts:")]
+    except OSError:
+        return None, "no profile summary"
+    if not lines:
+        return None, "no counts line in the profile summary"
+    c = json.loads(lines[-1][len("counts:"):])
+    if c.get("source_hash") != build.kernel_source_hash():
+        return None, "kernel sources changed since the ncu capture"
+    return c, None
 # steps of the oracle's timed sample (about 0.9 s each at 400 x 400 on 16 Arm cores)
 CPU_SAMPLE_STEPS = 12
 
@@ -78,6 +89,7 @@ def parse():
     p.add_argument("--blast-n", type=int, default=2048, help="mesh side of the blast workload")
     p.add_argument("--blast-t", type=float, default=0.01, help="end time of the blast workload")
     p.add_argument("--no-adjoint", action="store_true", help="leave the adjoint summary out of the default line")
+    p.add_argument("--no-batch", action="store_true", help="leave the 64-problem batch summary out of the default line")
     p.add_argument("--adj-n", type=int, default=256, help="mesh side of the adjoint workload")
     p.add_argument("--adj-steps", type=int, default=100, help="S2O4 steps of the adjoint workload")
     p.add_argument("--no-e2e", action="store_true")
@@ -219,23 +231,26 @@ def bench_ours(args, ws, rank, local):
     fl = timing["flux"]
     avg_flux_ms = fl["ms"] / max(fl["timed"], 1)
     gps_per_launch = 2.0 * (s.nx + 1) * s.ny       # x- and y-sweeps have the same count on a square mesh
-    traffic = FLUX_GKS_TRAFFIC_BYTES if args.n == BENCH_N else None
+    counts, why = profile_counts()
+    traffic = counts.get("traffic_bytes_per_launch") if counts and args.n == BENCH_N else None
     roof = {"kernel": "k_flux<GKS> (Gauss-point flux)", "bound": "alu", "unit": "GFLOP/s",
             "peak": round(FP64_PEAK_GFLOPS, 1), "peak_source": "derived: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz",
             "avg_launch_ms": avg_flux_ms, "launches_timed": fl["timed"], "traffic": traffic,
             "traffic_unit": "B per launch (ncu dram read+write)",
             "kernel_time_share": {k: round(v / max(sum(share.values()), 1e-30), 4) for k, v in share.items()},
-            "dominant_kernel_class": dominant}
-    if FLUX_GKS_FLOPS_PER_GP is not None:
-        achieved = FLUX_GKS_FLOPS_PER_GP * gps_per_launch / (avg_flux_ms * 1e-3) / 1e9
+            "dominant_kernel_class": dominant,
+            "counts_source": os.path.relpath(FLUX_PROFILE, ROOT) if counts else why}
+    if counts:
+        fpu = float(counts["flops_per_unit"])
+        achieved = fpu * gps_per_launch / (avg_flux_ms * 1e-3) / 1e9
         roof.update({"achieved": round(achieved, 2), "frac": round(achieved / FP64_PEAK_GFLOPS, 4),
-                     "flops_per_unit": FLUX_GKS_FLOPS_PER_GP, "unit_of_work": "Gauss point",
+                     "flops_per_unit": fpu, "unit_of_work": "Gauss point",
                      "units_per_launch": gps_per_launch})
-        if FLUX_GKS_FP64_INST_PER_GP is not None:
-            issue = FLUX_GKS_FP64_INST_PER_GP * gps_per_launch / (avg_flux_ms * 1e-3)
+        if counts.get("fp64_inst_per_unit"):
+            issue = float(counts["fp64_inst_per_unit"]) * gps_per_launch / (avg_flux_ms * 1e-3)
             roof["fp64_issue_frac"] = round(issue / (FP64_PEAK_GFLOPS / 2.0 * 1e9), 4)
-    if traffic is not None:
-        roof["dram_gbs"] = round(traffic / (avg_flux_ms * 1e-3) / 1e9, 1)
+        if traffic is not None:
+            roof["dram_gbs"] = round(traffic / (avg_flux_ms * 1e-3) / 1e9, 1)
     else:
         roof.update({"achieved": None, "frac": None})
     # FP64 probe as a cross-check of the denominator
@@ -279,75 +294,101 @@ def bench_ours(args, ws, rank, local):
     }
 
 
-def bench_batch(args):
-    """The 64-problem uneven batch (sides 64..512, mixed GKS / L-F, own dt each): one launch per
-    phase over all problems replayed from a CUDA graph, against per-problem launches of the same
-    kernels one problem after another on one stream.  Both advance every problem K steps."""
+BATCH_STEPS = 200       # S2O4 steps of the 64-problem batch
+
+
+def batch_summary(steps: int = BATCH_STEPS, warmup: int = 3, cpu: bool = True) -> dict:
+    """The 64-problem uneven batch (sides 64..512, mixed GKS / L-F, own dt each), advanced `steps`
+    S2O4 steps by one launch of a CUDA graph holding all of them, against per-problem launches of
+    the single-problem kernels one problem after another on one stream.  Both are timed with CUDA
+    events on the stream they run on, after `warmup` untimed steps and a 256 MiB L2 flush, with
+    nvidia-smi clocks sampled during both timed regions.  A problem that loses positivity stops at
+    its last good step in both paths; only completed cell-stages count."""
     import torch
-    from paper_2402_10914_gb300 import inputs as I
+    from paper_2402_10914_gb300 import _lib, inputs as I
     from paper_2402_10914_gb300.solver import BatchSolver, Solver
     ws = I.batch()
     cells = sum(w.settings.nx * w.settings.ny for w in ws)
-    units = 2.0 * cells * args.steps
     flush = torch.empty(32 * 1024 * 1024, dtype=torch.float64, device="cuda")
-    b = BatchSolver([w.settings for w in ws])
+    stream = torch.cuda.Stream()
+    b = BatchSolver([w.settings for w in ws], stream=stream)
     for p, w in enumerate(ws):
         b.set_ic(p, w.W0)
-    shapes, _ = b.autotune()
-    from paper_2402_10914_gb300 import _lib
-    b.step(args.warmup, use_graph=True)
+    blocks, _ = b.autotune()
+    b.step(warmup, use_graph=True)
+    b.prepare(steps)                                    # capture the steps-long graph, untimed
     before = [b.status(p)["step"] for p in range(len(ws))]
+    clocks = ClockSampler(torch.cuda.current_device())
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
     flush.fill_(1.0)
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    rc = b.step(args.steps, use_graph=True)
+    clocks.start()
+    e0.record(stream)
+    rc = b.step(steps, use_graph=True)                  # one graph launch
+    e1.record(stream)
     torch.cuda.synchronize()
-    t_batch = time.perf_counter() - t0
+    clk_b = clocks.stop()
+    t_batch = e0.elapsed_time(e1) * 1e-3
     done_batch = [b.status(p)["step"] - before[p] for p in range(len(ws))]
     failed = [p for p in range(len(ws)) if b.status(p)["err"]]
     b.close()
-    # a problem that loses positivity stops at its last good step in both paths; count the
-    # cell-stages actually completed
     units = sum(2.0 * w.settings.nx * w.settings.ny * d for w, d in zip(ws, done_batch))
-    sols = [Solver(w.settings) for w in ws]
-    for s, w in zip(sols, ws):
-        s.set_ic(w.W0)
+    sols = [Solver(w.settings, stream=stream) for w in ws]
+    for sol, w in zip(sols, ws):
+        sol.set_ic(w.W0)
         try:
-            s.step(args.warmup)
+            sol.step(warmup)
         except _lib.DfgksError:
             pass
+    before_seq = [sol.get_state()[3] for sol in sols]
+    clocks = ClockSampler(torch.cuda.current_device())
+    torch.cuda.synchronize()
     flush.fill_(2.0)
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    done_seq = []
-    for s in sols:
+    clocks.start()
+    e0.record(stream)
+    for sol in sols:
         try:
-            d, _ = s.step(args.steps)
+            sol.step(steps)
         except _lib.DfgksError:
-            d = -1
-        done_seq.append(d)
+            pass
+    e1.record(stream)
     torch.cuda.synchronize()
-    t_seq = time.perf_counter() - t0
-    done_seq = [s.get_state()[3] - args.warmup if d < 0 else d for s, d in zip(sols, done_seq)]
-    units_seq = sum(2.0 * w.settings.nx * w.settings.ny * max(d, 0) for w, d in zip(ws, done_seq))
-    for s in sols:
-        s.close()
-    line = {"metric": "FP64 cell-stage updates/s (64-problem uneven batch, mixed GKS/L-F)", "value": units / t_batch,
-            "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": t_batch / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "batch64_uneven_seed1000", "problems": len(ws), "cells": cells,
-                       "sides": sorted(set(w.settings.nx for w in ws)), "shapes": shapes, "status": rc,
-                       "problems_lost_positivity": failed, "l2": "one 256 MiB flush before each timed region"},
-            "per_problem_sequential": {"value": units_seq / t_seq, "ms_per_step": t_seq / args.steps * 1e3},
-            "speedup_vs_per_problem": (units / t_batch) / (units_seq / t_seq),
-            "timing": "host clock around each call, which returns after a device synchronisation (the batch "
-                      "runs on the handle's private stream, where its graph is captured)"}
-    if not args.no_cpu:
+    clk_s = clocks.stop()
+    t_seq = e0.elapsed_time(e1) * 1e-3
+    done_seq = [sol.get_state()[3] - b0 for sol, b0 in zip(sols, before_seq)]
+    units_seq = sum(2.0 * w.settings.nx * w.settings.ny * d for w, d in zip(ws, done_seq))
+    for sol in sols:
+        sol.close()
+    out = {"workload": "batch64_uneven_seed1000_%dsteps" % steps, "problems": len(ws), "cells": cells,
+           "steps": steps, "warmup": warmup, "value": units / t_batch, "unit": UNIT, "ms": t_batch * 1e3,
+           "graph_launches": 1, "kernel_launches_in_graph": 21 * steps, "blocks": blocks, "status": rc,
+           "problems_lost_positivity": failed, "cell_stages": units,
+           "per_problem_sequential": {"value": units_seq / t_seq, "ms": t_seq * 1e3, "cell_stages": units_seq},
+           "speedup_vs_per_problem": (units / t_batch) / (units_seq / t_seq),
+           "clocks": clk_b, "clocks_per_problem": clk_s,
+           "timing": "CUDA events on the stream both paths run on; 256 MiB L2 flush before each timed region"}
+    if cpu:
         try:
-            line["cpu_baseline"] = oracle_batch_sample(ws[:16])
+            out["cpu_baseline"] = oracle_batch_sample(ws[:16])
         except Exception as e:
-            line["cpu_baseline"] = {"value": None, "kind": "oracle", "sample": "failed: %s" % e}
+            out["cpu_baseline"] = {"value": None, "kind": "oracle", "sample": "failed: %s" % e}
+    return out
+
+
+def bench_batch(args):
+    """--workload batch: the batch summary as its own line (steps = --steps, default 200)."""
+    steps = args.steps if args.steps != 40 else BATCH_STEPS
+    r = batch_summary(steps, max(args.warmup, 3), cpu=not args.no_cpu)
+    line = {"metric": "FP64 cell-stage updates/s (64-problem uneven batch, mixed GKS/L-F)", "value": r["value"],
+            "unit": UNIT, "n_gpus": 1, "steps": steps, "warmup": r["warmup"], "ms_per_step": r["ms"] / steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": r["workload"], "problems": r["problems"], "cells": r["cells"],
+                       "blocks": r["blocks"], "l2": "one 256 MiB flush before each timed region"},
+            "batch": r, "clocks": r["clocks"], "gpu_launches": r["kernel_launches_in_graph"]}
+    if "cpu_baseline" in r:
+        line["cpu_baseline"] = r["cpu_baseline"]
     print(json.dumps(line))
 
 
@@ -413,8 +454,9 @@ def bench_blast(args):
 def bench_robustness(args):
     """Sect. 4.3 robustness measure: the largest Mach number at which a run keeps positivity, for
     the hybrid (DF + WENO-AO) and the plain WENO-AO reconstruction (alpha_thres = 0: the DF branch
-    never fires), GKS (S2O4) and L-F (SSP-RK3), with and without the Gauss-point fallback.  Found by
-    bisection in log Mach between 1 and 256 (12 halvings)."""
+    never fires), GKS (S2O4) and L-F (SSP-RK3), with and without the Gauss-point fallback, on the
+    123 problem, the hurricane-like flow and the planar rarefactions (Tables 3-5).  Found by
+    bisection in log Mach between 1 and 256 (12 halvings; the planar rarefactions from 0.5)."""
     import torch
     from paper_2402_10914_gb300 import _lib, inputs as I
     from paper_2402_10914_gb300.solver import Solver
@@ -437,13 +479,14 @@ def bench_robustness(args):
     t0 = time.perf_counter()
     rows = []
     for name, make in (("123 problem (100 cells, t = 0.14)", I.problem_123),
-                       ("hurricane-like (400 x 400, 50 steps)", I.hurricane)):
+                       ("hurricane-like (400 x 400, 50 steps)", I.hurricane),
+                       ("planar rarefactions (400 x 400, t = 0.15)", I.planar_rarefaction)):
         for flux, fname in ((I.GKS, "GKS S2O4"), (I.LF, "L-F SSP-RK3")):
             for thres, rname in ((0.5, "hybrid"), (0.0, "WENO-AO")):
                 for fb in (0, 1):
-                    lo, hi = 1.0, 256.0
+                    lo, hi = (0.5 if make is I.planar_rarefaction else 1.0), 256.0
                     if not survives(make, lo, flux, thres, fb):
-                        res = "< 1"
+                        res = "< %g" % lo
                     elif survives(make, hi, flux, thres, fb):
                         res = ">= 256"
                     else:
@@ -460,7 +503,7 @@ def bench_robustness(args):
     torch.cuda.synchronize()
     line = {"metric": "maximum Mach number keeping positivity (Sect. 4.3 robustness measure)", "value": None,
             "unit": "Mach", "n_gpus": 1, "steps": None, "warmup": 0, "higher_is_better": True,
-            "dtype": "f64", "data": "synthetic", "config": {"workload": "robustness_123_hurricane"},
+            "dtype": "f64", "data": "synthetic", "config": {"workload": "robustness_123_hurricane_planar_rarefaction"},
             "robustness": rows, "wall_s": time.perf_counter() - t0}
     print(json.dumps(line))
 
@@ -599,6 +642,45 @@ def oracle_adjoint_sample(n=32, steps=1):
             "forward_s": t_fwd, "gradient_s": t_grad, "gradient_over_forward": t_grad / t_fwd}
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the platform string)."""
+    import platform
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for l in out.splitlines():
+            if l.split(":")[0].strip() in ("Model name", "Model"):
+                name = l.split(":", 1)[1].strip()
+                if name and not name.isdigit():
+                    return name
+    except Exception:
+        pass
+    try:
+        for l in open("/proc/cpuinfo"):
+            if l.lower().startswith(("model name", "cpu model")):
+                return l.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return platform.processor() or platform.machine()
+
+
+def oracle_cpu_baseline(n: int = 400, steps_all: int = CPU_SAMPLE_STEPS) -> dict:
+    """The oracle as it stands on bounded samples of the benchmark workload: the first `steps_all`
+    S2O4 steps on every host core, and the first step on one core."""
+    import oracle
+    nproc = oracle.max_threads()
+    v, cores, dtw = oracle_sample(steps=steps_all, n=n)
+    try:
+        v1, _, dt1 = oracle_sample(n_threads=1, steps=1, n=n)
+    finally:
+        oracle.set_threads(nproc)
+    return {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu_model": cpu_model(),
+            "sample": "sample: the first %d S2O4 steps of the %dx%d workload on %d threads (%.1f s)"
+                      % (steps_all, n, n, cores, dtw),
+            "single_thread": {"value": v1, "unit": UNIT, "cores": 1,
+                              "sample": "sample: the first S2O4 step of the %dx%d workload on one thread (%.1f s)"
+                                        % (n, n, dt1)}}
+
+
 def oracle_sample(n_threads=None, steps=1, n=400):
     """The CPU oracle as it stands on one full S2O4 step of the same workload."""
     import oracle
@@ -684,10 +766,7 @@ def main():
     cpu = None
     if not args.no_cpu:
         try:
-            k = CPU_SAMPLE_STEPS
-            v, cores, dtw = oracle_sample(steps=k, n=args.n)
-            cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                   "sample": "the first %d S2O4 steps of the %dx%d workload (%.1f s)" % (k, args.n, args.n, dtw)}
+            cpu = oracle_cpu_baseline(args.n)
         except Exception as e:  # the benchmark line must still be printed
             cpu = {"value": None, "unit": UNIT, "cores": None, "kind": "oracle", "sample": "failed: %s" % e}
     line = {
@@ -700,6 +779,11 @@ def main():
         "roofline": r["roofline"], "cpu_baseline": cpu, "e2e": r["e2e"], "gpu_launches": r["launches"],
         "clocks": r["clocks"], "per_kernel_ms_per_step": r["per_kernel_ms_per_step"], "counters": r["counters"],
     }
+    if not args.no_batch and ws == 1:
+        try:
+            line["batch"] = batch_summary(BATCH_STEPS, 3, cpu=not args.no_cpu)
+        except Exception as e:  # the benchmark line must still be printed
+            line["batch"] = {"workload": "batch64_uneven_seed1000_%dsteps" % BATCH_STEPS, "value": None, "error": str(e)}
     if not args.no_adjoint and ws == 1:
         try:
             line["adjoint"] = bench_adjoint(1, 1)

@@ -190,11 +190,12 @@ DFGKS_API dfgks_status dfgks_adjoint_steps(dfgks* h, const double* W0, int n, co
 
 /* ---- Batched problems ----------------------------------------------------------------------
  * Many independent problems (each its own mesh size, boundary conditions, flux solver and CFL dt)
- * advanced together: every phase of a step is one launch over all problems, and the step's launch
- * sequence can be captured once in a CUDA graph and replayed.  Not part of the paper (a throughput
- * mode for many small problems on one GPU).  S2O4 only (time_scheme 0).  Each problem's state,
- * alpha, dt, time and step counter are its own; a problem that loses positivity stops at its last
- * good step while the others continue. */
+ * advanced together: every phase of a step is one launch over all problems, the sweep kernels on
+ * 1-D blocks of an autotuned size over each problem's face lines, face sides and Gauss points, and
+ * n steps are captured once in a CUDA graph that one launch replays.  Not part of the paper (a
+ * throughput mode for many small problems on one GPU).  S2O4 only (time_scheme 0).  Each problem's
+ * state, alpha, dt, time and step counter are its own; a problem that loses positivity stops at
+ * its last good step while the others continue. */
 typedef struct dfgks_batch dfgks_batch;
 
 /* cfgs[np], flux[np] (dfgks_flux); stream NULL creates a private stream (graph capture needs a
@@ -204,19 +205,69 @@ DFGKS_API dfgks_status dfgks_batch_create(const dfgks_config* cfgs, const int* f
 DFGKS_API dfgks_status dfgks_batch_destroy(dfgks_batch* b);
 /* Initial state of problem p (host if on_device == 0); alpha^0 as in dfgks_set_ic; ENONPHYS on bad data. */
 DFGKS_API dfgks_status dfgks_batch_set_ic(dfgks_batch* b, int p, const double* W, int on_device);
-/* Advance every problem n steps; use_graph != 0 replays a captured CUDA graph of one step.
+/* Capture the CUDA graph that advances every problem n steps (1 <= n <= 100000); dfgks_batch_step
+ * does this on first use of an n, so calling it ahead keeps the capture out of a timed region.
+ * The graph is dropped when the block sizes change. */
+DFGKS_API dfgks_status dfgks_batch_prepare(dfgks_batch* b, int n);
+/* Advance every problem n steps; use_graph != 0: one launch of the n-step graph, otherwise the
+ * same launches issued one by one.  Synchronises the batch's stream at the end.
  * Returns DFGKS_ENONPOS if any problem lost positivity (see dfgks_batch_status). */
 DFGKS_API dfgks_status dfgks_batch_step(dfgks_batch* b, int n, int use_graph);
 DFGKS_API dfgks_status dfgks_batch_get_state(dfgks_batch* b, int p, double* W, double* alpha, double* t, long* step,
                                              int on_device);
 /* Step count, error flag (0 or DFGKS_ENONPOS) and normal DF-branch count of problem p. */
 DFGKS_API dfgks_status dfgks_batch_status(dfgks_batch* b, int p, long* step, int* err, unsigned long long* df_normal);
-/* Block shapes (bx, by), bx*by = 128, bx a multiple of 32, of the face-line, tangential and flux kernels. */
-DFGKS_API dfgks_status dfgks_batch_set_shapes(dfgks_batch* b, const int* shapes6);
-/* Pick those shapes by timing one batched step per candidate (32x4, 64x2, 128x1), kernel class by
- * class; states are saved and restored around the trials.  shapes6 (may be NULL) receives the
- * choice, best_ms (may be NULL) the last class's best step time. */
-DFGKS_API dfgks_status dfgks_batch_autotune(dfgks_batch* b, int* shapes6, double* best_ms);
+/* Threads per block (64, 128 or 256) of the face-line, tangential and flux kernels. */
+DFGKS_API dfgks_status dfgks_batch_set_blocks(dfgks_batch* b, const int* blocks3);
+/* Pick those sizes by timing one batched step per candidate (64, 128, 256), kernel class by class;
+ * states are saved and restored around the trials.  blocks3 (may be NULL) receives the choice,
+ * best_ms (may be NULL) the last class's best step time. */
+DFGKS_API dfgks_status dfgks_batch_autotune(dfgks_batch* b, int* blocks3, double* best_ms);
+
+/* ---- One problem in blocks (domain decomposition) -------------------------------------------
+ * The mesh split into px x py rectangular blocks (block b = by * px + bx covers cells
+ * [i0, i1) x [j0, j1), i0 = floor(nx bx / px), likewise in y), each with its own ghosted buffers on
+ * the current device.  Before every stage the ghost layers are filled in two passes over all
+ * blocks: the ghost columns of the interior rows (a shared side by copying the neighbouring
+ * block's G boundary columns), then the ghost rows including the ghost columns (a shared side by
+ * copying the neighbour's G boundary rows, which carries the diagonal neighbour's cells into the
+ * corners); sides on the mesh boundary keep their boundary condition, and a periodic side of a
+ * split direction is shared with the block at the other end.  dt is the minimum over all blocks.
+ * A decomposed run reproduces dfgks_step on the whole mesh bit for bit.  Not part of the paper
+ * (one mesh per case there).  S2O4 only; a split direction needs at least 3 cells per block. */
+typedef struct dfgks_decomp dfgks_decomp;
+/* A block's place in the decomposition: its cells [i0, i1) x [j0, j1) of the whole mesh, per side
+ * (x-low, x-high, y-low, y-high) the boundary condition (dfgks_bc, or 3 for a side filled by a halo
+ * copy) and the neighbouring block the copy comes from (-1 for a boundary side).  Host only. */
+typedef struct dfgks_block_plan { int i0, i1, j0, j1; int bc[4]; int neighbour[4]; } dfgks_block_plan;
+DFGKS_API dfgks_status dfgks_decomp_plan(const dfgks_config* cfg, int px, int py, int block, dfgks_block_plan* out);
+/* The halo copy that fills side `side` (0 x-low, 1 x-high, 2 y-low, 3 y-high) of block `block`:
+ * the neighbouring block it comes from (-1: a boundary side, no copy), the window of this block's
+ * ghosted field it fills (first cell (di, dj) in the block's cell indices, ghosts negative or
+ * >= the block's size; w x h cells) and the first cell (si, sj) of the same-sized window in the
+ * neighbour's field.  x sides are copied in the first pass of the ghost fill, y sides (whose
+ * windows include the ghost columns) in the second.  Host only: a run with one block per device
+ * sends and receives exactly these windows. */
+typedef struct dfgks_halo_window { int neighbour, di, dj, si, sj, w, h; } dfgks_halo_window;
+DFGKS_API dfgks_status dfgks_decomp_halo(const dfgks_config* cfg, int px, int py, int block, int side,
+                                         dfgks_halo_window* out);
+/* Allocate the blocks (stream NULL: a private stream).  EINVAL for configurations the whole-mesh
+ * handle refuses, time_scheme != S2O4, or fewer than 3 cells per block along a split direction. */
+DFGKS_API dfgks_status dfgks_decomp_create(const dfgks_config* cfg, int px, int py, void* stream, dfgks_decomp** out);
+DFGKS_API dfgks_status dfgks_decomp_destroy(dfgks_decomp* d);
+/* Initial state of the whole mesh, dense [4][ny][nx] (host if on_device == 0), scattered to the
+ * blocks; alpha^0 as in dfgks_set_ic; ENONPHYS on a non-physical cell. */
+DFGKS_API dfgks_status dfgks_decomp_set_ic(dfgks_decomp* d, const double* W, int on_device);
+/* n S2O4 steps with the CFL dt, the last clipped to t_end > 0; synchronises once at the end.
+ * ENONPOS on a positivity failure, the state left at the last good step. */
+DFGKS_API dfgks_status dfgks_decomp_step(dfgks_decomp* d, int n, int flux, double t_end, int* steps_done);
+/* The whole mesh's state gathered from the blocks: W [4][ny][nx], alpha [ny][nx] (either may be
+ * NULL; host memory if on_device == 0), time and step count. */
+DFGKS_API dfgks_status dfgks_decomp_get_state(dfgks_decomp* d, double* W, double* alpha, double* t, long* step,
+                                              int on_device);
+/* Error flag (0 or DFGKS_ENONPOS), the first failing cell (whole-mesh indices, -1 if none) and the
+ * branch counters summed over the blocks.  Any pointer may be NULL. */
+DFGKS_API dfgks_status dfgks_decomp_status(dfgks_decomp* d, int* err, int* fail_i, int* fail_j, dfgks_counters* counters);
 
 /* Per-face intermediates of one stage, for diagnostics and kernel-by-kernel comparison.
  * dir 0: x-faces, [ny][nx+1] (face index fastest); dir 1: y-faces, [nx][ny+1].

@@ -30,6 +30,19 @@ class Counters(C.Structure):
     _fields_ = [("fallbacks", C.c_ulonglong), ("df_normal", C.c_ulonglong), ("df_tangential", C.c_ulonglong)]
 
 
+class BlockPlan(C.Structure):
+    _fields_ = [("i0", C.c_int), ("i1", C.c_int), ("j0", C.c_int), ("j1", C.c_int),
+                ("bc", C.c_int * 4), ("neighbour", C.c_int * 4)]
+
+
+class HaloWindow(C.Structure):
+    _fields_ = [("neighbour", C.c_int), ("di", C.c_int), ("dj", C.c_int), ("si", C.c_int), ("sj", C.c_int),
+                ("w", C.c_int), ("h", C.c_int)]
+
+
+BC_EXTERNAL = 3      # a block side whose ghost layers a halo copy fills
+
+
 class DfgksError(RuntimeError):
     def __init__(self, status: int, where: str):
         self.status = status
@@ -66,11 +79,20 @@ SIGNATURES = {
     "dfgks_batch_step": [_V, C.c_int, C.c_int],
     "dfgks_batch_get_state": [_V, C.c_int, _V, _V, _D, C.POINTER(C.c_long), C.c_int],
     "dfgks_batch_status": [_V, C.c_int, C.POINTER(C.c_long), C.POINTER(C.c_int), C.POINTER(C.c_ulonglong)],
-    "dfgks_batch_set_shapes": [_V, _V],
+    "dfgks_batch_set_blocks": [_V, _V],
+    "dfgks_batch_prepare": [_V, C.c_int],
     "dfgks_batch_autotune": [_V, _V, _D],
     "dfgks_adjoint_steps": [_V, _V, C.c_int, _D, C.c_int, C.c_int, _V, _V],
     "dfgks_forward_checkpointed": [_V, _V, C.c_int, _D, C.c_int, C.c_int, _D],
     "dfgks_adjoint_checkpointed": [_V, _V, _V],
+    "dfgks_decomp_plan": [C.POINTER(Config), C.c_int, C.c_int, C.c_int, C.POINTER(BlockPlan)],
+    "dfgks_decomp_halo": [C.POINTER(Config), C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(HaloWindow)],
+    "dfgks_decomp_create": [C.POINTER(Config), C.c_int, C.c_int, _V, C.POINTER(_V)],
+    "dfgks_decomp_destroy": [_V],
+    "dfgks_decomp_set_ic": [_V, _V, C.c_int],
+    "dfgks_decomp_step": [_V, C.c_int, C.c_int, C.c_double, C.POINTER(C.c_int)],
+    "dfgks_decomp_get_state": [_V, _V, _V, _D, C.POINTER(C.c_long), C.c_int],
+    "dfgks_decomp_status": [_V, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(Counters)],
 }
 
 

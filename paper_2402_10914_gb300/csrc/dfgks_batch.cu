@@ -4,9 +4,11 @@
 // stage update, bookkeeping) is one launch over all problems: each thread block looks its problem
 // up in a prefix table of per-problem block counts and runs the same per-thread body as the
 // single-problem kernels (dfgks_bodies.cuh), so small meshes fill the GPU together instead of
-// one after another.  Each problem keeps its own device-resident dt, time, halt flag and state
-// buffer parity, so one step is the same launch sequence for every step: it is captured once in
-// a CUDA graph and replayed.  The block shape of the sweep kernels is chosen by an autotuner.
+// one after another.  The sweep kernels use 1-D blocks over each problem's row-major index space
+// (face lines, face sides, Gauss points), so only a problem's last warp is partly idle; their
+// block size is chosen by an autotuner.  Each problem keeps its own device-resident dt, time, halt
+// flag and state buffer parity, so every step is the same launch sequence: n steps are captured
+// once in a CUDA graph and one graph launch advances all problems n steps.
 #include <cuda_runtime.h>
 #include <float.h>
 #include <string.h>
@@ -32,56 +34,77 @@ struct BatchProblem {
     DevState* st;
 };
 
-// Phases with a per-problem block grid.  For the sweep kernels the block shape (bx x by, 128
-// threads) is tunable; the grid of a problem follows from its mesh and that shape.
+// Phases with a per-problem block grid.  The sweep phases run 1-D blocks of a tunable size over a
+// problem's index space (lx x ly items, row-major; the face and flux phases twice, once per side /
+// Gauss point); the others have fixed shapes.
 enum Phase { PH_GX = 0, PH_GY, PH_CFL, PH_LINES0, PH_LINES1, PH_FACES0, PH_FACES1, PH_FLUX0, PH_FLUX1, PH_UPD,
              PH_COUNT };
 
-struct Shape { int bx, by; };
-
-__host__ __device__ inline void phase_grid(int ph, const Mesh& m, Shape sh, int& gx, int& gy, int& gz) {
-    gz = 1;
+__host__ __device__ inline void sweep_space(int ph, const Mesh& m, int& lx, int& ly, int& nz) {
+    nz = 1;
     switch (ph) {
-        case PH_GX: gx = (m.ny + 31) / 32; gy = 1; break;
-        case PH_GY: gx = (m.nx + 2 * G + 127) / 128; gy = 2 * G; break;
-        case PH_CFL: gx = (m.nx * m.ny + 255) / 256; gy = 1; break;
-        case PH_LINES0: gx = (m.nx + 1 + sh.bx - 1) / sh.bx; gy = (m.ny + 4 + sh.by - 1) / sh.by; break;
-        case PH_LINES1: gx = (m.nx + 4 + sh.bx - 1) / sh.bx; gy = (m.ny + 1 + sh.by - 1) / sh.by; break;
-        case PH_FACES0: case PH_FLUX0: gx = (m.nx + 1 + sh.bx - 1) / sh.bx; gy = (m.ny + sh.by - 1) / sh.by; gz = 2; break;
-        case PH_FACES1: case PH_FLUX1: gx = (m.nx + sh.bx - 1) / sh.bx; gy = (m.ny + 1 + sh.by - 1) / sh.by; gz = 2; break;
-        default: gx = (m.nx + 31) / 32; gy = (m.ny + 7) / 8; break;   // PH_UPD, 32 x 8
+        case PH_LINES0: lx = lines_lx<0>(m); ly = lines_ly<0>(m); break;
+        case PH_LINES1: lx = lines_lx<1>(m); ly = lines_ly<1>(m); break;
+        case PH_FACES0: case PH_FLUX0: lx = faces_lx<0>(m); ly = faces_ly<0>(m); nz = 2; break;
+        default: lx = faces_lx<1>(m); ly = faces_ly<1>(m); nz = 2; break;   // PH_FACES1, PH_FLUX1
+    }
+}
+
+__host__ __device__ inline bool is_sweep(int ph) { return ph >= PH_LINES0 && ph <= PH_FLUX1; }
+
+// blocks of one problem in phase ph (bs: threads per block of a sweep phase); for a sweep phase
+// also the blocks per side, per_z
+__host__ __device__ inline int phase_blocks(int ph, const Mesh& m, int bs, int& per_z) {
+    per_z = 0;
+    switch (ph) {
+        case PH_GX: return (m.ny + 31) / 32;
+        case PH_GY: return ((m.nx + 2 * G + 127) / 128) * 2 * G;
+        case PH_CFL: return (m.nx * m.ny + 255) / 256;
+        case PH_UPD: return ((m.nx + 31) / 32) * ((m.ny + 7) / 8);
+        default: {
+            int lx, ly, nz;
+            sweep_space(ph, m, lx, ly, nz);
+            per_z = (int)(((long long)lx * ly + bs - 1) / bs);
+            return per_z * nz;
+        }
     }
 }
 
 struct BlockMap {
     const int* start;     // device: np + 1 prefix of block counts
     int np;
-    Shape sh;
+    int bs;               // threads per block of a sweep phase
 };
 
-// problem of this block and the block's (bx, by, bz) inside that problem's grid
-__device__ __forceinline__ int locate(const BlockMap& bm, int ph, const BatchProblem* P, int& bx, int& by, int& bz) {
+// problem of this block and the block's index inside that problem's part of the grid
+__device__ __forceinline__ int locate(const BlockMap& bm, int& local) {
     int lo = 0, hi = bm.np;                 // start[lo] <= blockIdx.x < start[hi]
     const int b = blockIdx.x;
     while (hi - lo > 1) {
         int mid = (lo + hi) >> 1;
         if (bm.start[mid] <= b) lo = mid; else hi = mid;
     }
-    int gx, gy, gz;
-    phase_grid(ph, P[lo].m, bm.sh, gx, gy, gz);
-    int local = b - bm.start[lo];
-    bx = local % gx;
-    by = (local / gx) % gy;
-    bz = local / (gx * gy);
+    local = b - bm.start[lo];
     return lo;
 }
 
+// item (ax, ay) and side / Gauss point z of this thread in sweep phase ph
+__device__ __forceinline__ void sweep_item(int ph, const Mesh& m, int local, int& ax, int& ay, int& z) {
+    int lx, ly, nz;
+    sweep_space(ph, m, lx, ly, nz);
+    const int per_z = (int)(((long long)lx * ly + blockDim.x - 1) / blockDim.x);
+    z = local / per_z;
+    const long long i = (long long)(local - z * per_z) * blockDim.x + threadIdx.x;
+    ax = (int)(i % lx);
+    ay = (int)(i / lx);                     // >= ly past the end: rejected by the bodies' bounds checks
+}
+
 __global__ void kb_cfl(const BatchProblem* P, BlockMap bm) {
-    int bx, by, bz;
-    const int p = locate(bm, PH_CFL, P, bx, by, bz);
+    int local;
+    const int p = locate(bm, local);
     const BatchProblem& q = P[p];
     if (q.st->halt) return;
-    const int c = bx * 256 + threadIdx.x;
+    const int c = local * 256 + threadIdx.x;
     double v = c < q.m.nx * q.m.ny ? cfl_cell(q.m, q.W[q.st->par], q.S.gamma, c) : DBL_MAX;
     v = block_min(v);
     if (threadIdx.x == 0 && v > 0.0) atomicMin(&q.st->dtmin_bits, (unsigned long long)__double_as_longlong(v));
@@ -113,8 +136,8 @@ __global__ void kb_end_step(const BatchProblem* P, int np, double t_end) {
 
 // stage 0 reads W^n (and fills alpha^n ghosts), stage 1 reads W*
 __global__ void kb_ghost_x(const BatchProblem* P, BlockMap bm, int stage) {
-    int bx, by, bz;
-    const int p = locate(bm, PH_GX, P, bx, by, bz);
+    int bx;
+    const int p = locate(bm, bx);
     const BatchProblem& q = P[p];
     if (q.st->halt) return;
     double* W = stage == 0 ? q.W[q.st->par] : q.Ws;
@@ -123,9 +146,10 @@ __global__ void kb_ghost_x(const BatchProblem* P, BlockMap bm, int stage) {
 }
 
 __global__ void kb_ghost_y(const BatchProblem* P, BlockMap bm, int stage) {
-    int bx, by, bz;
-    const int p = locate(bm, PH_GY, P, bx, by, bz);
+    int local;
+    const int p = locate(bm, local);
     const BatchProblem& q = P[p];
+    const int gxb = (q.m.nx + 2 * G + 127) / 128, bx = local % gxb, by = local / gxb;
     if (q.st->halt) return;
     double* W = stage == 0 ? q.W[q.st->par] : q.Ws;
     double* A = stage == 0 ? q.A[q.st->par] : nullptr;
@@ -133,53 +157,55 @@ __global__ void kb_ghost_y(const BatchProblem* P, BlockMap bm, int stage) {
 }
 
 template <int DIR>
-__global__ void __launch_bounds__(128) kb_lines(const BatchProblem* P, BlockMap bm, int stage) {
-    int bx, by, bz;
-    const int p = locate(bm, DIR == 0 ? PH_LINES0 : PH_LINES1, P, bx, by, bz);
+__global__ void __launch_bounds__(256) kb_lines(const BatchProblem* P, BlockMap bm, int stage) {
+    int local, ax, ay, z;
+    const int p = locate(bm, local);
     const BatchProblem& q = P[p];
     if (q.st->halt) return;
+    sweep_item(DIR == 0 ? PH_LINES0 : PH_LINES1, q.m, local, ax, ay, z);
     const int par = q.st->par;
     const double* W = stage == 0 ? q.W[par] : q.Ws;
-    int ndf = lines_body<DIR>(q.m, q.S, W, q.A[par], q.B.lines, q.B.line_stride, bx * bm.sh.bx + threadIdx.x,
-                              by * bm.sh.by + threadIdx.y);
+    int ndf = lines_body<DIR>(q.m, q.S, W, q.A[par], q.B.lines, q.B.line_stride, ax, ay);
     warp_count_add(&q.st->df_normal, ndf);
 }
 
 template <int DIR>
-__global__ void __launch_bounds__(128) kb_faces(const BatchProblem* P, BlockMap bm, int stage) {
-    int bx, by, bz;
-    const int p = locate(bm, DIR == 0 ? PH_FACES0 : PH_FACES1, P, bx, by, bz);
+__global__ void __launch_bounds__(256) kb_faces(const BatchProblem* P, BlockMap bm, int stage) {
+    int local, ax, ay, z;
+    const int p = locate(bm, local);
     const BatchProblem& q = P[p];
     if (q.st->halt) return;
+    sweep_item(DIR == 0 ? PH_FACES0 : PH_FACES1, q.m, local, ax, ay, z);
     const int par = q.st->par;
     const double* W = stage == 0 ? q.W[par] : q.Ws;
     int nfb;
     int ndf = faces_body<DIR>(q.m, q.S, W, q.A[par], q.B.lines, q.B.line_stride, q.B.gp, q.B.gp_stride,
-                              bx * bm.sh.bx + threadIdx.x, by * bm.sh.by + threadIdx.y, bz, nfb);
+                              ax, ay, z, nfb);
     warp_count_add(&q.st->df_tangential, ndf);
     warp_count_add(&q.st->fallbacks, nfb);
 }
 
 template <int DIR>
-__global__ void __launch_bounds__(128) kb_flux(const BatchProblem* P, BlockMap bm) {
-    int bx, by, bz;
-    const int p = locate(bm, DIR == 0 ? PH_FLUX0 : PH_FLUX1, P, bx, by, bz);
+__global__ void __launch_bounds__(256) kb_flux(const BatchProblem* P, BlockMap bm) {
+    int local, ax, ay, z;
+    const int p = locate(bm, local);
     const BatchProblem& q = P[p];
     if (q.st->halt) return;
-    const int ax = bx * bm.sh.bx + threadIdx.x, ay = by * bm.sh.by + threadIdx.y;
+    sweep_item(DIR == 0 ? PH_FLUX0 : PH_FLUX1, q.m, local, ax, ay, z);
     if (q.flux == 0)
         flux_body<DIR, 0, false>(q.m, q.S, q.B.lines, q.B.line_stride, q.B.gp, q.B.gp_stride, q.B.flux[DIR],
-                                 q.B.flux_stride[DIR], q.st->dt, ax, ay, bz);
+                                 q.B.flux_stride[DIR], q.st->dt, ax, ay, z);
     else
         flux_body<DIR, 1, false>(q.m, q.S, q.B.lines, q.B.line_stride, q.B.gp, q.B.gp_stride, q.B.flux[DIR],
-                                 q.B.flux_stride[DIR], q.st->dt, ax, ay, bz);
+                                 q.B.flux_stride[DIR], q.st->dt, ax, ay, z);
 }
 
 template <int MODE>
 __global__ void __launch_bounds__(256) kb_update(const BatchProblem* P, BlockMap bm) {
-    int bx, by, bz;
-    const int p = locate(bm, PH_UPD, P, bx, by, bz);
+    int local;
+    const int p = locate(bm, local);
     const BatchProblem& q = P[p];
+    const int gxb = (q.m.nx + 31) / 32, bx = local % gxb, by = local / gxb;
     if (q.st->halt) return;
     const int par = q.st->par;
     UpdateArgs a;
@@ -205,11 +231,12 @@ struct dfgks_batch {
     int* starts;                         // PH_COUNT x (np + 1) prefix tables (device)
     std::vector<int> hstarts;
     int total[PH_COUNT];
-    Shape shape[3];                      // lines, faces, flux
+    int block[3];                        // threads per block: face lines, face sides, Gauss points
     std::vector<void*> allocs;
     unsigned long long bytes;
-    cudaGraphExec_t graph;
+    cudaGraphExec_t graph;               // n_graph steps of every problem
     bool graph_ok;
+    int n_graph;
     double t_end;
 };
 
@@ -220,25 +247,25 @@ static dfgks_status cst(cudaError_t e) {
 
 static long long rup(long long n, long long a) { return (n + a - 1) / a * a; }
 
-static Shape shape_of(const dfgks_batch* b, int ph) {
-    if (ph == PH_LINES0 || ph == PH_LINES1) return b->shape[0];
-    if (ph == PH_FACES0 || ph == PH_FACES1) return b->shape[1];
-    if (ph == PH_FLUX0 || ph == PH_FLUX1) return b->shape[2];
-    return Shape{32, 4};
+static int block_of(const dfgks_batch* b, int ph) {
+    if (ph == PH_LINES0 || ph == PH_LINES1) return b->block[0];
+    if (ph == PH_FACES0 || ph == PH_FACES1) return b->block[1];
+    if (ph == PH_FLUX0 || ph == PH_FLUX1) return b->block[2];
+    return 0;
 }
 
 static dfgks_status build_maps(dfgks_batch* b) {
     b->hstarts.assign((size_t)PH_COUNT * (b->np + 1), 0);
     for (int ph = 0; ph < PH_COUNT; ++ph) {
-        int acc = 0;
+        long long acc = 0;
         for (int p = 0; p < b->np; ++p) {
-            int gx, gy, gz;
-            phase_grid(ph, b->host[p].m, shape_of(b, ph), gx, gy, gz);
-            b->hstarts[(size_t)ph * (b->np + 1) + p] = acc;
-            acc += gx * gy * gz;
+            int per_z;
+            b->hstarts[(size_t)ph * (b->np + 1) + p] = (int)acc;
+            acc += phase_blocks(ph, b->host[p].m, block_of(b, ph), per_z);
         }
-        b->hstarts[(size_t)ph * (b->np + 1) + b->np] = acc;
-        b->total[ph] = acc;
+        if (acc > 0x7fffffffLL) return DFGKS_EINVAL;            // grid.x limit
+        b->hstarts[(size_t)ph * (b->np + 1) + b->np] = (int)acc;
+        b->total[ph] = (int)acc;
     }
     BCK(cudaMemcpyAsync(b->starts, b->hstarts.data(), b->hstarts.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream));
     BCK(cudaStreamSynchronize(b->stream));
@@ -249,7 +276,7 @@ static BlockMap bmap(const dfgks_batch* b, int ph) {
     BlockMap m;
     m.start = b->starts + (size_t)ph * (b->np + 1);
     m.np = b->np;
-    m.sh = shape_of(b, ph);
+    m.bs = block_of(b, ph);
     return m;
 }
 
@@ -262,28 +289,42 @@ static void enqueue_batch_step(dfgks_batch* b) {
     for (int stage = 0; stage < 2; ++stage) {
         kb_ghost_x<<<b->total[PH_GX], dim3(2 * G, 32), 0, s>>>(P, bmap(b, PH_GX), stage);
         kb_ghost_y<<<b->total[PH_GY], 128, 0, s>>>(P, bmap(b, PH_GY), stage);
-        for (int d = 0; d < 2; ++d) {
-            const int phl = d == 0 ? PH_LINES0 : PH_LINES1, phf = d == 0 ? PH_FACES0 : PH_FACES1;
-            const int phx = d == 0 ? PH_FLUX0 : PH_FLUX1;
-            dim3 bl(b->shape[0].bx, b->shape[0].by), bf(b->shape[1].bx, b->shape[1].by), bx(b->shape[2].bx, b->shape[2].by);
-            if (d == 0) {
-                kb_lines<0><<<b->total[phl], bl, 0, s>>>(P, bmap(b, phl), stage);
-                kb_faces<0><<<b->total[phf], bf, 0, s>>>(P, bmap(b, phf), stage);
-                kb_flux<0><<<b->total[phx], bx, 0, s>>>(P, bmap(b, phx));
-            } else {
-                kb_lines<1><<<b->total[phl], bl, 0, s>>>(P, bmap(b, phl), stage);
-                kb_faces<1><<<b->total[phf], bf, 0, s>>>(P, bmap(b, phf), stage);
-                kb_flux<1><<<b->total[phx], bx, 0, s>>>(P, bmap(b, phx));
-            }
-        }
+        kb_lines<0><<<b->total[PH_LINES0], b->block[0], 0, s>>>(P, bmap(b, PH_LINES0), stage);
+        kb_faces<0><<<b->total[PH_FACES0], b->block[1], 0, s>>>(P, bmap(b, PH_FACES0), stage);
+        kb_flux<0><<<b->total[PH_FLUX0], b->block[2], 0, s>>>(P, bmap(b, PH_FLUX0));
+        kb_lines<1><<<b->total[PH_LINES1], b->block[0], 0, s>>>(P, bmap(b, PH_LINES1), stage);
+        kb_faces<1><<<b->total[PH_FACES1], b->block[1], 0, s>>>(P, bmap(b, PH_FACES1), stage);
+        kb_flux<1><<<b->total[PH_FLUX1], b->block[2], 0, s>>>(P, bmap(b, PH_FLUX1));
         if (stage == 0) kb_update<UM_S2O4_1><<<b->total[PH_UPD], dim3(32, 8), 0, s>>>(P, bmap(b, PH_UPD));
         else kb_update<UM_S2O4_2><<<b->total[PH_UPD], dim3(32, 8), 0, s>>>(P, bmap(b, PH_UPD));
     }
     kb_end_step<<<nb, tb, 0, s>>>(P, np, b->t_end);
 }
 
-static void free_batch(dfgks_batch* b) {
+static void drop_graph(dfgks_batch* b) {
     if (b->graph_ok) cudaGraphExecDestroy(b->graph);
+    b->graph_ok = false;
+    b->n_graph = 0;
+}
+
+// capture n steps of every problem into one CUDA graph (n x 21 kernel nodes)
+static dfgks_status capture_steps(dfgks_batch* b, int n) {
+    drop_graph(b);
+    cudaGraph_t g;
+    BCK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    for (int k = 0; k < n; ++k) enqueue_batch_step(b);
+    cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+    if (e != cudaSuccess) return cst(e);
+    e = cudaGraphInstantiate(&b->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cst(e);
+    b->graph_ok = true;
+    b->n_graph = n;
+    return DFGKS_OK;
+}
+
+static void free_batch(dfgks_batch* b) {
+    drop_graph(b);
     for (void* p : b->allocs) cudaFree(p);
     if (b->st_host) cudaFreeHost(b->st_host);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
@@ -320,10 +361,11 @@ extern "C" DFGKS_API dfgks_status dfgks_batch_create(const dfgks_config* cfgs, c
     b->np = np;
     b->bytes = 0;
     b->graph_ok = false;
+    b->n_graph = 0;
     b->t_end = 0.0;
     b->st_host = nullptr;
     b->dev = nullptr;
-    b->shape[0] = b->shape[1] = b->shape[2] = Shape{32, 4};
+    b->block[0] = b->block[1] = b->block[2] = 128;
     if (stream) { b->stream = (cudaStream_t)stream; b->own_stream = false; }
     else if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) { delete b; return DFGKS_ECUDA; }
     else b->own_stream = true;
@@ -473,25 +515,27 @@ extern "C" DFGKS_API dfgks_status dfgks_batch_get_state(dfgks_batch* b, int p, d
     return DFGKS_OK;
 }
 
-// Advance every problem n steps (each with its own CFL dt).  use_graph != 0: the step's launch
-// sequence is captured once in a CUDA graph and replayed.  Returns DFGKS_ENONPOS if any problem
-// lost positivity (that problem stops at its last good step; the others continue).
+// Capture the graph that advances every problem n steps (done by dfgks_batch_step on first use
+// of that n; calling it ahead keeps the capture out of a timed region).
+extern "C" DFGKS_API dfgks_status dfgks_batch_prepare(dfgks_batch* b, int n) {
+    if (!b || n < 1 || n > 100000) return DFGKS_EINVAL;
+    if (b->graph_ok && b->n_graph == n) return DFGKS_OK;
+    return capture_steps(b, n);
+}
+
+// Advance every problem n steps (each with its own CFL dt).  use_graph != 0: one launch of a CUDA
+// graph holding all n steps (captured on first use of this n).  Returns DFGKS_ENONPOS if any
+// problem lost positivity (that problem stops at its last good step; the others continue).
 extern "C" DFGKS_API dfgks_status dfgks_batch_step(dfgks_batch* b, int n, int use_graph) {
-    if (!b || n < 0) return DFGKS_EINVAL;
-    if (use_graph && !b->graph_ok) {
-        cudaGraph_t g;
-        BCK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-        enqueue_batch_step(b);
-        cudaError_t e = cudaStreamEndCapture(b->stream, &g);
-        if (e != cudaSuccess) return cst(e);
-        e = cudaGraphInstantiate(&b->graph, g, 0);
-        cudaGraphDestroy(g);
-        if (e != cudaSuccess) return cst(e);
-        b->graph_ok = true;
-    }
-    for (int s = 0; s < n; ++s) {
-        if (use_graph) BCK(cudaGraphLaunch(b->graph, b->stream));
-        else enqueue_batch_step(b);
+    if (!b || n < 0 || n > 100000) return DFGKS_EINVAL;
+    if (n > 0 && use_graph) {
+        if (!b->graph_ok || b->n_graph != n) {
+            dfgks_status r = capture_steps(b, n);
+            if (r != DFGKS_OK) return r;
+        }
+        BCK(cudaGraphLaunch(b->graph, b->stream));
+    } else {
+        for (int s = 0; s < n; ++s) enqueue_batch_step(b);
     }
     BCK(cudaGetLastError());
     BCK(cudaMemcpyAsync(b->st_host, b->st, (size_t)b->np * sizeof(DevState), cudaMemcpyDeviceToHost, b->stream));
@@ -500,22 +544,21 @@ extern "C" DFGKS_API dfgks_status dfgks_batch_step(dfgks_batch* b, int n, int us
     return DFGKS_OK;
 }
 
-// Block shapes (bx, by with bx * by = 128) of the face-line, tangential and flux kernels.
-extern "C" DFGKS_API dfgks_status dfgks_batch_set_shapes(dfgks_batch* b, const int* shapes6) {
-    if (!b || !shapes6) return DFGKS_EINVAL;
-    for (int k = 0; k < 3; ++k) {
-        int bx = shapes6[2 * k], by = shapes6[2 * k + 1];
-        if (bx < 1 || by < 1 || bx * by != 128 || (bx % 32) != 0) return DFGKS_EINVAL;
-    }
-    for (int k = 0; k < 3; ++k) b->shape[k] = Shape{shapes6[2 * k], shapes6[2 * k + 1]};
-    if (b->graph_ok) { cudaGraphExecDestroy(b->graph); b->graph_ok = false; }
+static bool block_ok(int bs) { return bs == 64 || bs == 128 || bs == 256; }
+
+// Threads per block (64, 128 or 256) of the face-line, tangential and flux kernels.
+extern "C" DFGKS_API dfgks_status dfgks_batch_set_blocks(dfgks_batch* b, const int* blocks3) {
+    if (!b || !blocks3) return DFGKS_EINVAL;
+    for (int k = 0; k < 3; ++k) if (!block_ok(blocks3[k])) return DFGKS_EINVAL;
+    for (int k = 0; k < 3; ++k) b->block[k] = blocks3[k];
+    drop_graph(b);
     return build_maps(b);
 }
 
 // Autotuner: for each of the three sweep kernels in turn, time one batched step per candidate
-// block shape (32x4, 64x2, 128x1) with the others fixed, keep the fastest.  The problems' states
-// are saved before and restored after, so tuning does not advance them.  shapes6 receives the choice.
-extern "C" DFGKS_API dfgks_status dfgks_batch_autotune(dfgks_batch* b, int* shapes6, double* best_ms) {
+// block size (64, 128, 256 threads) with the others fixed, keep the fastest.  The problems' states
+// are saved before and restored after, so tuning does not advance them.  blocks3 receives the choice.
+extern "C" DFGKS_API dfgks_status dfgks_batch_autotune(dfgks_batch* b, int* blocks3, double* best_ms) {
     if (!b) return DFGKS_EINVAL;
     // snapshot: both state buffers, both alpha buffers, DevStates
     std::vector<double*> saved;
@@ -546,7 +589,7 @@ extern "C" DFGKS_API dfgks_status dfgks_batch_autotune(dfgks_batch* b, int* shap
     std::vector<DevState> st0(b->st_host, b->st_host + b->np);
     cudaError_t e = restore_or_save(true);
     if (e != cudaSuccess) { for (double* c : saved) cudaFree(c); return cst(e); }
-    const Shape cand[3] = {{32, 4}, {64, 2}, {128, 1}};
+    const int cand[3] = {64, 128, 256};
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -554,9 +597,9 @@ extern "C" DFGKS_API dfgks_status dfgks_batch_autotune(dfgks_batch* b, int* shap
     dfgks_status r = DFGKS_OK;
     for (int k = 0; k < 3 && r == DFGKS_OK; ++k) {
         float best = 1e30f;
-        Shape keep = b->shape[k];
+        int keep = b->block[k];
         for (int c = 0; c < 3 && r == DFGKS_OK; ++c) {
-            b->shape[k] = cand[c];
+            b->block[k] = cand[c];
             r = build_maps(b);
             if (r != DFGKS_OK) break;
             enqueue_batch_step(b);                           // warm-up
@@ -573,7 +616,7 @@ extern "C" DFGKS_API dfgks_status dfgks_batch_autotune(dfgks_batch* b, int* shap
             if (cudaMemcpyAsync(b->st, b->st_host, (size_t)b->np * sizeof(DevState), cudaMemcpyHostToDevice, b->stream) != cudaSuccess) { r = DFGKS_ECUDA; break; }
             cudaStreamSynchronize(b->stream);
         }
-        b->shape[k] = keep;
+        b->block[k] = keep;
         best_total = best;
     }
     cudaEventDestroy(e0);
@@ -582,8 +625,8 @@ extern "C" DFGKS_API dfgks_status dfgks_batch_autotune(dfgks_batch* b, int* shap
     for (double* c : saved) cudaFree(c);
     if (r != DFGKS_OK) return r;
     r = build_maps(b);
-    if (b->graph_ok) { cudaGraphExecDestroy(b->graph); b->graph_ok = false; }
-    if (shapes6) for (int k = 0; k < 3; ++k) { shapes6[2 * k] = b->shape[k].bx; shapes6[2 * k + 1] = b->shape[k].by; }
+    drop_graph(b);
+    if (blocks3) for (int k = 0; k < 3; ++k) blocks3[k] = b->block[k];
     if (best_ms) *best_ms = best_total;
     return r;
 }

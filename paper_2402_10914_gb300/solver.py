@@ -197,7 +197,9 @@ class BatchSolver:
     """Many independent problems advanced together (dfgks_batch_*): one launch per phase over all
     problems, optionally replayed from a CUDA graph.  ``settings`` is a list of ``Settings``."""
 
-    def __init__(self, settings: list, autotune_cache: str | None = None):
+    def __init__(self, settings: list, autotune_cache: str | None = None, stream=None):
+        """``stream``: a non-default torch.cuda.Stream to order the batch's work on (events recorded
+        on it time the batch); None lets the library create a private stream."""
         self.settings = list(settings)
         n = len(self.settings)
         cfgs = (_lib.Config * n)()
@@ -205,10 +207,12 @@ class BatchSolver:
             cfgs[k] = make_config(s)
         flux = (C.c_int * n)(*[int(s.flux) for s in self.settings])
         h = C.c_void_p()
-        _lib.check(_lib.lib().dfgks_batch_create(C.cast(cfgs, C.c_void_p), C.cast(flux, C.c_void_p), n, None,
+        self.stream = stream
+        handle = None if stream is None else C.c_void_p(stream.cuda_stream)
+        _lib.check(_lib.lib().dfgks_batch_create(C.cast(cfgs, C.c_void_p), C.cast(flux, C.c_void_p), n, handle,
                                                  C.byref(h)), "dfgks_batch_create")
         self._h = h
-        self.shapes = None
+        self.blocks = None
         self._cache = autotune_cache
 
     def close(self):
@@ -233,8 +237,9 @@ class BatchSolver:
         _lib.check(_lib.lib().dfgks_batch_set_ic(self._h, int(p), C.c_void_p(W.ctypes.data), 0), "dfgks_batch_set_ic")
 
     def step(self, n: int, use_graph: bool = True) -> int:
-        """Advance all problems n steps; returns the status (0 or ENONPOS) instead of raising on
-        positivity loss, since the other problems continue."""
+        """Advance all problems n steps (with use_graph, one launch of the n-step CUDA graph); returns
+        the status (0 or ENONPOS) instead of raising on positivity loss, since the other problems
+        continue."""
         rc = _lib.lib().dfgks_batch_step(self._h, int(n), int(use_graph))
         if rc not in (_lib.OK, _lib.ENONPOS):
             _lib.check(rc, "dfgks_batch_step")
@@ -255,16 +260,20 @@ class BatchSolver:
                    "dfgks_batch_status")
         return {"step": st.value, "err": err.value, "df_normal": dfn.value}
 
-    def set_shapes(self, shapes):
-        arr = (C.c_int * 6)(*[int(v) for pair in shapes for v in pair])
-        _lib.check(_lib.lib().dfgks_batch_set_shapes(self._h, C.cast(arr, C.c_void_p)), "dfgks_batch_set_shapes")
-        self.shapes = [tuple(x) for x in shapes]
+    def prepare(self, n: int):
+        """Capture the CUDA graph that advances every problem n steps (dfgks_batch_prepare)."""
+        _lib.check(_lib.lib().dfgks_batch_prepare(self._h, int(n)), "dfgks_batch_prepare")
+
+    def set_blocks(self, blocks):
+        arr = (C.c_int * 3)(*[int(v) for v in blocks])
+        _lib.check(_lib.lib().dfgks_batch_set_blocks(self._h, C.cast(arr, C.c_void_p)), "dfgks_batch_set_blocks")
+        self.blocks = [int(v) for v in blocks]
 
     def signature(self) -> str:
         return ";".join("%dx%d:%d" % (s.nx, s.ny, s.flux) for s in self.settings)
 
     def autotune(self):
-        """Pick the sweep kernels' block shapes by timing (dfgks_batch_autotune); with a cache file,
+        """Pick the sweep kernels' block sizes by timing (dfgks_batch_autotune); with a cache file,
         reuse an earlier choice for the same set of problems."""
         import json
         import os
@@ -275,13 +284,13 @@ class BatchSolver:
             except Exception:
                 cached = None
             if cached:
-                self.set_shapes(cached)
-                return self.shapes, None
-        arr = (C.c_int * 6)()
+                self.set_blocks(cached)
+                return self.blocks, None
+        arr = (C.c_int * 3)()
         best = C.c_double()
         _lib.check(_lib.lib().dfgks_batch_autotune(self._h, C.cast(arr, C.c_void_p), C.byref(best)),
                    "dfgks_batch_autotune")
-        self.shapes = [(arr[0], arr[1]), (arr[2], arr[3]), (arr[4], arr[5])]
+        self.blocks = [arr[0], arr[1], arr[2]]
         if self._cache:
             data = {}
             if os.path.exists(self._cache):
@@ -289,10 +298,94 @@ class BatchSolver:
                     data = json.load(open(self._cache))
                 except Exception:
                     data = {}
-            data[key] = self.shapes
+            data[key] = self.blocks
             with open(self._cache, "w") as f:
                 json.dump(data, f)
-        return self.shapes, best.value
+        return self.blocks, best.value
+
+
+def block_plan(settings: Settings, px: int, py: int, block: int) -> dict:
+    """Where block `block` of a px x py decomposition sits (dfgks_decomp_plan; host only): its cells
+    [i0, i1) x [j0, j1), per side (x-low, x-high, y-low, y-high) its boundary code (BC_EXTERNAL for
+    a side a halo copy fills) and the neighbouring block that copy comes from (-1 for none)."""
+    p = _lib.BlockPlan()
+    cfg = make_config(settings)
+    _lib.check(_lib.lib().dfgks_decomp_plan(C.byref(cfg), int(px), int(py), int(block), C.byref(p)),
+               "dfgks_decomp_plan")
+    return {"i0": p.i0, "i1": p.i1, "j0": p.j0, "j1": p.j1, "bc": list(p.bc), "neighbour": list(p.neighbour)}
+
+
+def halo_window(settings: Settings, px: int, py: int, block: int, side: int) -> dict:
+    """The halo copy filling one side of a block (dfgks_decomp_halo; host only): the neighbour it
+    comes from (-1: none), the window (di, dj, w, h) of the block's ghosted field and its start
+    (si, sj) in the neighbour's field, both in block cell indices (ghosts negative / >= size)."""
+    hw = _lib.HaloWindow()
+    cfg = make_config(settings)
+    _lib.check(_lib.lib().dfgks_decomp_halo(C.byref(cfg), int(px), int(py), int(block), int(side), C.byref(hw)),
+               "dfgks_decomp_halo")
+    return {f: getattr(hw, f) for f, _ in _lib.HaloWindow._fields_}
+
+
+class DecompSolver:
+    """One problem split into px x py blocks with halo exchange (dfgks_decomp_*), on the current
+    device; the state goes in and out as the whole mesh."""
+
+    def __init__(self, settings: Settings, px: int, py: int, stream: torch.cuda.Stream | None = None):
+        self.settings = settings
+        self.px, self.py = int(px), int(py)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self._cfg = make_config(settings)
+        h = C.c_void_p()
+        handle = self.stream.cuda_stream or CUDA_STREAM_LEGACY
+        _lib.check(_lib.lib().dfgks_decomp_create(C.byref(self._cfg), self.px, self.py, C.c_void_p(handle), C.byref(h)),
+                   "dfgks_decomp_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.lib().dfgks_decomp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_ic(self, W):
+        W = np.ascontiguousarray(np.asarray(W, dtype=np.float64))
+        assert W.shape == (4, self.settings.ny, self.settings.nx)
+        _lib.check(_lib.lib().dfgks_decomp_set_ic(self._h, C.c_void_p(W.ctypes.data), 0), "dfgks_decomp_set_ic")
+
+    def step(self, n: int, t_end: float = 0.0, flux: int | None = None) -> int:
+        done = C.c_int(0)
+        f = self.settings.flux if flux is None else flux
+        _lib.check(_lib.lib().dfgks_decomp_step(self._h, int(n), int(f), float(t_end), C.byref(done)),
+                   "dfgks_decomp_step")
+        return done.value
+
+    def get_state(self):
+        s = self.settings
+        W = np.empty((4, s.ny, s.nx))
+        a = np.empty((s.ny, s.nx))
+        t, st = C.c_double(), C.c_long()
+        _lib.check(_lib.lib().dfgks_decomp_get_state(self._h, C.c_void_p(W.ctypes.data), C.c_void_p(a.ctypes.data),
+                                                     C.byref(t), C.byref(st), 0), "dfgks_decomp_get_state")
+        return W, a, t.value, st.value
+
+    def status(self) -> dict:
+        err, fi, fj = C.c_int(), C.c_int(), C.c_int()
+        c = _lib.Counters()
+        _lib.check(_lib.lib().dfgks_decomp_status(self._h, C.byref(err), C.byref(fi), C.byref(fj), C.byref(c)),
+                   "dfgks_decomp_status")
+        return {"err": err.value, "fail_i": fi.value, "fail_j": fj.value, "fallbacks": c.fallbacks,
+                "df_normal": c.df_normal, "df_tangential": c.df_tangential}
 
 
 def _dev(t):

@@ -1,5 +1,5 @@
 """Batched path (dfgks_batch_*): many uneven problems advanced by one launch per phase, optionally
-replayed from a CUDA graph, against the per-problem handles.  Both run the same per-thread bodies,
+all n steps in one CUDA graph launch, against the per-problem handles and against the oracle.  Both run the same per-thread bodies,
 but in different kernels, where the compiler may contract a different multiply-add into an FMA;
 with the time limiter's amplification (about 2x per step) the results agree to ~1e-12 after a
 few steps rather than bitwise.  A failing problem stops alone; the autotuner does not advance
@@ -93,20 +93,56 @@ def test_autotune_keeps_state_and_results(tmp_path):
     from paper_2402_10914_gb300.solver import BatchSolver
     ws = mixed_problems()[:4]
     ref = per_problem(ws, 5)
-    cache = str(tmp_path / "shapes.json")
+    cache = str(tmp_path / "blocks.json")
     with BatchSolver([w.settings for w in ws], autotune_cache=cache) as b:
         for p, w in enumerate(ws):
             b.set_ic(p, w.W0)
         b.step(2, use_graph=False)
-        shapes, best = b.autotune()
-        assert len(shapes) == 3 and all(x * y == 128 for x, y in shapes)
+        blocks, best = b.autotune()
+        assert len(blocks) == 3 and all(x in (64, 128, 256) for x in blocks)
         b.step(3, use_graph=True)
         for p in range(len(ws)):
             W, a, t, step = b.get_state(p)
             assert step == 5 and comp_rel_err(W, ref[p][0]) <= BAR
     with BatchSolver([w.settings for w in ws], autotune_cache=cache) as b2:
-        shapes2, best2 = b2.autotune()          # served from the cache
-        assert best2 is None and shapes2 == shapes
+        blocks2, best2 = b2.autotune()          # served from the cache
+        assert best2 is None and blocks2 == blocks
+
+
+@pytest.mark.parametrize("blocks", [(64, 64, 64), (256, 256, 256), (128, 64, 256)])
+def test_block_sizes_give_the_same_results(blocks):
+    # every block size covers each problem's index space exactly once
+    from paper_2402_10914_gb300.solver import BatchSolver
+    ws = mixed_problems()
+    ref = per_problem(ws, 3)
+    with BatchSolver([w.settings for w in ws]) as b:
+        b.set_blocks(blocks)
+        for p, w in enumerate(ws):
+            b.set_ic(p, w.W0)
+        assert b.step(3, use_graph=False) == 0
+        for p in range(len(ws)):
+            W, a, t, step = b.get_state(p)
+            assert step == 3 and comp_rel_err(W, ref[p][0]) <= BAR, (blocks, p)
+
+
+def test_one_graph_launch_advances_n_steps():
+    # a graph of n steps, launched once, against the same kernels launched step by step: the
+    # same launches in the same order, so the states agree bit for bit
+    from paper_2402_10914_gb300.solver import BatchSolver
+    ws = mixed_problems()
+    with BatchSolver([w.settings for w in ws]) as a, BatchSolver([w.settings for w in ws]) as b:
+        for p, w in enumerate(ws):
+            a.set_ic(p, w.W0)
+            b.set_ic(p, w.W0)
+        a.prepare(5)                             # the 5-step graph, captured ahead
+        assert a.step(5) == 0                    # one launch
+        assert a.step(4) == 0                    # a new 4-step graph, one launch
+        assert b.step(9, use_graph=False) == 0
+        for p in range(len(ws)):
+            Wa, aa, ta, sa = a.get_state(p)
+            Wb, ab, tb, sb = b.get_state(p)
+            assert sa == sb == 9 and ta == tb
+            assert np.array_equal(Wa, Wb) and np.array_equal(aa, ab), p
 
 
 def test_batch_rejects_unsupported():
@@ -130,3 +166,39 @@ def test_c3_batch_first_steps_match_per_problem():
         for p in range(len(ws)):
             W, a, t, step = b.get_state(p)
             assert step == 2 and comp_rel_err(W, ref[p][0]) <= BAR, p
+
+
+def test_c3_batch_against_the_oracle():
+    # 2 steps of the 64-problem uneven batch itself, against the oracle, for the first problem of
+    # every (side length, flux) pair the batch holds: one-step bar 1e-12 per component, or within
+    # twice the oracle's own spread under 1e-15 input noise where the time limiter amplifies rounding
+    import oracle
+    from tests.parity_util import oracle_envelope
+    from paper_2402_10914_gb300.solver import BatchSolver
+    ws = I.batch()
+    pick = {}
+    for p, w in enumerate(ws):
+        pick.setdefault((w.settings.nx, w.settings.flux), p)
+    sides = {k[0] for k in pick}
+    assert sides == {64, 96, 128, 192, 256, 384, 512} and {k[1] for k in pick} == {I.GKS, I.LF}
+    with BatchSolver([w.settings for w in ws]) as b:
+        for p, w in enumerate(ws):
+            b.set_ic(p, w.W0)
+        b.step(2)
+        got = {p: b.get_state(p) for p in pick.values()}
+    strict, enveloped = 0, []
+    for (n, flux), p in sorted(pick.items()):
+        w = ws[p]
+        W, a, t, step = got[p]
+        rc, Wo, ao, to, dts, st = oracle.run(w.settings, w.W0, oracle.alpha0(w.settings, w.W0), 2)
+        assert rc == 0 and step == 2 and abs(t - to) <= 1e-14 * to, (n, flux)
+        err = comp_rel_err(W, Wo)
+        if err <= 1e-12:
+            strict += 1
+        else:
+            _, env, _ = oracle_envelope(w.settings, w.W0, 2)
+            assert err <= 2.0 * env, (n, flux, err, env)
+            enveloped.append((n, flux, err, env))
+        assert comp_rel_err(a[None], ao[None], floor_frac=1e-12) <= 1e-9, (n, flux)
+    print("C3 against the oracle: %d of %d strictly within 1e-12; within the oracle's spread: %s"
+          % (strict, len(pick), enveloped))
