@@ -25,6 +25,8 @@ Workloads (all FP64, gamma = 1.4):
                  rho = 1, u = -2 / +2, p0 set by the Mach number u / c, free boundaries, t = 0.14.
   hurricane      Sect. 4.3 hurricane-like flow: rho = 1, p = 25 (entropy A = 25), rotation speed v0
                  set by the Mach number v0 / c0, [-2,2]^2 at dx = 1/100, 50 steps.
+  planar_rarefaction  Sect. 4.3.3 interaction of planar rarefaction waves (a reading of the garbled
+                 initial state), off-diagonal density set by the Mach number, 400^2, t = 0.15.
 """
 from __future__ import annotations
 
@@ -265,6 +267,24 @@ def hurricane(ma: float, n: int = 400, flux: int = GKS, steps: int = 50) -> Work
     th = np.arctan2(Y, X)
     W = conserved(np.full_like(X, rho0), v0 * np.sin(th), -v0 * np.cos(th), np.full_like(X, p0), s.gamma)
     return Workload("hurricane_ma%g_%d" % (ma, n), s, W, steps=steps, meta={"mach": ma, "v0": v0})
+
+
+def planar_rarefaction(ma: float, n: int = 400, flux: int = GKS, t_end: float = 0.15) -> Workload:
+    """Sect. 4.3.3, interaction of planar rarefaction waves on [0,1]^2 with free (outflow) boundaries,
+    dx = 1/400, t = 0.15.  The printed initial state is garbled; read as: (1, -U, -U, 1.5) for
+    x < .5, y < .5; (rho, U, -U, A rho^gamma) for x >= .5, y < .5; (1, U, U, 1.5) for x >= .5, y >= .5
+    (the printed "1.0.6323" taken as rho = 1.0, u = 0.6323); (rho, -U, U, A rho^gamma) for x < .5,
+    y >= .5; U = 0.6323, A = 1.5 (so the rho = 1 quadrants also have p = A rho^gamma).  Every
+    quadrant moves away from the centre.  The off-diagonal density rho is the parameter that is
+    lowered; it sets the printed reference Mach number sqrt(2) U / sqrt(gamma A rho^(gamma-1)),
+    so rho = (2 U^2 / (gamma A Ma^2))^(1/(gamma-1))."""
+    s = Settings(nx=n, ny=n, cfl=0.5, bc=(OUTFLOW,) * 4, flux=flux, time_scheme=S2O4 if flux == GKS else SSPRK3)
+    U, A = 0.6323, 1.5
+    rho = (2.0 * U * U / (s.gamma * A * ma * ma)) ** (1.0 / (s.gamma - 1.0))
+    p = A * rho ** s.gamma
+    states = [(1.0, -U, -U, 1.5), (rho, U, -U, p), (1.0, U, U, 1.5), (rho, -U, U, p)]
+    return Workload("planar_rarefaction_ma%g_%d" % (ma, n), s, _four_states(s, states, 0.5, 0.5), t_end=t_end,
+                    meta={"mach": ma, "rho": rho, "p": p})
 
 
 def random_smooth(nx: int, ny: int, seed: int, amp: float = 0.1, bc=(PERIODIC,) * 4, **kw) -> Workload:

@@ -156,3 +156,28 @@ def test_robustness_cases_carry_their_mach_numbers(ma):
     assert np.allclose(speed / np.sqrt(h.settings.gamma * p / W[0]), ma, rtol=1e-12)
     assert np.allclose(u * X + v * Y, 0.0, atol=1e-12 * speed.max() * 2.0)   # purely rotational
     assert np.allclose(p, 25.0) and np.allclose(W[0], 1.0)
+
+
+@pytest.mark.parametrize("ma", [0.745, 2.1, 18.1])
+def test_planar_rarefaction_reading(ma):
+    # the reading of the garbled Sect. 4.3.3 state: every quadrant moves away from the centre with
+    # |u| = |v| = 0.6323, all four states on the isentrope p = 1.5 rho^gamma, and the printed
+    # reference Mach number sqrt(u^2 + v^2) / sqrt(gamma A rho^(gamma-1)) of the off-diagonal state
+    w = I.planar_rarefaction(ma, n=40)
+    s = w.settings
+    W = w.W0
+    xc, yc, _, _ = I.cell_centres(s)
+    X, Y = np.meshgrid(xc, yc)
+    rho, u, v = W[0], W[1] / W[0], W[2] / W[0]
+    p = (s.gamma - 1.0) * (W[3] - 0.5 * rho * (u * u + v * v))
+    assert np.allclose(np.abs(u), 0.6323) and np.allclose(np.abs(v), 0.6323)
+    assert np.all(np.sign(u) == np.sign(X - 0.5)) and np.all(np.sign(v) == np.sign(Y - 0.5))
+    assert np.allclose(p, 1.5 * rho ** s.gamma, rtol=1e-12)
+    diag = (X - 0.5) * (Y - 0.5) > 0
+    assert np.allclose(rho[diag], 1.0) and np.allclose(p[diag], 1.5)
+    off = ~diag
+    mach = np.hypot(u, v)[off] / np.sqrt(s.gamma * p[off] / rho[off])
+    assert np.allclose(mach, ma, rtol=1e-12)
+    assert s.bc == (I.OUTFLOW,) * 4 and w.t_end == 0.15
+    if ma == 0.745:                      # the paper's example case, p = 0.4 in the rarefied quadrants
+        assert abs(p[off][0] - 0.4) < 2e-3
