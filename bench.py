@@ -49,7 +49,7 @@ FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
 # FP64-pipe instructions per Gauss point, DRAM bytes per launch at 400 x 400) are read from the
 # machine-readable line of the committed ncu summary of that kernel, which also records a hash of
 # the kernel sources it was measured on; the counts are used only while that hash matches.
-FLUX_PROFILE = os.path.join(ROOT, "profiles", "k_flux_gks_counts.md")
+FLUX_PROFILE = os.path.join(ROOT, "profiles", "k_flux_gks_counts.txt")
 
 
 def profile_counts(path: str = FLUX_PROFILE):
@@ -230,10 +230,11 @@ def bench_ours(args, ws, rank, local):
     dominant = max(share, key=share.get)
     fl = timing["flux"]
     avg_flux_ms = fl["ms"] / max(fl["timed"], 1)
-    gps_per_launch = 2.0 * (s.nx + 1) * s.ny       # x- and y-sweeps have the same count on a square mesh
+    # one flux launch per stage covers the Gauss points of both directions (fused x/y sweeps)
+    gps_per_launch = 2.0 * ((s.nx + 1) * s.ny + (s.ny + 1) * s.nx)
     counts, why = profile_counts()
     traffic = counts.get("traffic_bytes_per_launch") if counts and args.n == BENCH_N else None
-    roof = {"kernel": "k_flux<GKS> (Gauss-point flux)", "bound": "alu", "unit": "GFLOP/s",
+    roof = {"kernel": "k_flux_xy<GKS> (Gauss-point flux, x and y faces)", "bound": "alu", "unit": "GFLOP/s",
             "peak": round(FP64_PEAK_GFLOPS, 1), "peak_source": "derived: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz",
             "avg_launch_ms": avg_flux_ms, "launches_timed": fl["timed"], "traffic": traffic,
             "traffic_unit": "B per launch (ncu dram read+write)",

@@ -369,29 +369,41 @@ DFK_HD int faces_body(const Mesh& m, const SchemeConsts& S, const double* __rest
     return ndf;
 }
 
-// one Gauss point (flux, time derivative, DF factor, omega^t)
-template <int DIR, int FLUX, bool ALPHA_ONLY, bool TAPE = false>
-DFK_HD void flux_body(const Mesh& m, const SchemeConsts& S, const double* __restrict__ lines,
-                                          long long ls, const double* __restrict__ gp, long long gs,
-                                          double* __restrict__ fr, long long fs, double dt, int ax, int ay, int mm,
-                         double* __restrict__ tape = nullptr) {
+// where one Gauss point's records live: side records eL / eR, its flux record e, its face line li
+struct FluxSite { long long eL, eR, e, li; bool ok; };
+
+template <int DIR>
+DFK_HD FluxSite flux_site(const Mesh& m, int ax, int ay, int mm) {
     Geo<DIR> g(m);
-    int f = DIR == 0 ? ax : ay;
-    int t = DIR == 0 ? ay : ax;
-    if (f > g.nn || t >= g.nt) return;
+    const int f = DIR == 0 ? ax : ay;
+    const int t = DIR == 0 ? ay : ax;
+    FluxSite s;
+    s.ok = f <= g.nn && t < g.nt;
+    if (!s.ok) { s.eL = s.eR = s.e = s.li = 0; return s; }
     const long long fid = g.face(f, t);
-    const long long eL = fid, eR = g.nfaces() + fid;
+    s.eL = fid;
+    s.eR = g.nfaces() + fid;
+    s.e = (long long)mm * g.nfaces() + fid;
+    s.li = g.line(f, t);
+    return s;
+}
+
+// one Gauss point (flux, time derivative, DF factor, omega^t) of direction dir at a site
+template <int FLUX, bool ALPHA_ONLY, bool TAPE = false>
+DFK_HD void flux_point(int dir, const SchemeConsts& S, const FluxSite& site, const double* __restrict__ lines,
+                       long long ls, const double* __restrict__ gp, long long gs, double* __restrict__ fr,
+                       long long fs, double dt, int mm, double* __restrict__ tape = nullptr) {
     GPState L, R;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        L.W[k] = gp[(mm * 12 + k) * gs + eL];
-        L.Wn[k] = gp[(mm * 12 + 4 + k) * gs + eL];
-        L.Wt[k] = gp[(mm * 12 + 8 + k) * gs + eL];
-        R.W[k] = gp[(mm * 12 + k) * gs + eR];
-        R.Wn[k] = gp[(mm * 12 + 4 + k) * gs + eR];
-        R.Wt[k] = gp[(mm * 12 + 8 + k) * gs + eR];
+        L.W[k] = gp[(mm * 12 + k) * gs + site.eL];
+        L.Wn[k] = gp[(mm * 12 + 4 + k) * gs + site.eL];
+        L.Wt[k] = gp[(mm * 12 + 8 + k) * gs + site.eL];
+        R.W[k] = gp[(mm * 12 + k) * gs + site.eR];
+        R.Wn[k] = gp[(mm * 12 + 4 + k) * gs + site.eR];
+        R.Wt[k] = gp[(mm * 12 + 8 + k) * gs + site.eR];
     }
-    const long long e = (long long)mm * g.nfaces() + fid;
+    const long long e = site.e;
     fr[FR_ALPHA * fs + e] = df_alpha(L.W, R.W, S);
     if (ALPHA_ONLY) return;
     double F[4], dF[4];
@@ -404,11 +416,21 @@ DFK_HD void flux_body(const Mesh& m, const SchemeConsts& S, const double* __rest
         }
     }
     else lf_flux(L, R, S, F, dF);
-    to_global<DIR>(F);
-    to_global<DIR>(dF);
+    if (dir == 1) { to_global<1>(F); to_global<1>(dF); }
 #pragma unroll
     for (int k = 0; k < 4; ++k) { fr[(FR_F + k) * fs + e] = F[k]; fr[(FR_DF + k) * fs + e] = dF[k]; }
-    fr[FR_OMEGA * fs + e] = S.time_limiter ? lines[LR_TL * ls + g.line(f, t)] : 1.0;
+    fr[FR_OMEGA * fs + e] = S.time_limiter ? lines[LR_TL * ls + site.li] : 1.0;
+}
+
+// one Gauss point (flux, time derivative, DF factor, omega^t)
+template <int DIR, int FLUX, bool ALPHA_ONLY, bool TAPE = false>
+DFK_HD void flux_body(const Mesh& m, const SchemeConsts& S, const double* __restrict__ lines,
+                                          long long ls, const double* __restrict__ gp, long long gs,
+                                          double* __restrict__ fr, long long fs, double dt, int ax, int ay, int mm,
+                         double* __restrict__ tape = nullptr) {
+    const FluxSite site = flux_site<DIR>(m, ax, ay, mm);
+    if (!site.ok) return;
+    flux_point<FLUX, ALPHA_ONLY, TAPE>(DIR, S, site, lines, ls, gp, gs, fr, fs, dt, mm, tape);
 }
 
 // one cell: residual, limited time derivative, stage combination, alpha product, positivity

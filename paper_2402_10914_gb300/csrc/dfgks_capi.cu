@@ -26,6 +26,7 @@ struct dfgks {
     double* As;            // ghosted alpha scratch for the residual input
     double* acc;           // dense [4][ny][nx]: S2O4 accumulator and transfer staging
     SweepBuffers B;
+    SweepBuffers By;       // the y-faces' face-line and Gauss-point records of the fused x/y sweeps
     DevState* st;          // device step state
     DevState* st_host;     // pinned mirror
     int* flag;             // device scratch flag
@@ -54,7 +55,9 @@ struct dfgks {
     // last segment, so the reverse pass recomputes only the earlier ones
     double* seg_arena;
     long long seg_cap;           // doubles allocated
-    int seg_k, seg_records, seg_tape, seg_gks, seg_last_kept;
+    int seg_k, seg_records, seg_tape, seg_gks;
+    int seg_slots;               // segments the arena holds
+    int seg_kept;                // trailing segments of the last forward pass still in the arena (0: none)
 };
 
 static dfgks_status cuda_status(cudaError_t e) {
@@ -114,7 +117,8 @@ static bool config_ok(const dfgks_config* c) {
 
 static void free_all(dfgks* h) {
     double* ptrs[] = {h->W[0], h->W[1], h->A[0], h->A[1], h->Ws, h->As, h->acc, h->B.lines, h->B.gp,
-                      h->B.flux[0], h->B.flux[1], h->dt_scratch, h->dts, h->adj_lines, h->adj_gp, h->adj_Wg};
+                      h->B.flux[0], h->B.flux[1], h->By.lines, h->By.gp, h->dt_scratch, h->dts, h->adj_lines,
+                      h->adj_gp, h->adj_Wg};
     for (double* p : ptrs) if (p) cudaFree(p);
     if (h->seg_arena) cudaFree(h->seg_arena);
     if (h->ck_W) cudaFree(h->ck_W);
@@ -206,6 +210,11 @@ extern "C" dfgks_status dfgks_create(const dfgks_config* cfg, void* stream, dfgk
     if (e == cudaSuccess) e = dalloc(h, &h->B.gp, (long long)GP_COUNT * h->B.gp_stride);
     if (e == cudaSuccess) e = dalloc(h, &h->B.flux[0], (long long)FR_COUNT * h->B.flux_stride[0]);
     if (e == cudaSuccess) e = dalloc(h, &h->B.flux[1], (long long)FR_COUNT * h->B.flux_stride[1]);
+    h->By = h->B;
+    h->By.lines = nullptr;
+    h->By.gp = nullptr;
+    if (e == cudaSuccess) e = dalloc(h, &h->By.lines, (long long)LR_COUNT * h->B.line_stride);
+    if (e == cudaSuccess) e = dalloc(h, &h->By.gp, (long long)GP_COUNT * h->B.gp_stride);
     if (e == cudaSuccess) e = dalloc(h, &h->dt_scratch, 4);
     if (e == cudaSuccess) { h->dts_cap = 1024; e = dalloc(h, &h->dts, h->dts_cap); }
     if (e == cudaSuccess) e = cudaMalloc((void**)&h->st, sizeof(DevState));
@@ -252,8 +261,7 @@ static dfgks_status compute_alpha0(dfgks* h, double* Wg, double* Ag) {
     launch_fill_value(Ag, h->mesh.plane, 1.0, h->stream);
     launch_fill_ghosts(h->mesh, Wg, nullptr, nullptr, h->stream);
     launch_set_scalar(h->dt_scratch, 1.0, h->stream);
-    for (int dir = 0; dir < 2; ++dir)
-        launch_sweep(dir, h->mesh, h->S, 1, true, Wg, Ag, h->dt_scratch, h->B, nullptr, nullptr, h->stream);
+    launch_sweep_xy(h->mesh, h->S, 1, true, Wg, Ag, h->dt_scratch, h->B, h->By, nullptr, nullptr, h->stream);
     UpdateArgs a;
     memset(&a, 0, sizeof(a));
     a.alpha_out = Ag;
@@ -348,25 +356,26 @@ static void enqueue_step(dfgks* h, int s, double dt, int flux, double t_end, int
                 Bu[q].flux[0] = rec[2 * q].flux[0]; Bu[q].flux_stride[0] = rec[2 * q].flux_stride[0];
                 Bu[q].flux[1] = rec[2 * q + 1].flux[1]; Bu[q].flux_stride[1] = rec[2 * q + 1].flux_stride[1];
             }
-        for (int d = 0; d < 2; ++d) launch_sweep(d, m, S, flux, false, in, ain, dtp, rec ? rec[d] : h->B, h->st, halt, st, T);
+        if (rec) launch_sweep_xy(m, S, flux, false, in, ain, dtp, rec[0], rec[1], h->st, halt, st, T);
+        else launch_sweep_xy(m, S, flux, false, in, ain, dtp, h->B, h->By, h->st, halt, st, T);
         a.Win = in; a.Wout = h->Ws; a.acc = h->acc;
         launch_update(UM_S2O4_1, m, S, a, Bu[0], dtp, h->st, halt, st, T);
         if (Wstar_store) launch_ghosted_to_dense(m, h->Ws, 4, Wstar_store, st);
         launch_fill_ghosts(m, h->Ws, nullptr, halt, st, T);
-        for (int d = 0; d < 2; ++d)
-            launch_sweep(d, m, S, flux, false, h->Ws, ain, dtp, rec ? rec[2 + d] : h->B, h->st, halt, st, T);
+        if (rec) launch_sweep_xy(m, S, flux, false, h->Ws, ain, dtp, rec[2], rec[3], h->st, halt, st, T);
+        else launch_sweep_xy(m, S, flux, false, h->Ws, ain, dtp, h->B, h->By, h->st, halt, st, T);
         a.Win = h->Ws; a.Wout = out; a.alpha_out = aout;
         launch_update(UM_S2O4_2, m, S, a, Bu[1], dtp, h->st, halt, st, T);
     } else {
-        for (int d = 0; d < 2; ++d) launch_sweep(d, m, S, flux, false, in, ain, dtp, h->B, h->st, halt, st, T);
+        launch_sweep_xy(m, S, flux, false, in, ain, dtp, h->B, h->By, h->st, halt, st, T);
         a.Win = in; a.Wout = h->Ws;
         launch_update(UM_RK_1, m, S, a, h->B, dtp, h->st, halt, st, T);
         launch_fill_ghosts(m, h->Ws, nullptr, halt, st, T);
-        for (int d = 0; d < 2; ++d) launch_sweep(d, m, S, flux, false, h->Ws, ain, dtp, h->B, h->st, halt, st, T);
+        launch_sweep_xy(m, S, flux, false, h->Ws, ain, dtp, h->B, h->By, h->st, halt, st, T);
         a.Wn = in; a.Win = h->Ws; a.Wout = out;
         launch_update(UM_RK_2, m, S, a, h->B, dtp, h->st, halt, st, T);
         launch_fill_ghosts(m, out, nullptr, halt, st, T);
-        for (int d = 0; d < 2; ++d) launch_sweep(d, m, S, flux, false, out, ain, dtp, h->B, h->st, halt, st, T);
+        launch_sweep_xy(m, S, flux, false, out, ain, dtp, h->B, h->By, h->st, halt, st, T);
         a.Wn = in; a.Win = out; a.Wout = out; a.alpha_out = aout;
         launch_update(UM_RK_3, m, S, a, h->B, dtp, h->st, halt, st, T);
     }
@@ -528,11 +537,17 @@ static void record_sets(const dfgks* h, double* base, bool tape, bool gks, Sweep
 // flux tapes when those fit too).
 struct SegArena { double* W; double* A; double* Ws; double* recs; bool tape, gks; long long rec_step; };
 
-// the arena's layout as last decided (seg_k, seg_records, seg_tape, seg_gks)
-static void arena_view(const dfgks* h, SegArena& a) {
+// doubles of one segment slot: W^s, alpha^s, W* of k steps and, when kept, their records
+static long long slot_doubles(const dfgks* h, int k, bool records, bool tape, bool gks) {
+    const long long N = (long long)h->mesh.nx * h->mesh.ny;
+    return (long long)k * (9 * N) + (records ? (long long)k * record_doubles_per_step(h, tape, gks) : 0);
+}
+
+// slot `slot` of the arena in the layout last decided (seg_k, seg_records, seg_tape, seg_gks)
+static void arena_view(const dfgks* h, SegArena& a, int slot = 0) {
     const long long N = (long long)h->mesh.nx * h->mesh.ny, N4 = 4 * N;
     const int k = h->seg_k;
-    a.W = h->seg_arena;
+    a.W = h->seg_arena + (long long)slot * slot_doubles(h, k, h->seg_records != 0, h->seg_tape != 0, h->seg_gks != 0);
     a.A = a.W + (long long)k * N4;
     a.Ws = a.A + (long long)k * N;
     a.recs = h->seg_records ? a.Ws + (long long)k * N4 : nullptr;
@@ -540,37 +555,44 @@ static void arena_view(const dfgks* h, SegArena& a) {
     a.rec_step = record_doubles_per_step(h, a.tape, a.gks);
 }
 
-static dfgks_status ensure_segment_arena(dfgks* h, int k, int flux, SegArena& a) {
-    const Mesh& m = h->mesh;
-    const long long N = (long long)m.nx * m.ny, N4 = 4 * N;
+// Lay out the arena for segments of k steps: the records (with tapes if they fit) of as many as
+// `want` segments within 60 % of the free device memory, at least one slot.  The forward pass
+// keeps its last segments there, so the reverse pass recomputes only the ones that did not fit.
+static dfgks_status ensure_segment_arena(dfgks* h, int k, int flux, int want, SegArena& a) {
     const bool gks = flux == DFGKS_FLUX_GKS;
-    const long long base = (long long)k * (2 * N4 + N);
     size_t free_b = 0, total_b = 0;
     cudaMemGetInfo(&free_b, &total_b);
-    const double budget = 0.5 * ((double)free_b + (double)h->seg_cap * sizeof(double));
-    auto need = [&](int records, bool tape) {
-        return base + (records ? (long long)k * record_doubles_per_step(h, tape, gks) : 0);
-    };
+    const double budget = 0.6 * ((double)free_b + (double)h->seg_cap * sizeof(double));
     int records = 1;
     bool tape = true;
-    if ((double)need(1, true) * sizeof(double) > budget) tape = false;
-    if ((double)need(1, false) * sizeof(double) > budget) records = 0;
-    const long long want = need(records, tape);
-    if (want > h->seg_cap) {
+    if ((double)slot_doubles(h, k, true, true, gks) * sizeof(double) > budget) tape = false;
+    if ((double)slot_doubles(h, k, true, false, gks) * sizeof(double) > budget) records = 0;
+    const long long per = slot_doubles(h, k, records, tape, gks);
+    int slots = (int)(budget / ((double)per * sizeof(double)));
+    if (slots > want) slots = want;
+    if (slots < 1) slots = 1;
+    const long long need = (long long)slots * per;
+    if (need > h->seg_cap) {
         if (h->seg_arena) { cudaFree(h->seg_arena); h->bytes -= (unsigned long long)h->seg_cap * sizeof(double); }
         h->seg_arena = nullptr;
         h->seg_cap = 0;
-        if (dalloc(h, &h->seg_arena, want) != cudaSuccess) {
+        if (dalloc(h, &h->seg_arena, need) != cudaSuccess) {
             cudaGetLastError();
-            if (!records || dalloc(h, &h->seg_arena, base) != cudaSuccess) { cudaGetLastError(); return DFGKS_ENOMEM; }
+            slots = 1;
+            const long long one = slot_doubles(h, k, false, false, gks);
+            if (dalloc(h, &h->seg_arena, one) != cudaSuccess) { cudaGetLastError(); return DFGKS_ENOMEM; }
             records = 0;
-            h->seg_cap = base;
+            tape = false;
+            h->seg_cap = one;
         } else {
-            h->seg_cap = want;
+            h->seg_cap = need;
         }
+    } else {
+        slots = (int)(h->seg_cap / per);
+        if (slots > want) slots = want;
     }
-    h->seg_k = k; h->seg_records = records; h->seg_tape = tape; h->seg_gks = gks;
-    arena_view(h, a);
+    h->seg_k = k; h->seg_records = records; h->seg_tape = tape; h->seg_gks = gks; h->seg_slots = slots;
+    arena_view(h, a, 0);
     return DFGKS_OK;
 }
 
@@ -603,21 +625,24 @@ static dfgks_status forward_checkpointed(dfgks* h, const double* W0, int n, cons
         h->dts_cap = n;
     }
     SegArena a;
-    h->seg_last_kept = 0;
-    dfgks_status r = ensure_segment_arena(h, k, flux, a);
+    h->seg_kept = 0;
+    dfgks_status r = ensure_segment_arena(h, k, flux, nseg, a);
     if (r) return r;
     r = load_state(h, W0, nullptr, 0.0, 0, 1);
     if (r) return r;
     const int cur0 = h->cur;
-    const int last0 = (nseg - 1) * k;          // the last segment's steps fill the arena as they run
+    // the last `kept` segments fill the arena's slots as they run (segment nseg - kept in slot 0)
+    const int kept = h->seg_slots < nseg ? h->seg_slots : nseg;
+    const int first_kept = nseg - kept;
     for (int s = 0; s < n; ++s) {
         const int c = (cur0 + s) & 1;
         if (s % k == 0) {
             launch_ghosted_to_dense(m, h->W[c], 4, h->ck_W + (long long)(s / k) * N4, h->stream);
             launch_ghosted_to_dense(m, h->A[c], 1, h->ck_A + (long long)(s / k) * N, h->stream);
         }
-        if (s >= last0) {
-            const int j = s - last0;
+        if (s / k >= first_kept) {
+            arena_view(h, a, s / k - first_kept);
+            const int j = s % k;
             launch_ghosted_to_dense(m, h->W[c], 4, a.W + (long long)j * N4, h->stream);
             launch_ghosted_to_dense(m, h->A[c], 1, a.A + (long long)j * N, h->stream);
             SweepBuffers rec[4];
@@ -637,7 +662,7 @@ static dfgks_status forward_checkpointed(dfgks* h, const double* W0, int n, cons
     if (h->st_host->err || done != n) return DFGKS_ENONPOS;
     CK(cudaMemcpy(h->ck_dts, h->dts, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost));
     h->ck_n = n; h->ck_k = k; h->ck_flux = flux;
-    h->seg_last_kept = 1;
+    h->seg_kept = kept;
     h->ck_gen = ++h->gen;
     return DFGKS_OK;
 }
@@ -651,13 +676,14 @@ static dfgks_status backward_checkpointed(dfgks* h, const double* WT_bar, double
     const long long N = (long long)m.nx * m.ny, N4 = 4 * N;
     const int n = h->ck_n, k = h->ck_k, flux = h->ck_flux, nseg = (n + k - 1) / k;
     const double* dts = h->ck_dts;
-    // the last segment's states and records are still in the arena if the forward pass kept them
-    const bool kept = h->seg_last_kept && h->seg_arena && h->seg_k == k && h->seg_gks == (flux == DFGKS_FLUX_GKS);
-    h->seg_last_kept = 0;                       // the recompute below overwrites the arena
+    // the last segments' states and records are still in the arena if the forward pass kept them
+    const int kept = (h->seg_arena && h->seg_k == k && h->seg_gks == (flux == DFGKS_FLUX_GKS)) ? h->seg_kept : 0;
+    h->seg_kept = 0;                            // the recompute below overwrites the arena
+    const int first_kept = nseg - kept;
     SegArena a;
     dfgks_status r = DFGKS_OK;
-    if (kept) arena_view(h, a);                 // the layout the forward pass wrote
-    else r = ensure_segment_arena(h, k, flux, a);
+    if (kept) arena_view(h, a, 0);              // the layout the forward pass wrote
+    else r = ensure_segment_arena(h, k, flux, 1, a);
     if (r) return r;
     std::vector<double*> bufs;
     auto get = [&](long long cnt) -> double* {
@@ -688,7 +714,10 @@ static dfgks_status backward_checkpointed(dfgks* h, const double* WT_bar, double
         CK(cudaMemcpyAsync(Wb, WT_bar, (size_t)N4 * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
         for (int seg = nseg - 1; seg >= 0 && r == DFGKS_OK; --seg) {
             const int s0 = seg * k, s1 = (s0 + k < n) ? s0 + k : n;
-            if (!(kept && seg == nseg - 1)) {
+            // a kept segment sits in its slot; the others are recomputed into slot 0, which the
+            // kept segments (all later than any recomputed one) have already been reversed out of
+            arena_view(h, a, seg >= first_kept ? seg - first_kept : 0);
+            if (seg < first_kept) {
                 // recompute the segment from its checkpoint, keeping W^s, alpha^s, W* and the records
                 launch_dense_to_ghosted(m, h->ck_W + (long long)seg * N4, 4, h->W[h->cur], h->stream);
                 launch_dense_to_ghosted(m, h->ck_A + (long long)seg * N, 1, h->A[h->cur], h->stream);

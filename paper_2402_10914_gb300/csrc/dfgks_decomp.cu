@@ -36,7 +36,8 @@ struct Block {
     double* A[2];
     double* Ws;
     double* acc;          // dense [4][ny][nx]: S2O4 accumulator and transfer staging
-    SweepBuffers B;
+    SweepBuffers B;       // x-faces' records and both flux record sets
+    SweepBuffers By;      // y-faces' face-line and Gauss-point records (fused x/y sweeps)
 };
 
 long long round4(long long n) { return (n + 3) & ~3LL; }
@@ -259,6 +260,9 @@ extern "C" DFGKS_API dfgks_status dfgks_decomp_create(const dfgks_config* cfg, i
         if (e == cudaSuccess) e = dalloc(d, &k.B.gp, (long long)GP_COUNT * k.B.gp_stride);
         if (e == cudaSuccess) e = dalloc(d, &k.B.flux[0], (long long)FR_COUNT * k.B.flux_stride[0]);
         if (e == cudaSuccess) e = dalloc(d, &k.B.flux[1], (long long)FR_COUNT * k.B.flux_stride[1]);
+        k.By = k.B;
+        if (e == cudaSuccess) e = dalloc(d, &k.By.lines, (long long)LR_COUNT * k.B.line_stride);
+        if (e == cudaSuccess) e = dalloc(d, &k.By.gp, (long long)GP_COUNT * k.B.gp_stride);
         if (e == cudaSuccess) {
             launch_fill_value(k.W[0], 4 * m.plane, 1.0, d->stream);
             launch_fill_value(k.W[1], 4 * m.plane, 1.0, d->stream);
@@ -317,8 +321,7 @@ extern "C" DFGKS_API dfgks_status dfgks_decomp_set_ic(dfgks_decomp* d, const dou
     for (Block& b : d->blk) launch_fill_value(b.A[0], b.m.plane, 1.0, d->stream);
     DCK(halo(d, 0, 0, false));
     for (Block& b : d->blk) {
-        for (int dir = 0; dir < 2; ++dir)
-            launch_sweep(dir, b.m, d->S, 1, true, b.W[0], b.A[0], d->one, b.B, nullptr, nullptr, d->stream);
+        launch_sweep_xy(b.m, d->S, 1, true, b.W[0], b.A[0], d->one, b.B, b.By, nullptr, nullptr, d->stream);
         UpdateArgs a;
         memset(&a, 0, sizeof(a));
         a.alpha_out = b.A[0];
@@ -343,7 +346,7 @@ static cudaError_t enqueue_decomp_step(dfgks_decomp* d, int s, int in, int flux,
     cudaError_t e = halo(d, 0, in, true);
     if (e != cudaSuccess) return e;
     for (Block& b : d->blk) {
-        for (int dir = 0; dir < 2; ++dir) launch_sweep(dir, b.m, d->S, flux, false, b.W[in], b.A[in], dtp, b.B, ds, halt, st);
+        launch_sweep_xy(b.m, d->S, flux, false, b.W[in], b.A[in], dtp, b.B, b.By, ds, halt, st);
         UpdateArgs a;
         memset(&a, 0, sizeof(a));
         a.Win = b.W[in]; a.Wout = b.Ws; a.acc = b.acc;
@@ -352,7 +355,7 @@ static cudaError_t enqueue_decomp_step(dfgks_decomp* d, int s, int in, int flux,
     e = halo(d, 1, in, false);
     if (e != cudaSuccess) return e;
     for (Block& b : d->blk) {
-        for (int dir = 0; dir < 2; ++dir) launch_sweep(dir, b.m, d->S, flux, false, b.Ws, b.A[in], dtp, b.B, ds, halt, st);
+        launch_sweep_xy(b.m, d->S, flux, false, b.Ws, b.A[in], dtp, b.B, b.By, ds, halt, st);
         UpdateArgs a;
         memset(&a, 0, sizeof(a));
         a.Win = b.Ws; a.Wout = b.W[out]; a.acc = b.acc; a.alpha_out = b.A[out];

@@ -139,6 +139,12 @@ void launch_end_step(DevState* st, double t_end, cudaStream_t s, KernelTimer* T 
 void launch_sweep(int dir, const Mesh& m, const SchemeConsts& S, int flux, bool alpha_only,
                   const double* W, const double* alpha, const double* dtp, const SweepBuffers& B,
                   DevState* st, const int* halt, cudaStream_t s, KernelTimer* T = nullptr);
+// both directions in one launch per kernel class: the x-faces use Bx's face-line and Gauss-point
+// records, flux[0] and tapes, the y-faces By's records, flux[1] and tapes (with tapes in both or
+// in neither)
+void launch_sweep_xy(const Mesh& m, const SchemeConsts& S, int flux, bool alpha_only, const double* W,
+                     const double* alpha, const double* dtp, const SweepBuffers& Bx, const SweepBuffers& By,
+                     DevState* st, const int* halt, cudaStream_t s, KernelTimer* T = nullptr);
 void launch_update(int mode, const Mesh& m, const SchemeConsts& S, const UpdateArgs& a, const SweepBuffers& B,
                    const double* dtp, DevState* st, const int* halt, cudaStream_t s, KernelTimer* T = nullptr);
 void launch_dense_to_ghosted(const Mesh& m, const double* dense, int ncomp, double* ghosted, cudaStream_t s);

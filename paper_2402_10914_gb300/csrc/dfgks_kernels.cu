@@ -141,6 +141,124 @@ __global__ void __launch_bounds__(128) k_flux(Mesh m, SchemeConsts S, const doub
                                            blockIdx.y, tape);
 }
 
+// ---------------------------------------------------------------------------------------------
+// Both directions of a sweep in one launch: blocks [0, nb0) take the x-faces' index space, the
+// rest the y-faces', each on its own face-line and Gauss-point buffers.  The two halves are
+// independent; one launch of twice the blocks evens out the last round of blocks over the SMs and
+// saves three launches per stage.
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ void sweep_at(int b, int lx, int& ax, int& ay) {
+    const int i = b * (int)blockDim.x + (int)threadIdx.x;
+    ax = i % lx;
+    ay = i / lx;
+}
+
+template <bool TAPE>
+__global__ void __launch_bounds__(128, 3) k_lines_xy(Mesh m, SchemeConsts S, const double* __restrict__ W,
+                                                  const double* __restrict__ alpha, double* __restrict__ lines0,
+                                                  double* __restrict__ lines1, long long ls, double* __restrict__ ltape0,
+                                                  double* __restrict__ ltape1, int nb0, DevState* st, const int* halt) {
+    if (halted(halt)) return;
+    int ax, ay, ndf;
+    if ((int)blockIdx.x < nb0) {
+        sweep_at(blockIdx.x, lines_lx<0>(m), ax, ay);
+        ndf = lines_body<0, TAPE>(m, S, W, alpha, lines0, ls, ax, ay, ltape0);
+    } else {
+        sweep_at(blockIdx.x - nb0, lines_lx<1>(m), ax, ay);
+        ndf = lines_body<1, TAPE>(m, S, W, alpha, lines1, ls, ax, ay, ltape1);
+    }
+    if (st) warp_count_add(&st->df_normal, ndf);
+}
+
+template <bool TAPE>
+__global__ void __launch_bounds__(128) k_faces_xy(Mesh m, SchemeConsts S, const double* __restrict__ W,
+                                               const double* __restrict__ alpha, const double* __restrict__ lines0,
+                                               const double* __restrict__ lines1, long long ls, double* __restrict__ gp0,
+                                               double* __restrict__ gp1, long long gs, double* __restrict__ ftape0,
+                                               double* __restrict__ ftape1, int nb0, DevState* st, const int* halt) {
+    if (halted(halt)) return;
+    int nfb, ax, ay, ndf;
+    if ((int)blockIdx.x < nb0) {
+        sweep_at(blockIdx.x, faces_lx<0>(m), ax, ay);
+        ndf = faces_body<0, TAPE>(m, S, W, alpha, lines0, ls, gp0, gs, ax, ay, blockIdx.y, nfb, ftape0);
+    } else {
+        sweep_at(blockIdx.x - nb0, faces_lx<1>(m), ax, ay);
+        ndf = faces_body<1, TAPE>(m, S, W, alpha, lines1, ls, gp1, gs, ax, ay, blockIdx.y, nfb, ftape1);
+    }
+    if (st) { warp_count_add(&st->df_tangential, ndf); warp_count_add(&st->fallbacks, nfb); }
+}
+
+template <int FLUX, bool ALPHA_ONLY, bool TAPE = false>
+__global__ void __launch_bounds__(128) k_flux_xy(Mesh m, SchemeConsts S, const double* __restrict__ lines0,
+                                              const double* __restrict__ lines1, long long ls,
+                                              const double* __restrict__ gp0, const double* __restrict__ gp1,
+                                              long long gs, double* __restrict__ fr0, long long fs0,
+                                              double* __restrict__ fr1, long long fs1, double* __restrict__ tape0,
+                                              double* __restrict__ tape1, const double* dtp, int nb0, const int* halt) {
+    if (halted(halt)) return;
+    const double dt = ALPHA_ONLY ? 0.0 : *dtp;
+    // the direction selects the records and the index map; the flux arithmetic is inlined once
+    int ax, ay, dir;
+    FluxSite site;
+    if ((int)blockIdx.x < nb0) {
+        sweep_at(blockIdx.x, faces_lx<0>(m), ax, ay);
+        site = flux_site<0>(m, ax, ay, blockIdx.y);
+        dir = 0;
+    } else {
+        sweep_at(blockIdx.x - nb0, faces_lx<1>(m), ax, ay);
+        site = flux_site<1>(m, ax, ay, blockIdx.y);
+        dir = 1;
+    }
+    if (!site.ok) return;
+    flux_point<FLUX, ALPHA_ONLY, TAPE>(dir, S, site, dir == 0 ? lines0 : lines1, ls, dir == 0 ? gp0 : gp1, gs,
+                                       dir == 0 ? fr0 : fr1, dir == 0 ? fs0 : fs1, dt, blockIdx.y,
+                                       dir == 0 ? tape0 : tape1);
+}
+
+void launch_sweep_xy(const Mesh& m, const SchemeConsts& S, int flux, bool alpha_only, const double* W,
+                     const double* alpha, const double* dtp, const SweepBuffers& Bx, const SweepBuffers& By,
+                     DevState* st, const int* halt, cudaStream_t s, KernelTimer* T) {
+    const dim3 blk(128);
+    const int nl0 = (int)sweep_blocks(lines_lx<0>(m), lines_ly<0>(m)), nl1 = (int)sweep_blocks(lines_lx<1>(m), lines_ly<1>(m));
+    const int nf0 = (int)sweep_blocks(faces_lx<0>(m), faces_ly<0>(m)), nf1 = (int)sweep_blocks(faces_lx<1>(m), faces_ly<1>(m));
+    const bool tape = Bx.ltape != nullptr;      // both directions' record sets carry tapes or neither
+    const long long ls = Bx.line_stride, gs = Bx.gp_stride;
+    if (T) T->begin(KK_LINES);
+    if (tape)
+        k_lines_xy<true><<<dim3(nl0 + nl1), blk, 0, s>>>(m, S, W, alpha, Bx.lines, By.lines, ls, Bx.ltape, By.ltape, nl0,
+                                                         st, halt);
+    else
+        k_lines_xy<false><<<dim3(nl0 + nl1), blk, 0, s>>>(m, S, W, alpha, Bx.lines, By.lines, ls, nullptr, nullptr, nl0,
+                                                          st, halt);
+    if (T) T->end(KK_LINES, 1);
+    const dim3 gf(nf0 + nf1, 2);
+    if (T) T->begin(KK_FACES);
+    if (tape)
+        k_faces_xy<true><<<gf, blk, 0, s>>>(m, S, W, alpha, Bx.lines, By.lines, ls, Bx.gp, By.gp, gs, Bx.ftape,
+                                            By.ftape, nf0, st, halt);
+    else
+        k_faces_xy<false><<<gf, blk, 0, s>>>(m, S, W, alpha, Bx.lines, By.lines, ls, Bx.gp, By.gp, gs, nullptr,
+                                             nullptr, nf0, st, halt);
+    if (T) T->end(KK_FACES, 1);
+    double* f0 = Bx.flux[0];
+    double* f1 = By.flux[1];
+    const long long fs0 = Bx.flux_stride[0], fs1 = By.flux_stride[1];
+    if (T) T->begin(KK_FLUX);
+    if (alpha_only)
+        k_flux_xy<1, true><<<gf, blk, 0, s>>>(m, S, Bx.lines, By.lines, ls, Bx.gp, By.gp, gs, f0, fs0, f1, fs1,
+                                               nullptr, nullptr, dtp, nf0, halt);
+    else if (flux == 0 && Bx.tape[0])        // GKS forward that also tapes its intermediates for a reverse sweep
+        k_flux_xy<0, false, true><<<gf, blk, 0, s>>>(m, S, Bx.lines, By.lines, ls, Bx.gp, By.gp, gs, f0, fs0, f1, fs1,
+                                                     Bx.tape[0], By.tape[1], dtp, nf0, halt);
+    else if (flux == 0)
+        k_flux_xy<0, false><<<gf, blk, 0, s>>>(m, S, Bx.lines, By.lines, ls, Bx.gp, By.gp, gs, f0, fs0, f1, fs1,
+                                                nullptr, nullptr, dtp, nf0, halt);
+    else
+        k_flux_xy<1, false><<<gf, blk, 0, s>>>(m, S, Bx.lines, By.lines, ls, Bx.gp, By.gp, gs, f0, fs0, f1, fs1,
+                                                nullptr, nullptr, dtp, nf0, halt);
+    if (T) T->end(KK_FLUX, 1);
+}
+
 template <int DIR>
 static void sweep_dir(const Mesh& m, const SchemeConsts& S, int flux, bool alpha_only, const double* W,
                       const double* alpha, const double* dtp, const SweepBuffers& B, DevState* st,

@@ -4,6 +4,10 @@ import sys
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+# the oracle's OpenMP threads sleep between parallel regions instead of spinning: many tests run it
+# on small meshes with thousands of short regions, where spinning threads compete with each other
+# and with whatever else runs on the host (set before the oracle library loads its runtime)
+os.environ.setdefault("OMP_WAIT_POLICY", "PASSIVE")
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 

@@ -172,6 +172,7 @@ def test_c4_vortex_gradient_against_finite_differences():
         rng = np.random.default_rng(11)
         cells = rng.choice(s.nx * s.ny, size=32, replace=False)
         worst = 0.0
+        entries = []
         for q in cells:
             j, i = divmod(int(q), s.nx)
             for k in range(4):
@@ -181,7 +182,16 @@ def test_c4_vortex_gradient_against_finite_differences():
                 Wm[k, j, i] -= h
                 fd = sum_rho2_difference(run_fixed(sol, Wp, dts), run_fixed(sol, Wm, dts)) / (2 * h)
                 worst = max(worst, abs(g[k, j, i] - fd))
-    assert worst <= 1e-6 * np.abs(g).max(), (worst, np.abs(g).max())
+                entries.append((abs(g[k, j, i]), abs(g[k, j, i] - fd)))
+    gmax = np.abs(g).max()
+    assert worst <= 1e-6 * gmax, (worst, gmax)
+    # per entry: every entry of at least 5 % of the largest one within 1e-6 of itself; smaller
+    # entries are reported (their difference quotients' rounding, ~3e-8, is of their size scale)
+    big = [(a, e) for a, e in entries if a >= 0.05 * gmax]
+    assert big and all(e <= 1e-6 * a for a, e in big), max(e / a for a, e in big)
+    rel = sorted(e / a for a, e in entries if a > 0.0)
+    print("C4 gradient vs central differences: %d entries >= 5%% of max, worst relative %.2e; all %d entries: "
+          "median relative %.2e, max %.2e" % (len(big), max(e / a for a, e in big), len(rel), rel[len(rel) // 2], rel[-1]))
 
 
 def test_checkpointed_forward_and_backward():

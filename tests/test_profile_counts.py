@@ -25,7 +25,7 @@ def test_flux_kernel_counts_belong_to_the_current_sources():
 def test_stale_counts_are_not_used(tmp_path):
     bench = _bench()
     src = open(bench.FLUX_PROFILE).read().replace('"source_hash": "', '"source_hash": "0')
-    p = tmp_path / "stale.md"
+    p = tmp_path / "stale.txt"
     p.write_text(src)
     counts, why = bench.profile_counts(str(p))
     assert counts is None and "changed" in why
