@@ -462,9 +462,9 @@ def bench_robustness(args):
     from paper_2402_10914_gb300 import _lib, inputs as I
     from paper_2402_10914_gb300.solver import Solver
 
-    def survives(make, ma, flux, thres, fb):
+    def survives(make, ma, flux, thres, fb, dfs=0):
         w = make(ma, flux=flux)
-        s = w.settings.with_(alpha_thres=thres, gp_fallback=fb)
+        s = w.settings.with_(alpha_thres=thres, gp_fallback=fb, df_states=dfs)
         with Solver(s) as sol:
             try:
                 sol.set_ic(w.W0)
@@ -483,17 +483,19 @@ def bench_robustness(args):
                        ("hurricane-like (400 x 400, 50 steps)", I.hurricane),
                        ("planar rarefactions (400 x 400, t = 0.15)", I.planar_rarefaction)):
         for flux, fname in ((I.GKS, "GKS S2O4"), (I.LF, "L-F SSP-RK3")):
-            for thres, rname in ((0.5, "hybrid"), (0.0, "WENO-AO")):
+            # the hybrid with the paper's DF states, plain WENO-AO, and the hybrid with the DF factor
+            # taken from the cell averages beside each face (df_states = 1, not the paper's reading)
+            for thres, rname, dfs in ((0.5, "hybrid", 0), (0.0, "WENO-AO", 0), (0.5, "hybrid, DF from cell averages", 1)):
                 for fb in (0, 1):
                     lo, hi = (0.5 if make is I.planar_rarefaction else 1.0), 256.0
-                    if not survives(make, lo, flux, thres, fb):
+                    if not survives(make, lo, flux, thres, fb, dfs):
                         res = "< %g" % lo
-                    elif survives(make, hi, flux, thres, fb):
+                    elif survives(make, hi, flux, thres, fb, dfs):
                         res = ">= 256"
                     else:
                         for _ in range(12):
                             mid = math.sqrt(lo * hi)
-                            if survives(make, mid, flux, thres, fb):
+                            if survives(make, mid, flux, thres, fb, dfs):
                                 lo = mid
                             else:
                                 hi = mid

@@ -69,6 +69,10 @@ typedef struct dfgks_config {
     int time_scheme;               /* dfgks_time_scheme */
     int dt_rule;                   /* CFL bound per cell (Alg. 1 gives no formula): 0 min(dx/(|U|+c), dy/(|V|+c)),
                                       1 1/((|U|+c)/dx + (|V|+c)/dy) */
+    int df_states;                 /* the left and right states of a Gauss point's DF factor (Sect. 3.2):
+                                      0 the reconstructed Gauss-point states (the paper's interface
+                                      reconstruction values; default), 1 the cell averages of the two
+                                      cells beside the face (an alternative, not the paper's reading) */
 } dfgks_config;
 
 typedef struct dfgks dfgks;        /* opaque; owns every device buffer it uses */

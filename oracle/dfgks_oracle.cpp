@@ -69,6 +69,8 @@ typedef struct {
     int gp_fallback;      // 1: non-physical Gauss-point states fall back to the cell average
     int time_scheme;      // 0: S2O4, 1: SSP-RK3
     int dt_rule;          // 0: per-direction minimum, 1: CFL / max((|U|+c)/dx + (|V|+c)/dy)
+    int df_states;        // left/right states of a Gauss point's DF factor: 0 the reconstructed
+                          // Gauss-point states, 1 the cell averages beside the face
 } oracle_cfg;
 
 typedef struct {
@@ -884,6 +886,13 @@ static FaceRec<R> face_flux(const Ctx& C, const Field<R>& F, const Dir& d, int f
     for (int s = 0; s < 2; ++s) for (int m = 0; m < 2; ++m) fr.nfallback += sides[s].fallback[m] ? 1 : 0;
     if (sides_out) { sides_out[0] = sides[0]; sides_out[1] = sides[1]; }
     for (int m = 0; m < 2; ++m) fr.alpha_gp[m] = df_alpha_point(sides[0].W[m], sides[1].W[m], cf.gamma);
+    if (cf.df_states == 1) {
+        // the alternative reading: the states on either side of the Gauss point are the cell averages
+        R Wl[4], Wr[4];
+        cell_local(F, d, f - 1, t, Wl);
+        cell_local(F, d, f, t, Wr);
+        for (int m = 0; m < 2; ++m) fr.alpha_gp[m] = df_alpha_point(Wl, Wr, cf.gamma);
+    }
     for (int k = 0; k < 4; ++k) { fr.F[k] = R(0.0); fr.dtF[k] = R(0.0); }
     fr.omega = cf.time_limiter ? lines[(size_t)(t + 2) * line_stride + f].tl_alpha : R(1.0);
     if (!want_flux) return fr;

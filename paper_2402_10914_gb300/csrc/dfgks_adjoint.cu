@@ -55,7 +55,7 @@ DFK_HD void ka_flux_body(const Mesh& m, const SchemeConsts& S, const AdjointArgs
             if (a.dtLtb) ddLt[k] += sg * a.dtLtb[k * dplane + c];
         }
     }
-    const double idn = 1.0 / g.dn;
+    const double idn = g.idn;
     const double om = fr[FR_OMEGA * fs + fid];
     double Fb[4], dFb[4];
     for (int k = 0; k < 4; ++k) {
@@ -124,7 +124,7 @@ DFK_HD void ka_faces_body(const Mesh& m, const SchemeConsts& S, const double* __
     double al[3];
     for (int b = 0; b < 3; ++b) al[b] = alpha[g.cell(m, ncell, t + Geo<DIR>::sigma * (b - 1))];
     const bool df = fmax(fmax(al[0], al[1]), al[2]) < S.alpha_thres;
-    const double idt = 1.0 / g.dtan;
+    const double idt = g.idtan;
     const long long e = (long long)side * g.nfaces() + g.face(f, t);
     const int fbits = (int)gp[GP_FB * gs + e];
     // Gauss-point adjoints -> characteristic value and tangential-slope adjoints (R^T, independent
@@ -225,7 +225,7 @@ DFK_HD void ka_lines_body(const Mesh& m, const SchemeConsts& S, const double* __
     for (int s = 0; s < 6; ++s) project(B, Wc[s], Q[s]);
     const bool dfL = fmax(fmax(al[1], al[2]), al[3]) < S.alpha_thres;
     const bool dfR = fmax(fmax(al[2], al[3]), al[4]) < S.alpha_thres;
-    const double idn = 1.0 / g.dn;
+    const double idn = g.idn;
     // the reconstruction that set the limiter weight in the forward pass (2k + side) and the
     // weight's adjoint
     const int tlk = S.time_limiter ? (int)lines[LR_TLK * ls + li] : -1;

@@ -347,7 +347,8 @@ static bool batch_config_ok(const dfgks_config* c) {
     // periodic wrap and wall mirror both copy G interior cells into the ghost layers
     if ((c->bc_xlo != 1 || c->bc_xhi != 1) && c->nx < G) return false;
     if ((c->bc_ylo != 1 || c->bc_yhi != 1) && c->ny < G) return false;
-    return c->time_scheme == 0 && (c->tau_reading == 0 || c->tau_reading == 1) && (c->dt_rule == 0 || c->dt_rule == 1);
+    return c->time_scheme == 0 && (c->tau_reading == 0 || c->tau_reading == 1) && (c->dt_rule == 0 || c->dt_rule == 1)
+        && (c->df_states == 0 || c->df_states == 1);
 }
 
 extern "C" DFGKS_API dfgks_status dfgks_batch_create(const dfgks_config* cfgs, const int* flux, int np, void* stream,
@@ -387,6 +388,7 @@ extern "C" DFGKS_API dfgks_status dfgks_batch_create(const dfgks_config* cfgs, c
         m.plane = (long long)m.P * m.NYg;
         m.dx = (c->x1 - c->x0) / c->nx;
         m.dy = (c->y1 - c->y0) / c->ny;
+        m.rdx = 1.0 / m.dx; m.rdy = 1.0 / m.dy;
         m.bc[0] = c->bc_xlo; m.bc[1] = c->bc_xhi; m.bc[2] = c->bc_ylo; m.bc[3] = c->bc_yhi;
         m.dt_rule = c->dt_rule;
         SchemeConsts& S = q.S;
@@ -396,6 +398,7 @@ extern "C" DFGKS_API dfgks_status dfgks_batch_create(const dfgks_config* cfgs, c
         S.inv_d3 = 1.0 / c->dH;
         S.eps = c->eps; S.alpha_thres = c->alpha_thres; S.C1 = c->C1; S.C2 = c->C2;
         S.time_limiter = c->time_limiter; S.tau_reading = c->tau_reading; S.gp_fallback = c->gp_fallback;
+        S.df_states = c->df_states;
         q.flux = flux[p];
         cfl[p] = c->cfl;
         const long long nfx = (long long)(m.nx + 1) * m.ny, nfy = (long long)(m.ny + 1) * m.nx;

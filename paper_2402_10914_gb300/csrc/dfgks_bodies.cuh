@@ -27,11 +27,14 @@ template <int DIR>
 struct Geo {
     int nn, nt;                  // cells along normal / tangential
     double dn, dtan;             // cell sizes along normal / tangential
+    double idn, idtan;           // their reciprocals
     DFK_HD Geo(const Mesh& m) {
         nn = DIR == 0 ? m.nx : m.ny;
         nt = DIR == 0 ? m.ny : m.nx;
         dn = DIR == 0 ? m.dx : m.dy;
         dtan = DIR == 0 ? m.dy : m.dx;
+        idn = DIR == 0 ? m.rdx : m.rdy;
+        idtan = DIR == 0 ? m.rdy : m.rdx;
     }
     static constexpr int sigma = DIR == 0 ? 1 : -1;
     DFK_HD long long cell(const Mesh& m, int n, int t) const {
@@ -185,8 +188,11 @@ DFK_HD int lines_body(const Mesh& m, const SchemeConsts& S, const double* __rest
         const bool dfL = fmax(fmax(al[1], al[2]), al[3]) < S.alpha_thres;     // Eq. 34, cell f-1
         const bool dfR = fmax(fmax(al[2], al[3]), al[4]) < S.alpha_thres;     // Eq. 34, cell f
         ndf = (int)dfL + (int)dfR;
-        const double idn = 1.0 / g.dn;
+        const double idn = g.idn;
         const long long li = g.line(f, t);
+        // the cell-average reading of the DF states, stored before the reconstructions so that
+        // the two cell states need not stay live through them
+        if (S.df_states) lines[LR_DFC * ls + li] = df_alpha(Wc[2], Wc[3], S);
         double qL[4], qLn[4], qR[4], qRn[4];
         // the limiter weight so far as tn / td (1 until a reconstruction gives less); fractions are
         // compared by cross-multiplication (denominators >= 2), one division at the end
@@ -305,7 +311,7 @@ DFK_HD int faces_body(const Mesh& m, const SchemeConsts& S, const double* __rest
         const bool df = fmax(fmax(al[0], al[1]), al[2]) < S.alpha_thres;    // Eq. 34, tangential
         ndf = (int)df;
         double qv[2][4], qt[2][4];
-        const double idt = 1.0 / g.dtan;
+        const double idt = g.idtan;
         const long long e = (long long)side * g.nfaces() + g.face(f, t);
         if (!TAPE && !df) {
             // the four components' reconstructions in two pairs, one division per pair
@@ -404,16 +410,18 @@ DFK_HD void flux_point(int dir, const SchemeConsts& S, const FluxSite& site, con
         R.Wt[k] = gp[(mm * 12 + 8 + k) * gs + site.eR];
     }
     const long long e = site.e;
-    fr[FR_ALPHA * fs + e] = df_alpha(L.W, R.W, S);
+    // the two sides' Maxwellians serve the DF factor and the GKS flux.  The Gauss-point reading of
+    // Eq. 33 is always evaluated (the default path stays branch-free); the cell-average reading,
+    // when selected, overwrites it with its face line's value
+    Maxw sl, sr;
+    maxw_pair(L.W, R.W, S, sl, sr);
+    fr[FR_ALPHA * fs + e] = df_alpha_maxw(sl, sr, S);
+    if (S.df_states) fr[FR_ALPHA * fs + e] = lines[LR_DFC * ls + site.li];
     if (ALPHA_ONLY) return;
     double F[4], dF[4];
     if (FLUX == 0) {
-        if (TAPE) {
-            PlaneTape tp{tape + e, fs};
-            gks_flux_t(L, R, dt, S, F, dF, tp);
-        } else {
-            gks_flux(L, R, dt, S, F, dF);
-        }
+        if (TAPE) gks_flux_t(L, R, sl, sr, dt, S, F, dF, PlaneTape{tape + e, fs});
+        else gks_flux_t(L, R, sl, sr, dt, S, F, dF, NoTape{});
     }
     else lf_flux(L, R, S, F, dF);
     if (dir == 1) { to_global<1>(F); to_global<1>(dF); }
@@ -458,7 +466,7 @@ DFK_HD void update_body(const Mesh& m, const SchemeConsts& S, const UpdateArgs& 
         return;
     }
     double L[4], dL[4], dLt[4];
-    const double idx = 1.0 / m.dx, idy = 1.0 / m.dy;     // two divisions per cell instead of twelve
+    const double idx = m.rdx, idy = m.rdy;
     const double ow = frx[FR_OMEGA * fsx + fw], oe = frx[FR_OMEGA * fsx + fe];
     const double os = fry[FR_OMEGA * fsy + fsf], on = fry[FR_OMEGA * fsy + fn];
 #pragma unroll

@@ -93,6 +93,7 @@ extern "C" dfgks_status dfgks_config_default(dfgks_config* c, int nx, int ny) {
     c->alpha_thres = 0.5; c->dH = 0.85; c->dL = 0.85; c->eps = 1e-6; c->C1 = 0.01; c->C2 = 5.0;
     c->time_limiter = 1; c->tau_reading = 0; c->gp_fallback = 1; c->time_scheme = DFGKS_TIME_S2O4;
     c->dt_rule = 0;
+    c->df_states = 0;
     return DFGKS_OK;
 }
 
@@ -112,6 +113,7 @@ static bool config_ok(const dfgks_config* c) {
     if (c->time_scheme != 0 && c->time_scheme != 1) return false;
     if (c->tau_reading != 0 && c->tau_reading != 1) return false;
     if (c->dt_rule != 0 && c->dt_rule != 1) return false;
+    if (c->df_states != 0 && c->df_states != 1) return false;
     return true;
 }
 
@@ -178,6 +180,7 @@ extern "C" dfgks_status dfgks_create(const dfgks_config* cfg, void* stream, dfgk
     m.plane = (long long)m.P * m.NYg;
     m.dx = (cfg->x1 - cfg->x0) / cfg->nx;
     m.dy = (cfg->y1 - cfg->y0) / cfg->ny;
+    m.rdx = 1.0 / m.dx; m.rdy = 1.0 / m.dy;
     m.bc[0] = cfg->bc_xlo; m.bc[1] = cfg->bc_xhi; m.bc[2] = cfg->bc_ylo; m.bc[3] = cfg->bc_yhi;
     m.dt_rule = cfg->dt_rule;
     SchemeConsts& S = h->S;
@@ -190,6 +193,7 @@ extern "C" dfgks_status dfgks_create(const dfgks_config* cfg, void* stream, dfgk
     S.inv_d3 = 1.0 / cfg->dH;
     S.eps = cfg->eps; S.alpha_thres = cfg->alpha_thres; S.C1 = cfg->C1; S.C2 = cfg->C2;
     S.time_limiter = cfg->time_limiter; S.tau_reading = cfg->tau_reading; S.gp_fallback = cfg->gp_fallback;
+    S.df_states = cfg->df_states;
 
     const long long nfx = (long long)(m.nx + 1) * m.ny, nfy = (long long)(m.ny + 1) * m.nx;
     const long long nlx = (long long)(m.nx + 1) * (m.ny + 4), nly = (long long)(m.ny + 1) * (m.nx + 4);

@@ -59,7 +59,8 @@ bool decomp_config_ok(const dfgks_config* c, int px, int py) {
     if (px == 1 && (c->bc_xlo != 1 || c->bc_xhi != 1) && c->nx < G) return false;
     if (py == 1 && (c->bc_ylo != 1 || c->bc_yhi != 1) && c->ny < G) return false;
     if (c->time_scheme != DFGKS_TIME_S2O4) return false;
-    return (c->tau_reading == 0 || c->tau_reading == 1) && (c->dt_rule == 0 || c->dt_rule == 1);
+    return (c->tau_reading == 0 || c->tau_reading == 1) && (c->dt_rule == 0 || c->dt_rule == 1)
+        && (c->df_states == 0 || c->df_states == 1);
 }
 
 void make_plan(const dfgks_config* c, int px, int py, int b, dfgks_block_plan* p) {
@@ -228,6 +229,7 @@ extern "C" DFGKS_API dfgks_status dfgks_decomp_create(const dfgks_config* cfg, i
     S.inv_d3 = 1.0 / cfg->dH;
     S.eps = cfg->eps; S.alpha_thres = cfg->alpha_thres; S.C1 = cfg->C1; S.C2 = cfg->C2;
     S.time_limiter = cfg->time_limiter; S.tau_reading = cfg->tau_reading; S.gp_fallback = cfg->gp_fallback;
+    S.df_states = cfg->df_states;
     const double dx = (cfg->x1 - cfg->x0) / cfg->nx, dy = (cfg->y1 - cfg->y0) / cfg->ny;
     cudaError_t e = cudaSuccess;
     d->blk.resize((size_t)px * py);
@@ -241,6 +243,7 @@ extern "C" DFGKS_API dfgks_status dfgks_decomp_create(const dfgks_config* cfg, i
         m.NYg = m.ny + 2 * G;
         m.plane = (long long)m.P * m.NYg;
         m.dx = dx; m.dy = dy;
+        m.rdx = 1.0 / dx; m.rdy = 1.0 / dy;
         for (int s = 0; s < 4; ++s) m.bc[s] = k.plan.bc[s];
         m.dt_rule = cfg->dt_rule;
         m.gi0 = k.plan.i0; m.gj0 = k.plan.j0; m.gnx = cfg->nx;

@@ -29,6 +29,7 @@ struct SchemeConsts {
     double inv_d3;
     double eps, alpha_thres, C1, C2;
     int time_limiter, tau_reading, gp_fallback;
+    int df_states;                         // DF factor from 0: Gauss-point states, 1: the face's two cell averages
 };
 
 // ------------------------------------------------------------------------------------------
@@ -63,8 +64,9 @@ DFK_HD CharBasis make_basis(const double Wl[4], const double Wr[4], const Scheme
     B.v = n * ir;
     B.q2 = 0.5 * (B.u * B.u + B.v * B.v);
     double p = S.gm1 * (E - r * B.q2);
-    B.c = sqrt(S.gamma * p * ir);
-    B.ic = 1.0 / B.c;
+    const double c2 = S.gamma * p * ir;
+    B.ic = rsqrt(c2);                  // one reciprocal square root for 1/c and c = c^2 / c
+    B.c = c2 * B.ic;
     B.H = (E + p) * ir;
     B.b1 = S.gm1 * B.ic * B.ic;
     B.b2 = B.q2 * B.b1;
@@ -382,18 +384,52 @@ struct Mom {
 // qK = U^2 + V^2 + (K+2)/(2 lambda); the slope solves of a state share them.
 struct Maxw { double rho, ir, U, V, p, il2, tl, f4, qK; };
 
+// velocities and pressure of W given ir = 1/rho
+DFK_HD void maxw_velocities(const double W[4], double ir, const SchemeConsts& S, Maxw& s) {
+    s.rho = W[0];
+    s.ir = ir;
+    s.U = W[1] * ir;
+    s.V = W[2] * ir;
+    s.p = S.gm1 * (W[3] - 0.5 * W[0] * (s.U * s.U + s.V * s.V));
+}
+
+// the rest given tl = 2 lambda = rho / p
+DFK_HD void maxw_finish(double tl, const SchemeConsts& S, Maxw& s) {
+    s.tl = tl;
+    s.il2 = s.p * s.ir;
+    s.f4 = tl * tl * S.inv_K2;
+    s.qK = s.U * s.U + s.V * s.V + (S.K + 2.0) * s.il2;
+}
+
 DFK_HD Maxw maxw_of(const double W[4], const SchemeConsts& S) {
     Maxw s;
-    s.rho = W[0];
-    s.ir = 1.0 / W[0];
-    s.U = W[1] * s.ir;
-    s.V = W[2] * s.ir;
-    s.p = S.gm1 * (W[3] - 0.5 * W[0] * (s.U * s.U + s.V * s.V));
-    s.tl = W[0] / s.p;
-    s.il2 = s.p * s.ir;
-    s.f4 = s.tl * s.tl * S.inv_K2;
-    s.qK = s.U * s.U + s.V * s.V + (S.K + 2.0) * s.il2;
+    maxw_velocities(W, 1.0 / W[0], S, s);
+    maxw_finish(W[0] / s.p, S, s);
     return s;
+}
+
+// the two sides' Maxwellians with two divisions instead of four: 1/(rho_l rho_r) gives both 1/rho
+// and 1/(p_l p_r) both rho/p.  A product outside [1e-150, 1e150] (non-physical or extreme states)
+// is divided side by side as in maxw_of.
+DFK_HD void maxw_pair(const double WL[4], const double WR[4], const SchemeConsts& S, Maxw& a, Maxw& b) {
+    const double rr = WL[0] * WR[0];
+    if (rr > 1e-150 && rr < 1e150) {
+        const double r = 1.0 / rr;
+        maxw_velocities(WL, WR[0] * r, S, a);
+        maxw_velocities(WR, WL[0] * r, S, b);
+    } else {
+        maxw_velocities(WL, 1.0 / WL[0], S, a);
+        maxw_velocities(WR, 1.0 / WR[0], S, b);
+    }
+    const double pp = a.p * b.p;
+    if (pp > 1e-150 && pp < 1e150) {
+        const double r = 1.0 / pp;
+        maxw_finish(WL[0] * b.p * r, S, a);
+        maxw_finish(WR[0] * a.p * r, S, b);
+    } else {
+        maxw_finish(WL[0] / a.p, S, a);
+        maxw_finish(WR[0] / b.p, S, b);
+    }
 }
 
 // half: 0 full, +1 u>0, -1 u<0
@@ -406,9 +442,17 @@ DFK_HD void fill_moments(const Maxw& s, double K, Mom& m) {
         double lam = 0.5 * s.tl;
         double isl = rsqrt(lam);                              // 1/sqrt(lambda)
         double x = lam * isl * s.U;                           // sqrt(lambda) U
-        double e = exp(-x * x) * (0.28209479177387814347 * isl);  // exp(-lambda U^2) / (2 sqrt(pi lambda))
-        if (HALF > 0) { m.mu[0] = 0.5 * erfc(-x); m.mu[1] = s.U * m.mu[0] + e; }
-        else          { m.mu[0] = 0.5 * erfc(x);  m.mu[1] = s.U * m.mu[0] - e; }
+        double G = exp(-x * x);
+        double e = G * (0.28209479177387814347 * isl);        // exp(-lambda U^2) / (2 sqrt(pi lambda))
+        // erfc(|x|) / 2 from the scaled function erfcx(|x|) = exp(x^2) erfc(|x|) and the Gaussian
+        // above (one exponential for both); erfc(-|x|) = 2 - erfc(|x|)
+#ifdef __CUDA_ARCH__
+        double h = 0.5 * G * erfcx(fabs(x));
+#else
+        double h = 0.5 * erfc(fabs(x));
+#endif
+        if (HALF > 0) { m.mu[0] = x >= 0.0 ? 1.0 - h : h; m.mu[1] = s.U * m.mu[0] + e; }   // erfc(-x) / 2
+        else          { m.mu[0] = x >= 0.0 ? h : 1.0 - h; m.mu[1] = s.U * m.mu[0] - e; }   // erfc(x) / 2
     }
 #pragma unroll
     for (int n = 2; n < 7; ++n) m.mu[n] = s.U * m.mu[n - 1] + (double)(n - 1) * s.il2 * m.mu[n - 2];
@@ -502,11 +546,11 @@ DFK_HD void tape_vec(const Tape& tp, int b, const double v[4]) {
     for (int i = 0; i < 4; ++i) tp.put(b + i, v[i]);
 }
 
+// sl, sr: the Maxwellians of L.W and R.W (maxw_pair)
 template <class Tape>
-DFK_HD void gks_flux_t(const GPState& L, const GPState& R, double dt, const SchemeConsts& S,
-                       double F[4], double dF[4], const Tape& tp) {
+DFK_HD void gks_flux_t(const GPState& L, const GPState& R, const Maxw& sl, const Maxw& sr, double dt,
+                       const SchemeConsts& S, double F[4], double dF[4], const Tape& tp) {
     const double K = S.K;
-    Maxw sl = maxw_of(L.W, S), sr = maxw_of(R.W, S);
     Mom ml, mr;
     fill_moments<+1>(sl, K, ml);
     fill_moments<-1>(sr, K, mr);
@@ -542,7 +586,31 @@ DFK_HD void gks_flux_t(const GPState& L, const GPState& R, double dt, const Sche
 #pragma unroll
     for (int i = 0; i < 4; ++i) Wcy[i] = sl.rho * t1[i] + sr.rho * t2[i];
     tape_vec(tp, TG_WC, Wc); tape_vec(tp, TG_WCX, Wcx); tape_vec(tp, TG_WCY, Wcy);
-    Maxw sc = maxw_of(Wc, S);
+    // the equilibrium state's Maxwellian: 1/rho_c shares a division with 1/dt, and rho_c / p_c one
+    // with 1/(p_l + p_r) of the pressure ratio in tau_n (products outside [1e-150, 1e150] are
+    // divided separately)
+    Maxw sc;
+    double idt, ips;
+    {
+        const double a = Wc[0] * dt;
+        if (a > 1e-150 && a < 1e150) {
+            const double r = 1.0 / a;
+            maxw_velocities(Wc, dt * r, S, sc);
+            idt = Wc[0] * r;
+        } else {
+            maxw_velocities(Wc, 1.0 / Wc[0], S, sc);
+            idt = 1.0 / dt;
+        }
+        const double ps = sl.p + sr.p, b = sc.p * ps;
+        if (b > 1e-150 && b < 1e150) {
+            const double r = 1.0 / b;
+            maxw_finish(Wc[0] * ps * r, S, sc);
+            ips = sc.p * r;
+        } else {
+            maxw_finish(Wc[0] / sc.p, S, sc);
+            ips = 1.0 / ps;
+        }
+    }
     Mom mc;
     fill_moments<0>(sc, K, mc);
     tape_maxw(tp, TG_SC, sc); tape_mom(tp, TG_MC, mc);
@@ -578,7 +646,7 @@ DFK_HD void gks_flux_t(const GPState& L, const GPState& R, double dt, const Sche
     tape_vec(tp, TG_MC0, Mc0); tape_vec(tp, TG_MC1, Mc1); tape_vec(tp, TG_MC2, Mc2);
     tape_vec(tp, TG_ML0, Ml0); tape_vec(tp, TG_MR0, Mr0); tape_vec(tp, TG_ML1, Ml1); tape_vec(tp, TG_MR1, Mr1);
     // numerical collision time (Sect. 2.2) and the combined time coefficients of Eq. 27
-    const double q = (sl.p - sr.p) / (sl.p + sr.p);
+    const double q = (sl.p - sr.p) * ips;
     tp.put(TG_Q, q);
     double rT = S.C1 + S.C2 * fabs(q);   // tau_n / dt
     double T = rT * dt;
@@ -588,7 +656,6 @@ DFK_HD void gks_flux_t(const GPState& L, const GPState& R, double dt, const Sche
     double E1 = E2 * E2;
     double om = 1.0 - E2;
     double S3 = om * (3.0 - E2);                       // 3 - 4 E2 + E1
-    double idt = 1.0 / dt;
     // F-coefficients (4 G(dt/2) - G(dt)) / dt and dF-coefficients 4 (G(dt) - 2 G(dt/2)) / dt^2
     double glrF = r * S3, glrD = -4.0 * r * om * om * idt;
     double gcF = 1.0 - glrF, gcD = -glrD;
@@ -625,6 +692,14 @@ DFK_HD void gks_flux_t(const GPState& L, const GPState& R, double dt, const Sche
         F[i] = gcF * c0 + acF * c1 + AcF * c2 + glrF * g0 + alrF * g1 + AlrF * g2;
         dF[i] = gcD * c0 + acD * c1 + AcD * c2 + glrD * g0 + alrD * g1 + AlrD * g2;
     }
+}
+
+template <class Tape>
+DFK_HD void gks_flux_t(const GPState& L, const GPState& R, double dt, const SchemeConsts& S,
+                       double F[4], double dF[4], const Tape& tp) {
+    Maxw sl, sr;
+    maxw_pair(L.W, R.W, S, sl, sr);
+    gks_flux_t(L, R, sl, sr, dt, S, F, dF, tp);
 }
 
 DFK_HD void gks_flux(const GPState& L, const GPState& R, double dt, const SchemeConsts& S, double F[4], double dF[4]) {
@@ -687,24 +762,29 @@ DFK_HD void lf_flux(const GPState& L, const GPState& R, const SchemeConsts& S,
     }
 }
 
-// DF factor of one Gauss point (Sect. 3.2), local-frame states: one division for both densities,
-// reciprocal square roots for the sound speeds, |dp|/p_l + |dp|/p_r as |dp| (p_l + p_r)/(p_l p_r)
-DFK_HD double df_alpha(const double WL[4], const double WR[4], const SchemeConsts& S) {
-    const double rr = 1.0 / (WL[0] * WR[0]);
-    const double irl = WR[0] * rr, irr = WL[0] * rr;
-    const double ul = WL[1] * irl, vl = WL[2] * irl, ur = WR[1] * irr, vr = WR[2] * irr;
-    const double pl = S.gm1 * (WL[3] - 0.5 * WL[0] * (ul * ul + vl * vl));
-    const double pr = S.gm1 * (WR[3] - 0.5 * WR[0] * (ur * ur + vr * vr));
-    const double icl = rsqrt(S.gamma * pl * irl), icr = rsqrt(S.gamma * pr * irr);
-    const double dn = ul * icl - ur * icr, dtg = vl * icl - vr * icr;
-    const double D = fabs(pl - pr) * (pl + pr) / (pl * pr) + dn * dn + dtg * dtg;
+// DF factor of one Gauss point (Sect. 3.2, Eq. 33) from the Maxwellians of its two local-frame
+// states (maxw_pair, which the GKS flux shares): reciprocal square roots for the sound speeds, one
+// division at the end
+DFK_HD double df_alpha_maxw(const Maxw& l, const Maxw& r, const SchemeConsts& S) {
+    const double icl = rsqrt(S.gamma * l.il2), icr = rsqrt(S.gamma * r.il2);   // 1/c of each side
+    const double dn = l.U * icl - r.U * icr, dtg = l.V * icl - r.V * icr;
+    // |p_l - p_r| (p_l + p_r) / (p_l p_r) = |p_l - p_r| (1/p_l + 1/p_r), 1/p = (rho/p) (1/rho)
+    const double D = fabs(l.p - r.p) * (l.tl * l.ir + r.tl * r.ir) + dn * dn + dtg * dtg;
     return 1.0 / (1.0 + D * D);
+}
+
+DFK_HD double df_alpha(const double WL[4], const double WR[4], const SchemeConsts& S) {
+    Maxw l, r;
+    maxw_pair(WL, WR, S, l, r);
+    return df_alpha_maxw(l, r, S);
 }
 
 DFK_HD bool physical_state(const double W[4], double gm1) {
     if (!(W[0] > 0.0)) return false;
-    double p = gm1 * (W[3] - 0.5 * (W[1] * W[1] + W[2] * W[2]) / W[0]);
-    return p > 0.0;
+    // p > 0 tested as rho p = (gamma - 1) (rho E - |rho u|^2 / 2) > 0: the same sign for rho > 0,
+    // without a division
+    double rp = gm1 * (W[0] * W[3] - 0.5 * (W[1] * W[1] + W[2] * W[2]));
+    return rp > 0.0;
 }
 
 }  // namespace dfk

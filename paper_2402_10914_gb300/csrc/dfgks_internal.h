@@ -56,6 +56,7 @@ struct Mesh {
     int NYg;            // ny + 2G
     long long plane;    // P * NYg
     double dx, dy;
+    double rdx, rdy;    // 1/dx and 1/dy, divided once on the host (the same correctly rounded values)
     int bc[4];          // x-low, x-high, y-low, y-high; BC_EXTERNAL: ghosts written by a halo copy
     int dt_rule;        // CFL bound per cell: 0 per-direction minimum, 1 summed inverse
     int gi0, gj0, gnx;  // a block of a larger mesh: its first cell there and that mesh's nx
@@ -87,9 +88,10 @@ struct DevState {
 };
 
 // Per-face-line record of the normal reconstruction (Algorithm 1, normal step), SoA planes
-// (LR_TLK: which of the face's eight reconstructions set the limiter weight, 2k + side, or -1)
+// (LR_TLK: which of the face's eight reconstructions set the limiter weight, 2k + side, or -1;
+// LR_DFC: the DF factor of the face's two cell averages, written when df_states = 1)
 enum LineField { LR_WL = 0, LR_WLN = 4, LR_WR = 8, LR_WRN = 12, LR_TL = 16,
-                 LR_U = 17, LR_V, LR_C, LR_IC, LR_H, LR_B1, LR_B2, LR_Q2, LR_TLK, LR_COUNT };
+                 LR_U = 17, LR_V, LR_C, LR_IC, LR_H, LR_B1, LR_B2, LR_Q2, LR_TLK, LR_DFC, LR_COUNT };
 // Per-(face, side) Gauss-point record of the tangential step: m=1 {W, Wn, Wt}, m=2 {W, Wn, Wt},
 // then GP_FB: bit m set if Gauss point m fell back to the cell average
 constexpr int GP_FB = 24;

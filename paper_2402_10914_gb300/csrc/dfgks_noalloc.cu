@@ -19,7 +19,7 @@ using namespace dfk;
 namespace {
 
 // 16 MiB of scratch, enough for every mesh whose sides are both at most 128 cells (128 x 128
-// needs 2,019,928 doubles of the 2,097,152).  Every GPU that loads the library holds this array
+// needs 2,036,956 doubles of the 2,097,152).  Every GPU that loads the library holds this array
 // until the process exits.
 constexpr long long kScratchDoubles = 2LL * 1024 * 1024;
 constexpr int kMaxSide = 128;
@@ -60,6 +60,7 @@ bool valid(const dfgks_config* c) {
     if ((c->bc_xlo != 1 || c->bc_xhi != 1) && c->nx < G) return false;
     if ((c->bc_ylo != 1 || c->bc_yhi != 1) && c->ny < G) return false;
     if (c->tau_reading != 0 && c->tau_reading != 1) return false;
+    if (c->df_states != 0 && c->df_states != 1) return false;
     return true;
 }
 
@@ -79,6 +80,7 @@ extern "C" DFGKS_API dfgks_status dfgks_residual_noalloc(const dfgks_config* cfg
     m.plane = (long long)m.P * m.NYg;
     m.dx = (cfg->x1 - cfg->x0) / cfg->nx;
     m.dy = (cfg->y1 - cfg->y0) / cfg->ny;
+    m.rdx = 1.0 / m.dx; m.rdy = 1.0 / m.dy;
     m.bc[0] = cfg->bc_xlo; m.bc[1] = cfg->bc_xhi; m.bc[2] = cfg->bc_ylo; m.bc[3] = cfg->bc_yhi;
     m.dt_rule = cfg->dt_rule;
     m.gi0 = 0; m.gj0 = 0; m.gnx = cfg->nx;
@@ -93,6 +95,7 @@ extern "C" DFGKS_API dfgks_status dfgks_residual_noalloc(const dfgks_config* cfg
     S.inv_d3 = 1.0 / cfg->dH;
     S.eps = cfg->eps; S.alpha_thres = cfg->alpha_thres; S.C1 = cfg->C1; S.C2 = cfg->C2;
     S.time_limiter = cfg->time_limiter; S.tau_reading = cfg->tau_reading; S.gp_fallback = cfg->gp_fallback;
+    S.df_states = cfg->df_states;
 
     // carve the scratch: ghosted W and alpha, line, Gauss-point and flux records, dt
     const long long nfx = (long long)(m.nx + 1) * m.ny, nfy = (long long)(m.ny + 1) * m.nx;

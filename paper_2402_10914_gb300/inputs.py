@@ -64,6 +64,7 @@ class Settings:
     gp_fallback: int = 1
     time_scheme: int = S2O4
     dt_rule: int = 0
+    df_states: int = 0                 # DF factor from 0: Gauss-point states, 1: the face's cell averages
 
     def with_(self, **kw) -> "Settings":
         return replace(self, **kw)

@@ -36,6 +36,7 @@ int main(int argc, char** argv) {
     Mesh m;
     m.nx = in.nx; m.ny = in.ny; m.P = (in.nx + 2 * G + 3) & ~3; m.NYg = in.ny + 2 * G; m.plane = (long long)m.P * m.NYg;
     m.dx = (in.x1 - in.x0) / in.nx; m.dy = (in.y1 - in.y0) / in.ny;
+    m.rdx = 1.0 / m.dx; m.rdy = 1.0 / m.dy;
     for (int q = 0; q < 4; ++q) m.bc[q] = in.bc[q];
     m.dt_rule = 0; m.gi0 = 0; m.gj0 = 0; m.gnx = in.nx;
     SchemeConsts S;
@@ -43,6 +44,7 @@ int main(int argc, char** argv) {
     S.d[3] = in.dH; S.d[0] = (1.0 - in.dH) * (1.0 - in.dL) / 2.0; S.d[1] = (1.0 - in.dH) * in.dL; S.d[2] = S.d[0];
     S.inv_d3 = 1.0 / in.dH; S.eps = in.eps; S.alpha_thres = in.alpha_thres; S.C1 = in.C1; S.C2 = in.C2;
     S.time_limiter = in.time_limiter; S.tau_reading = in.tau_reading; S.gp_fallback = in.gp_fallback;
+    S.df_states = 0;
     const long long nfx = (long long)(m.nx + 1) * m.ny, nfy = (long long)(m.ny + 1) * m.nx;
     const long long nlx = (long long)(m.nx + 1) * (m.ny + 4), nly = (long long)(m.ny + 1) * (m.nx + 4);
     SweepBuffers B;

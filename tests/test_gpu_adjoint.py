@@ -150,12 +150,16 @@ def test_vortex_gradient_with_time_limiter_matches_oracle():
 
 def test_c4_vortex_gradient_against_finite_differences():
     # isentropic vortex 256^2 on [0,10]^2, 100 GKS steps, J = sum rho^2 at the final time, checkpoint
-    # every 10 steps; central differences on 32 random cells x 4 components, the recorded dt frozen.
+    # every 10 steps; difference quotients on 16 random cells x 4 components, the recorded dt frozen.
     # The time limiter is off here: with it on, J is only piecewise smooth at this scale (after 100
     # steps the difference quotients of one entry spread over [-2.5, 2.1] for h in 1e-7..1e-5 while
     # the adjoint gives 2.0), so no step size checks 1e-6; the limiter-on adjoint is checked against
-    # the oracle's reverse sweep above.  The bar is relative to the gradient's largest entry: the
-    # difference quotients carry ~3e-8 of forward rounding, far above 1e-6 of the energy entries.
+    # the oracle's reverse sweep above.
+    # Step size: the forward runs' rounding puts ~8e-13 of noise on each J(W+) - J(W-), i.e. ~4e-7 on
+    # a quotient with h = 1e-6 -- a fifth of the bar on the largest entries (~2) and several times it
+    # on an entry of 5 % of that.  Central differences at h and 2h (h = 2e-5 of the entry's scale)
+    # combined by Richardson extrapolation, (4 D(h) - D(2h)) / 3, cancel the O(h^2) truncation and
+    # leave ~3e-8 of rounding noise.
     from paper_2402_10914_gb300.solver import GKSRun, Solver
     w = I.vortex(256, steps=100)
     s = w.settings.with_(time_limiter=0)
@@ -170,27 +174,31 @@ def test_c4_vortex_gradient_against_finite_differences():
         done, dts = sol.step(100, record_dts=True)
         assert done == 100
         rng = np.random.default_rng(11)
-        cells = rng.choice(s.nx * s.ny, size=32, replace=False)
+        cells = rng.choice(s.nx * s.ny, size=16, replace=False)
+
+        def quotient(k, j, i, h):
+            Wp, Wm = w.W0.copy(), w.W0.copy()
+            Wp[k, j, i] += h
+            Wm[k, j, i] -= h
+            return sum_rho2_difference(run_fixed(sol, Wp, dts), run_fixed(sol, Wm, dts)) / (2 * h)
+
         worst = 0.0
         entries = []
         for q in cells:
             j, i = divmod(int(q), s.nx)
             for k in range(4):
-                h = 1e-6 * max(1.0, abs(w.W0[k, j, i]))
-                Wp, Wm = w.W0.copy(), w.W0.copy()
-                Wp[k, j, i] += h
-                Wm[k, j, i] -= h
-                fd = sum_rho2_difference(run_fixed(sol, Wp, dts), run_fixed(sol, Wm, dts)) / (2 * h)
+                h = 2e-5 * max(1.0, abs(w.W0[k, j, i]))
+                fd = (4.0 * quotient(k, j, i, h) - quotient(k, j, i, 2.0 * h)) / 3.0
                 worst = max(worst, abs(g[k, j, i] - fd))
                 entries.append((abs(g[k, j, i]), abs(g[k, j, i] - fd)))
     gmax = np.abs(g).max()
     assert worst <= 1e-6 * gmax, (worst, gmax)
     # per entry: every entry of at least 5 % of the largest one within 1e-6 of itself; smaller
-    # entries are reported (their difference quotients' rounding, ~3e-8, is of their size scale)
+    # entries are reported (the quotients' rounding noise approaches their own scale)
     big = [(a, e) for a, e in entries if a >= 0.05 * gmax]
     assert big and all(e <= 1e-6 * a for a, e in big), max(e / a for a, e in big)
     rel = sorted(e / a for a, e in entries if a > 0.0)
-    print("C4 gradient vs central differences: %d entries >= 5%% of max, worst relative %.2e; all %d entries: "
+    print("C4 gradient vs difference quotients: %d entries >= 5%% of max, worst relative %.2e; all %d entries: "
           "median relative %.2e, max %.2e" % (len(big), max(e / a for a, e in big), len(rel), rel[len(rel) // 2], rel[-1]))
 
 

@@ -548,3 +548,34 @@ def test_full_run_parity_resolution_workloads(name):
     g = w.settings.gamma
     p = (g - 1) * (W[3] - 0.5 * (W[1] ** 2 + W[2] ** 2) / W[0])
     assert W[0].min() > 0 and p.min() > 0
+
+
+@pytest.mark.parametrize("name", ["quadrants", "p123_gks", "p123_lf", "blast"])
+def test_one_step_parity_df_from_cell_averages(name):
+    # the alternative DF-state reading (df_states = 1): one step against the oracle with the same
+    # reading, and the face records' DF factors
+    if name == "quadrants":
+        w = I.quadrants(96, seed=3)
+    elif name == "p123_gks":
+        w = I.problem_123(3.0, flux=I.GKS)
+    elif name == "p123_lf":
+        w = I.problem_123(3.0, flux=I.LF)
+    else:
+        w = I.blast(64)
+    w.settings = w.settings.with_(df_states=1)
+    (rc, Wo, ao, to, dts_o, st), (done, W, a, t, dts, cnt) = run_both(w, 1)
+    assert rc == 0 and done == 1
+    err = comp_rel_err(W, Wo)
+    if err > 1e-12:
+        _, env, _ = oracle_envelope(w.settings, w.W0, 1)
+        assert err <= 2.0 * env, (err, env)
+    assert comp_rel_err(a[None], ao[None], floor_frac=1e-12) <= 1e-11
+    assert cnt["df_normal"] == st.df_normal and cnt["df_tangential"] == st.df_tangential
+    s = w.settings
+    alpha = oracle.alpha0(s, w.W0)
+    dt = 0.4 * oracle.cfl_dt(s, w.W0)
+    for direction in (0, 1):
+        ref, _ = oracle.face_records(s, w.W0, alpha, dt, direction)
+        with Solver(s) as sol:
+            got = host(sol.face_records(dev(w.W0), dev(alpha), dt, direction, flux=s.flux))
+        assert field_err(got[..., 9:11], ref[..., 9:11]) < 1e-12

@@ -444,3 +444,29 @@ def test_df_alpha_point():
     cl, cr = math.sqrt(1.4 / 1.0), math.sqrt(1.4 * 0.25 / 0.5)
     D = 0.75 / 1.0 + 0.75 / 0.25 + (0.5 / cl + 0.1 / cr) ** 2 + (-0.2 / cl - 0.3 / cr) ** 2
     assert oracle.df_alpha_point(WL, WR) == pytest.approx(1 / (1 + D * D), rel=1e-14)
+
+
+def test_df_factor_from_cell_averages_reading():
+    # df_states = 1 (an alternative to the paper's reading): both Gauss points of a face take the DF
+    # factor of the two cell averages beside it, in the face's local frame; df_states = 0 keeps the
+    # reconstructed Gauss-point states
+    from paper_2402_10914_gb300 import inputs as I
+    w = I.random_rough(9, 7, seed=21)
+    s1 = w.settings.with_(df_states=1)
+    alpha = np.ones((7, 9))
+    for direction in (0, 1):
+        faces, _ = oracle.face_records(s1, w.W0, alpha, 1e-3, direction)
+        faces0, _ = oracle.face_records(w.settings, w.W0, alpha, 1e-3, direction)
+        nt, nf = faces.shape[:2]
+        for t in range(nt):
+            for f in range(1, nf - 1):                      # faces with interior cells on both sides
+                if direction == 0:
+                    Wl, Wr = w.W0[:, t, f - 1], w.W0[:, t, f]
+                else:                                        # local frame of a y-face: (rho, rhoV, -rhoU, E)
+                    Wl = np.array([w.W0[0, f - 1, t], w.W0[2, f - 1, t], -w.W0[1, f - 1, t], w.W0[3, f - 1, t]])
+                    Wr = np.array([w.W0[0, f, t], w.W0[2, f, t], -w.W0[1, f, t], w.W0[3, f, t]])
+                a = oracle.df_alpha_point(Wl, Wr)
+                assert faces[t, f, 9] == a and faces[t, f, 10] == a
+                # the fluxes themselves do not depend on where the DF factor comes from
+                assert np.array_equal(faces[t, f, :8], faces0[t, f, :8])
+        assert not np.array_equal(faces[..., 9], faces0[..., 9])

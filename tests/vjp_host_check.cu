@@ -25,7 +25,7 @@ static SchemeConsts consts(int tau_reading) {
     S.gamma = 1.4; S.gm1 = 0.4; S.K = 3.0; S.inv_K2 = 0.2;
     S.d[3] = 0.85; S.d[0] = 0.15 * 0.15 / 2; S.d[1] = 0.15 * 0.85; S.d[2] = S.d[0]; S.inv_d3 = 1.0 / 0.85;
     S.eps = 1e-6; S.alpha_thres = 0.5; S.C1 = 0.01; S.C2 = 5.0;
-    S.time_limiter = 1; S.tau_reading = tau_reading; S.gp_fallback = 1;
+    S.time_limiter = 1; S.tau_reading = tau_reading; S.gp_fallback = 1; S.df_states = 0;
     return S;
 }
 
