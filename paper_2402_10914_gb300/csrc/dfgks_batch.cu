@@ -394,6 +394,7 @@ extern "C" DFGKS_API dfgks_status dfgks_batch_create(const dfgks_config* cfgs, c
         SchemeConsts& S = q.S;
         S.gamma = c->gamma; S.gm1 = c->gamma - 1.0; S.K = (4.0 - 2.0 * c->gamma) / (c->gamma - 1.0);
         S.inv_K2 = 1.0 / (S.K + 2.0);
+        S.r2g = sqrt(2.0 / S.gamma);
         S.d[3] = c->dH; S.d[0] = (1.0 - c->dH) * (1.0 - c->dL) / 2.0; S.d[1] = (1.0 - c->dH) * c->dL; S.d[2] = S.d[0];
         S.inv_d3 = 1.0 / c->dH;
         S.eps = c->eps; S.alpha_thres = c->alpha_thres; S.C1 = c->C1; S.C2 = c->C2;

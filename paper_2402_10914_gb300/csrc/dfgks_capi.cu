@@ -186,6 +186,7 @@ extern "C" dfgks_status dfgks_create(const dfgks_config* cfg, void* stream, dfgk
     SchemeConsts& S = h->S;
     S.gamma = cfg->gamma; S.gm1 = cfg->gamma - 1.0; S.K = (4.0 - 2.0 * cfg->gamma) / (cfg->gamma - 1.0);
     S.inv_K2 = 1.0 / (S.K + 2.0);
+    S.r2g = sqrt(2.0 / S.gamma);
     S.d[3] = cfg->dH;
     S.d[0] = (1.0 - cfg->dH) * (1.0 - cfg->dL) / 2.0;
     S.d[1] = (1.0 - cfg->dH) * cfg->dL;

@@ -225,6 +225,7 @@ extern "C" DFGKS_API dfgks_status dfgks_decomp_create(const dfgks_config* cfg, i
     memset(&S, 0, sizeof(S));
     S.gamma = cfg->gamma; S.gm1 = cfg->gamma - 1.0; S.K = (4.0 - 2.0 * cfg->gamma) / (cfg->gamma - 1.0);
     S.inv_K2 = 1.0 / (S.K + 2.0);
+    S.r2g = sqrt(2.0 / S.gamma);
     S.d[3] = cfg->dH; S.d[0] = (1.0 - cfg->dH) * (1.0 - cfg->dL) / 2.0; S.d[1] = (1.0 - cfg->dH) * cfg->dL; S.d[2] = S.d[0];
     S.inv_d3 = 1.0 / cfg->dH;
     S.eps = cfg->eps; S.alpha_thres = cfg->alpha_thres; S.C1 = cfg->C1; S.C2 = cfg->C2;

@@ -25,6 +25,7 @@ constexpr double kGaussEta = 0.28867513459481288225;   // sqrt(3)/6: Gauss point
 
 struct SchemeConsts {
     double gamma, gm1, K, inv_K2;          // gamma, gamma-1, internal degrees of freedom, 1/(K+2)
+    double r2g;                            // sqrt(2/gamma): 1/c = sqrt(2/gamma) sqrt(lambda)
     double d[4];                           // WENO-AO linear weights d0..d3 (Sect. 3.1)
     double inv_d3;
     double eps, alpha_thres, C1, C2;
@@ -382,7 +383,7 @@ struct Mom {
 
 // One Maxwellian: il2 = 1/(2 lambda) = p/rho, tl = 2 lambda, f4 = 4 lambda^2/(K+2),
 // qK = U^2 + V^2 + (K+2)/(2 lambda); the slope solves of a state share them.
-struct Maxw { double rho, ir, U, V, p, il2, tl, f4, qK; };
+struct Maxw { double rho, ir, U, V, p, il2, tl, f4, qK, isl; };   // isl = 1/sqrt(lambda)
 
 // velocities and pressure of W given ir = 1/rho
 DFK_HD void maxw_velocities(const double W[4], double ir, const SchemeConsts& S, Maxw& s) {
@@ -399,6 +400,7 @@ DFK_HD void maxw_finish(double tl, const SchemeConsts& S, Maxw& s) {
     s.il2 = s.p * s.ir;
     s.f4 = tl * tl * S.inv_K2;
     s.qK = s.U * s.U + s.V * s.V + (S.K + 2.0) * s.il2;
+    s.isl = rsqrt(0.5 * tl);           // the half-space moments and the DF factor's 1/c need it
 }
 
 DFK_HD Maxw maxw_of(const double W[4], const SchemeConsts& S) {
@@ -440,7 +442,7 @@ DFK_HD void fill_moments(const Maxw& s, double K, Mom& m) {
         m.mu[1] = s.U;
     } else {
         double lam = 0.5 * s.tl;
-        double isl = rsqrt(lam);                              // 1/sqrt(lambda)
+        double isl = s.isl;                                   // 1/sqrt(lambda)
         double x = lam * isl * s.U;                           // sqrt(lambda) U
         double G = exp(-x * x);
         double e = G * (0.28209479177387814347 * isl);        // exp(-lambda U^2) / (2 sqrt(pi lambda))
@@ -766,7 +768,8 @@ DFK_HD void lf_flux(const GPState& L, const GPState& R, const SchemeConsts& S,
 // states (maxw_pair, which the GKS flux shares): reciprocal square roots for the sound speeds, one
 // division at the end
 DFK_HD double df_alpha_maxw(const Maxw& l, const Maxw& r, const SchemeConsts& S) {
-    const double icl = rsqrt(S.gamma * l.il2), icr = rsqrt(S.gamma * r.il2);   // 1/c of each side
+    // 1/c = sqrt(rho / (gamma p)) = sqrt(2/gamma) lambda / sqrt(lambda) on each side
+    const double icl = S.r2g * (0.5 * l.tl) * l.isl, icr = S.r2g * (0.5 * r.tl) * r.isl;
     const double dn = l.U * icl - r.U * icr, dtg = l.V * icl - r.V * icr;
     // |p_l - p_r| (p_l + p_r) / (p_l p_r) = |p_l - p_r| (1/p_l + 1/p_r), 1/p = (rho/p) (1/rho)
     const double D = fabs(l.p - r.p) * (l.tl * l.ir + r.tl * r.ir) + dn * dn + dtg * dtg;

@@ -41,6 +41,7 @@ int main(int argc, char** argv) {
     m.dt_rule = 0; m.gi0 = 0; m.gj0 = 0; m.gnx = in.nx;
     SchemeConsts S;
     S.gamma = in.gamma; S.gm1 = in.gamma - 1.0; S.K = (4.0 - 2.0 * in.gamma) / (in.gamma - 1.0); S.inv_K2 = 1.0 / (S.K + 2.0);
+    S.r2g = sqrt(2.0 / S.gamma);
     S.d[3] = in.dH; S.d[0] = (1.0 - in.dH) * (1.0 - in.dL) / 2.0; S.d[1] = (1.0 - in.dH) * in.dL; S.d[2] = S.d[0];
     S.inv_d3 = 1.0 / in.dH; S.eps = in.eps; S.alpha_thres = in.alpha_thres; S.C1 = in.C1; S.C2 = in.C2;
     S.time_limiter = in.time_limiter; S.tau_reading = in.tau_reading; S.gp_fallback = in.gp_fallback;

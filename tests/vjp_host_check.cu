@@ -22,7 +22,7 @@ static void report(const char* name, double err, double tol) {
 
 static SchemeConsts consts(int tau_reading) {
     SchemeConsts S{};
-    S.gamma = 1.4; S.gm1 = 0.4; S.K = 3.0; S.inv_K2 = 0.2;
+    S.gamma = 1.4; S.gm1 = 0.4; S.K = 3.0; S.inv_K2 = 0.2; S.r2g = sqrt(2.0 / 1.4);
     S.d[3] = 0.85; S.d[0] = 0.15 * 0.15 / 2; S.d[1] = 0.15 * 0.85; S.d[2] = S.d[0]; S.inv_d3 = 1.0 / 0.85;
     S.eps = 1e-6; S.alpha_thres = 0.5; S.C1 = 0.01; S.C2 = 5.0;
     S.time_limiter = 1; S.tau_reading = tau_reading; S.gp_fallback = 1; S.df_states = 0;
