@@ -185,8 +185,8 @@ DFK_HD int lines_body(const Mesh& m, const SchemeConsts& S, const double* __rest
         double Q[6][4];
 #pragma unroll
         for (int s = 0; s < 6; ++s) project(B, Wc[s], Q[s]);
-        const bool dfL = fmax(fmax(al[1], al[2]), al[3]) < S.alpha_thres;     // Eq. 34, cell f-1
-        const bool dfR = fmax(fmax(al[2], al[3]), al[4]) < S.alpha_thres;     // Eq. 34, cell f
+        const bool dfL = nn_less(nn_max(nn_max(al[1], al[2]), al[3]), S.alpha_thres);   // Eq. 34, cell f-1
+        const bool dfR = nn_less(nn_max(nn_max(al[2], al[3]), al[4]), S.alpha_thres);   // Eq. 34, cell f
         ndf = (int)dfL + (int)dfR;
         const double idn = g.idn;
         const long long li = g.line(f, t);
@@ -218,9 +218,9 @@ DFK_HD int lines_body(const Mesh& m, const SchemeConsts& S, const double* __rest
                     if (S.time_limiter) {
                         double n, d;
                         limiter_fraction(oL, n, d);
-                        if (n * td < tn * d) { tn = n; td = d; tlk = 2 * k; }
+                        if (nn_less(n * td, tn * d)) { tn = n; td = d; tlk = 2 * k; }
                         limiter_fraction(oR, n, d);
-                        if (n * td < tn * d) { tn = n; td = d; tlk = 2 * k + 1; }
+                        if (nn_less(n * td, tn * d)) { tn = n; td = d; tlk = 2 * k + 1; }
                     }
                     if (!dfL) { ao_at_right_edge(oL, sL[2], v, sl); qL[k] = v; qLn[k] = sl * idn; }
                     if (!dfR) { ao_at_right_edge(oR, sR[2], v, sl); qR[k] = v; qRn[k] = -sl * idn; }
@@ -234,7 +234,7 @@ DFK_HD int lines_body(const Mesh& m, const SchemeConsts& S, const double* __rest
                 if (S.time_limiter) {
                     double n, d;
                     limiter_fraction(o, n, d);
-                    if (n * td < tn * d) { tn = n; td = d; tlk = 2 * k; }
+                    if (nn_less(n * td, tn * d)) { tn = n; td = d; tlk = 2 * k; }
                 }
                 if (!dfL) ao_at_right_edge(o, sL[2], v, sl);
             }
@@ -245,7 +245,7 @@ DFK_HD int lines_body(const Mesh& m, const SchemeConsts& S, const double* __rest
                 if (S.time_limiter) {
                     double n, d;
                     limiter_fraction(o, n, d);
-                    if (n * td < tn * d) { tn = n; td = d; tlk = 2 * k + 1; }
+                    if (nn_less(n * td, tn * d)) { tn = n; td = d; tlk = 2 * k + 1; }
                 }
                 if (!dfR) ao_at_right_edge(o, sR[2], v, sl);
             }
@@ -308,7 +308,7 @@ DFK_HD int faces_body(const Mesh& m, const SchemeConsts& S, const double* __rest
         double al[3];
 #pragma unroll
         for (int b = 0; b < 3; ++b) al[b] = alpha[g.cell(m, ncell, t + Geo<DIR>::sigma * (b - 1))];
-        const bool df = fmax(fmax(al[0], al[1]), al[2]) < S.alpha_thres;    // Eq. 34, tangential
+        const bool df = nn_less(nn_max(nn_max(al[0], al[1]), al[2]), S.alpha_thres);    // Eq. 34, tangential
         ndf = (int)df;
         double qv[2][4], qt[2][4];
         const double idt = g.idtan;

@@ -14,6 +14,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <math.h>
+#include <string.h>
 
 // every arithmetic routine also compiles for the host, so its derivatives can be checked there
 #define DFK_HD __host__ __device__ __forceinline__
@@ -22,6 +23,36 @@ namespace dfk {
 
 constexpr int G = 3;                       // ghost layers: the normal stencil spans i-3 .. i+2
 constexpr double kGaussEta = 0.28867513459481288225;   // sqrt(3)/6: Gauss points at eta = -/+ this
+
+// Order of doubles on their bit patterns.  Read as signed 64-bit integers, the IEEE encodings of
+// +0 .. +inf compare as the values do, and every negative value (-0 included) reads as negative.
+// Maxima, minima and tests of quantities that are never negative (WENO ratios and weight sums, DF
+// factors, products of positive states) run on the integer units this way, leaving the FP64 units
+// (two per SM) to the arithmetic; the results are the same bits as fmax / fmin / < on such values.
+DFK_HD long long dbits(double x) {
+#ifdef __CUDA_ARCH__
+    return __double_as_longlong(x);
+#else
+    long long b;
+    memcpy(&b, &x, sizeof b);
+    return b;
+#endif
+}
+DFK_HD double dval(long long b) {
+#ifdef __CUDA_ARCH__
+    return __longlong_as_double(b);
+#else
+    double x;
+    memcpy(&x, &b, sizeof x);
+    return x;
+#endif
+}
+DFK_HD double nn_max(double a, double b) { const long long x = dbits(a), y = dbits(b); return dval(x > y ? x : y); }
+DFK_HD double nn_min(double a, double b) { const long long x = dbits(a), y = dbits(b); return dval(x < y ? x : y); }
+// a < b for a >= +0 (b of any sign)
+DFK_HD bool nn_less(double a, double b) { return dbits(a) < dbits(b); }
+// lo < a < hi for lo, hi > 0: false for a negative, -0 or NaN
+DFK_HD bool in_range(double a, double lo, double hi) { const long long x = dbits(a); return dbits(lo) < x && x < dbits(hi); }
 
 struct SchemeConsts {
     double gamma, gm1, K, inv_K2;          // gamma, gamma-1, internal degrees of freedom, 1/(K+2)
@@ -268,8 +299,8 @@ DFK_HD AOCore ao_core(const double q[5], const double a2s_q[3], const SchemeCons
     const double e0 = b0 + S.eps, e1 = b1 + S.eps, e2 = b2 + S.eps, e3 = b3 + S.eps;
     const double p01 = e0 * e1, p23 = e2 * e3, prod = p01 * p23;
     const double t0 = tau * (e1 * p23), t1 = tau * (e0 * p23), t2 = tau * (p01 * e3), t3 = tau * (p01 * e2);
-    const double tmax = fmax(fmax(t0, t1), fmax(t2, t3)), tmin = fmin(fmin(t0, t1), fmin(t2, t3));
-    if (prod < 1e150 && tmax < 1e150) {
+    const double tmax = nn_max(nn_max(t0, t1), nn_max(t2, t3)), tmin = nn_min(nn_min(t0, t1), nn_min(t2, t3));
+    if (nn_less(prod, 1e150) && nn_less(tmax, 1e150)) {
         const double p2 = prod * prod;
         c.v[0] = S.d[0] * (p2 + t0 * t0); c.v[1] = S.d[1] * (p2 + t1 * t1);
         c.v[2] = S.d[2] * (p2 + t2 * t2); c.v[3] = S.d[3] * (p2 + t3 * t3);
@@ -278,7 +309,7 @@ DFK_HD AOCore ao_core(const double q[5], const double a2s_q[3], const SchemeCons
         const double r0 = tau / e0, r1 = tau / e1, r2 = tau / e2, r3 = tau / e3;
         c.v[0] = S.d[0] * (1.0 + r0 * r0); c.v[1] = S.d[1] * (1.0 + r1 * r1);
         c.v[2] = S.d[2] * (1.0 + r2 * r2); c.v[3] = S.d[3] * (1.0 + r3 * r3);
-        c.rmax = fmax(fmax(r0, r1), fmax(r2, r3)); c.rmin = fmin(fmin(r0, r1), fmin(r2, r3)); c.rs = 1.0;
+        c.rmax = nn_max(nn_max(r0, r1), nn_max(r2, r3)); c.rmin = nn_min(nn_min(r0, r1), nn_min(r2, r3)); c.rs = 1.0;
     }
     c.sum = (c.v[0] + c.v[1]) + (c.v[2] + c.v[3]);
     return c;
@@ -308,7 +339,7 @@ DFK_HD AO ao_finish(const AOCore& c, double iv, const SchemeConsts& S) {
 // [1e-50, 1e150] on the scaled branch, so the product neither overflows nor underflows)
 DFK_HD void ao_finish_pair(const AOCore& a, const AOCore& b, const SchemeConsts& S, AO& oa, AO& ob) {
     double ia, ib;
-    if (a.sum < 1e150 && b.sum < 1e150) {
+    if (nn_less(a.sum, 1e150) && nn_less(b.sum, 1e150)) {
         const double r = 1.0 / (a.sum * b.sum);
         ia = b.sum * r;
         ib = a.sum * r;
@@ -415,7 +446,7 @@ DFK_HD Maxw maxw_of(const double W[4], const SchemeConsts& S) {
 // is divided side by side as in maxw_of.
 DFK_HD void maxw_pair(const double WL[4], const double WR[4], const SchemeConsts& S, Maxw& a, Maxw& b) {
     const double rr = WL[0] * WR[0];
-    if (rr > 1e-150 && rr < 1e150) {
+    if (in_range(rr, 1e-150, 1e150)) {
         const double r = 1.0 / rr;
         maxw_velocities(WL, WR[0] * r, S, a);
         maxw_velocities(WR, WL[0] * r, S, b);
@@ -424,7 +455,7 @@ DFK_HD void maxw_pair(const double WL[4], const double WR[4], const SchemeConsts
         maxw_velocities(WR, 1.0 / WR[0], S, b);
     }
     const double pp = a.p * b.p;
-    if (pp > 1e-150 && pp < 1e150) {
+    if (in_range(pp, 1e-150, 1e150)) {
         const double r = 1.0 / pp;
         maxw_finish(WL[0] * b.p * r, S, a);
         maxw_finish(WR[0] * a.p * r, S, b);
@@ -453,8 +484,9 @@ DFK_HD void fill_moments(const Maxw& s, double K, Mom& m) {
 #else
         double h = 0.5 * erfc(fabs(x));
 #endif
-        if (HALF > 0) { m.mu[0] = x >= 0.0 ? 1.0 - h : h; m.mu[1] = s.U * m.mu[0] + e; }   // erfc(-x) / 2
-        else          { m.mu[0] = x >= 0.0 ? h : 1.0 - h; m.mu[1] = s.U * m.mu[0] - e; }   // erfc(x) / 2
+        const bool xpos = dbits(x) >= 0;                      // x >= +0 (at -0 both forms give 1/2)
+        if (HALF > 0) { m.mu[0] = xpos ? 1.0 - h : h; m.mu[1] = s.U * m.mu[0] + e; }   // erfc(-x) / 2
+        else          { m.mu[0] = xpos ? h : 1.0 - h; m.mu[1] = s.U * m.mu[0] - e; }   // erfc(x) / 2
     }
 #pragma unroll
     for (int n = 2; n < 7; ++n) m.mu[n] = s.U * m.mu[n - 1] + (double)(n - 1) * s.il2 * m.mu[n - 2];
@@ -595,7 +627,7 @@ DFK_HD void gks_flux_t(const GPState& L, const GPState& R, const Maxw& sl, const
     double idt, ips;
     {
         const double a = Wc[0] * dt;
-        if (a > 1e-150 && a < 1e150) {
+        if (in_range(a, 1e-150, 1e150)) {
             const double r = 1.0 / a;
             maxw_velocities(Wc, dt * r, S, sc);
             idt = Wc[0] * r;
@@ -604,7 +636,7 @@ DFK_HD void gks_flux_t(const GPState& L, const GPState& R, const Maxw& sl, const
             idt = 1.0 / dt;
         }
         const double ps = sl.p + sr.p, b = sc.p * ps;
-        if (b > 1e-150 && b < 1e150) {
+        if (in_range(b, 1e-150, 1e150)) {
             const double r = 1.0 / b;
             maxw_finish(Wc[0] * ps * r, S, sc);
             ips = sc.p * r;
@@ -654,7 +686,7 @@ DFK_HD void gks_flux_t(const GPState& L, const GPState& R, const Maxw& sl, const
     double T = rT * dt;
     double tau = (S.tau_reading == 1) ? T : 0.0;
     double E2 = 0.0, r = 0.0;
-    if (rT > 0.0) { E2 = exp(-0.5 / rT); r = rT; }
+    if (dbits(rT) > 0) { E2 = exp(-0.5 / rT); r = rT; }   // rT >= 0
     double E1 = E2 * E2;
     double om = 1.0 - E2;
     double S3 = om * (3.0 - E2);                       // 3 - 4 E2 + E1
