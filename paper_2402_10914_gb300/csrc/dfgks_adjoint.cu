@@ -123,7 +123,7 @@ DFK_HD void ka_faces_body(const Mesh& m, const SchemeConsts& S, const double* __
     const int ncell = f - 1 + side;
     double al[3];
     for (int b = 0; b < 3; ++b) al[b] = alpha[g.cell(m, ncell, t + Geo<DIR>::sigma * (b - 1))];
-    const bool df = fmax(fmax(al[0], al[1]), al[2]) < S.alpha_thres;
+    const bool df = nn_less(nn_max(nn_max(al[0], al[1]), al[2]), S.alpha_thres);
     const double idt = g.idtan;
     const long long e = (long long)side * g.nfaces() + g.face(f, t);
     const int fbits = (int)gp[GP_FB * gs + e];
@@ -223,8 +223,8 @@ DFK_HD void ka_lines_body(const Mesh& m, const SchemeConsts& S, const double* __
     CharBasis B = make_basis(Wc[2], Wc[3], S);
     double Q[6][4];
     for (int s = 0; s < 6; ++s) project(B, Wc[s], Q[s]);
-    const bool dfL = fmax(fmax(al[1], al[2]), al[3]) < S.alpha_thres;
-    const bool dfR = fmax(fmax(al[2], al[3]), al[4]) < S.alpha_thres;
+    const bool dfL = nn_less(nn_max(nn_max(al[1], al[2]), al[3]), S.alpha_thres);
+    const bool dfR = nn_less(nn_max(nn_max(al[2], al[3]), al[4]), S.alpha_thres);
     const double idn = g.idn;
     // the reconstruction that set the limiter weight in the forward pass (2k + side) and the
     // weight's adjoint

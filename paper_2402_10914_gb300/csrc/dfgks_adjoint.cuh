@@ -527,7 +527,7 @@ DFK_HD TimeCoeffs time_coeffs(double rT, double dt, int tau_reading) {
     Dual T = dscale(dt, r);
     Dual tau = tau_reading == 1 ? T : Dual{0.0, 0.0};
     Dual E2 = {0.0, 0.0}, rr = {0.0, 0.0};
-    if (rT > 0.0) { double e = exp(-0.5 / rT); E2 = Dual{e, e * 0.5 / (rT * rT)}; rr = r; }
+    if (dbits(rT) > 0) { double e = exp(-0.5 / rT); E2 = Dual{e, e * 0.5 / (rT * rT)}; rr = r; }
     Dual E1 = dmul(E2, E2);
     Dual om = dsub(Dual{1.0, 0.0}, E2);
     Dual S3 = dmul(om, dsub(Dual{3.0, 0.0}, E2));
@@ -867,7 +867,7 @@ DFK_HD void lf_flux_vjp(const GPState& L, const GPState& R, const SchemeConsts& 
                         const double dFb[4], GPStateBar& Lb, GPStateBar& Rb) {
     EulerPt el = euler_pt(L.W, S), er = euler_pt(R.W, S);
     double sL = fabs(el.u) + el.c, sR = fabs(er.u) + er.c;
-    bool left = !(sL < sR);                       // fmax / std::max keep the first argument on a tie
+    bool left = !nn_less(sL, sR);                 // the left speed on a tie (both >= 0)
     double s = left ? sL : sR;
     double t1[4], t2[4], WtL[4], WtR[4];
     jac_x(el, S.gm1, L.Wn, t1); jac_y(el, S.gm1, L.Wt, t2);

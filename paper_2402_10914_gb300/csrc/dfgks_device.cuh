@@ -196,11 +196,11 @@ DFK_HD AO weno_ao_t(const double q[5], const SchemeConsts& S, const Tape& tp, in
     double p01 = e0 * e1, p23 = e2 * e3, prod = p01 * p23;
     const double P0 = e1 * p23, P1 = e0 * p23, P2 = p01 * e3, P3 = p01 * e2;
     const double t0 = tau * P0, t1 = tau * P1, t2 = tau * P2, t3 = tau * P3;     // prod * r_k
-    const double tmax = fmax(fmax(t0, t1), fmax(t2, t3)), tmin = fmin(fmin(t0, t1), fmin(t2, t3));
+    const double tmax = nn_max(nn_max(t0, t1), nn_max(t2, t3)), tmin = nn_min(nn_min(t0, t1), nn_min(t2, t3));
     AO o;
     double c0, c1, c2, c3;
     double r0, r1, r2, r3;                           // the ratios themselves: tape and fallback only
-    if (prod < 1e150 && tmax < 1e150) {              // beta+eps >= eps, so prod >= eps^4 > 0
+    if (nn_less(prod, 1e150) && nn_less(tmax, 1e150)) {   // beta+eps >= eps, so prod >= eps^4 > 0
         const double p2 = prod * prod;
         const double v0 = S.d[0] * (p2 + t0 * t0), v1 = S.d[1] * (p2 + t1 * t1);
         const double v2 = S.d[2] * (p2 + t2 * t2), v3 = S.d[3] * (p2 + t3 * t3);
@@ -225,7 +225,7 @@ DFK_HD AO weno_ao_t(const double q[5], const SchemeConsts& S, const Tape& tp, in
         c3 = w3 * iw * S.inv_d3;
         c0 = w0 * iw - c3 * S.d[0]; c1 = w1 * iw - c3 * S.d[1]; c2 = w2 * iw - c3 * S.d[2];
         // tau >= 0, so the ratio is largest at beta_min and smallest at beta_max
-        o.rmax = fmax(fmax(r0, r1), fmax(r2, r3)); o.rmin = fmin(fmin(r0, r1), fmin(r2, r3)); o.rs = 1.0;
+        o.rmax = nn_max(nn_max(r0, r1), nn_max(r2, r3)); o.rmin = nn_min(nn_min(r0, r1), nn_min(r2, r3)); o.rs = 1.0;
     }
     if constexpr (Tape::active) {
         // the reverse differentiates w_k = d_k (1 + r_k^2) and c_k = w_k / sum w - c_3 d_k
@@ -240,7 +240,7 @@ DFK_HD AO weno_ao_t(const double q[5], const SchemeConsts& S, const Tape& tp, in
         int kmax = 0, kmin = 0;
         const double rr[4] = {r0, r1, r2, r3};
 #pragma unroll
-        for (int k = 1; k < 4; ++k) { if (rr[k] > rr[kmax]) kmax = k; if (rr[k] < rr[kmin]) kmin = k; }
+        for (int k = 1; k < 4; ++k) { if (nn_less(rr[kmax], rr[k])) kmax = k; if (nn_less(rr[k], rr[kmin])) kmin = k; }
         tp.put(base + AT_KMAX, (double)kmax);
         tp.put(base + AT_KMIN, (double)kmin);
     }
@@ -779,7 +779,7 @@ DFK_HD void lf_flux(const GPState& L, const GPState& R, const SchemeConsts& S,
     EulerPt el = euler_pt(L.W, S), er = euler_pt(R.W, S);
     double FL[4] = {L.W[1], L.W[1] * el.u + el.p, L.W[1] * el.v, el.u * (L.W[3] + el.p)};
     double FR[4] = {R.W[1], R.W[1] * er.u + er.p, R.W[1] * er.v, er.u * (R.W[3] + er.p)};
-    double s = fmax(fabs(el.u) + el.c, fabs(er.u) + er.c);
+    double s = nn_max(fabs(el.u) + el.c, fabs(er.u) + er.c);
     double t1[4], t2[4], WtL[4], WtR[4], AL[4], AR[4];
     jac_x(el, S.gm1, L.Wn, t1); jac_y(el, S.gm1, L.Wt, t2);
 #pragma unroll
@@ -814,12 +814,15 @@ DFK_HD double df_alpha(const double WL[4], const double WR[4], const SchemeConst
     return df_alpha_maxw(l, r, S);
 }
 
+// 0 < x <= +inf on the bit pattern (false for negatives, zeros and NaN)
+DFK_HD bool positive_bits(double x) { const long long b = dbits(x); return b > 0 && b <= 0x7FF0000000000000LL; }
+
 DFK_HD bool physical_state(const double W[4], double gm1) {
-    if (!(W[0] > 0.0)) return false;
+    if (!positive_bits(W[0])) return false;
     // p > 0 tested as rho p = (gamma - 1) (rho E - |rho u|^2 / 2) > 0: the same sign for rho > 0,
     // without a division
     double rp = gm1 * (W[0] * W[3] - 0.5 * (W[1] * W[1] + W[2] * W[2]));
-    return rp > 0.0;
+    return positive_bits(rp);
 }
 
 }  // namespace dfk

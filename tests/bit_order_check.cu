@@ -1,6 +1,7 @@
 // Host check of the bit-pattern order helpers of dfgks_device.cuh (nn_max, nn_min, nn_less,
-// in_range) against fmax, fmin and <: bit for bit on non-negative values (zero, subnormals, normals,
-// the overflow guards' bounds, infinity), and in_range on values of any sign, -0 and NaN included.
+// in_range, positive_bits) against fmax, fmin, < and >: bit for bit on non-negative values (zero,
+// subnormals, normals, the overflow guards' bounds, infinity), and in_range and positive_bits on
+// values of any sign, -0 and NaN included.
 // Prints the number of mismatches; exit status 1 if there is any.
 #include <cstdio>
 #include <cstdint>
@@ -43,8 +44,9 @@ int main() {
     const double probes[] = {-1.0, -0.0, 0.0, 1e-200, 1e-150, 2e-150, 1.0, 1e149, 1e150, 1e151, -1e150,
                              INFINITY, -INFINITY, NAN, -NAN};
     for (double a : probes) {
-        ++n;
+        n += 2;
         if (in_range(a, 1e-150, 1e150) != (a > 1e-150 && a < 1e150)) ++bad;
+        if (positive_bits(a) != (a > 0.0)) ++bad;
     }
     printf("%ld mismatches in %ld comparisons\n", bad, n);
     return bad ? 1 : 0;
