@@ -455,9 +455,11 @@ def bench_blast(args):
 def bench_robustness(args):
     """Sect. 4.3 robustness measure: the largest Mach number at which a run keeps positivity, for
     the hybrid (DF + WENO-AO) and the plain WENO-AO reconstruction (alpha_thres = 0: the DF branch
-    never fires), GKS (S2O4) and L-F (SSP-RK3), with and without the Gauss-point fallback, on the
-    123 problem, the hurricane-like flow and the planar rarefactions (Tables 3-5).  Found by
-    bisection in log Mach between 1 and 256 (12 halvings; the planar rarefactions from 0.5)."""
+    never fires), and for the hybrid with the DF states taken from the cell averages beside each
+    face (df_states = 1, an alternative to the paper's reading), GKS (S2O4) and L-F (SSP-RK3), with
+    and without the Gauss-point fallback, on the 123 problem, the hurricane-like flow and the
+    planar rarefactions (Tables 3-5).  Found by bisection in log Mach between 1 and 256 (12
+    halvings; the planar rarefactions from 0.5)."""
     import torch
     from paper_2402_10914_gb300 import _lib, inputs as I
     from paper_2402_10914_gb300.solver import Solver
