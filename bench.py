@@ -455,8 +455,9 @@ def bench_blast(args):
 def bench_robustness(args):
     """Sect. 4.3 robustness measure: the largest Mach number at which a run keeps positivity, for
     the hybrid (DF + WENO-AO) and the plain WENO-AO reconstruction (alpha_thres = 0: the DF branch
-    never fires), and for the hybrid with the DF states taken from the cell averages beside each
-    face (df_states = 1, an alternative to the paper's reading), GKS (S2O4) and L-F (SSP-RK3), with
+    never fires), for the hybrid with the DF states taken from the cell averages beside each face
+    (df_states = 1, an alternative to the paper's reading) and for the hybrid with alpha^{n+1} from a
+    reconstruction of W^{n+1} (alpha_source = 1), GKS (S2O4) and L-F (SSP-RK3), with
     and without the Gauss-point fallback, on the 123 problem, the hurricane-like flow and the
     planar rarefactions (Tables 3-5).  Found by bisection in log Mach between 1 and 256 (12
     halvings; the planar rarefactions from 0.5)."""
@@ -464,9 +465,9 @@ def bench_robustness(args):
     from paper_2402_10914_gb300 import _lib, inputs as I
     from paper_2402_10914_gb300.solver import Solver
 
-    def survives(make, ma, flux, thres, fb, dfs=0):
+    def survives(make, ma, flux, thres, fb, dfs=0, asrc=0):
         w = make(ma, flux=flux)
-        s = w.settings.with_(alpha_thres=thres, gp_fallback=fb, df_states=dfs)
+        s = w.settings.with_(alpha_thres=thres, gp_fallback=fb, df_states=dfs, alpha_source=asrc)
         with Solver(s) as sol:
             try:
                 sol.set_ic(w.W0)
@@ -485,19 +486,22 @@ def bench_robustness(args):
                        ("hurricane-like (400 x 400, 50 steps)", I.hurricane),
                        ("planar rarefactions (400 x 400, t = 0.15)", I.planar_rarefaction)):
         for flux, fname in ((I.GKS, "GKS S2O4"), (I.LF, "L-F SSP-RK3")):
-            # the hybrid with the paper's DF states, plain WENO-AO, and the hybrid with the DF factor
+            # the hybrid with the paper's DF states, plain WENO-AO, the hybrid with the DF factor
             # taken from the cell averages beside each face (df_states = 1, not the paper's reading)
-            for thres, rname, dfs in ((0.5, "hybrid", 0), (0.0, "WENO-AO", 0), (0.5, "hybrid, DF from cell averages", 1)):
+            # and the hybrid with alpha^{n+1} from a reconstruction of W^{n+1} (alpha_source = 1)
+            for thres, rname, dfs, asrc in ((0.5, "hybrid", 0, 0), (0.0, "WENO-AO", 0, 0),
+                                            (0.5, "hybrid, DF from cell averages", 1, 0),
+                                            (0.5, "hybrid, DF updated from W^{n+1}", 0, 1)):
                 for fb in (0, 1):
                     lo, hi = (0.5 if make is I.planar_rarefaction else 1.0), 256.0
-                    if not survives(make, lo, flux, thres, fb, dfs):
+                    if not survives(make, lo, flux, thres, fb, dfs, asrc):
                         res = "< %g" % lo
-                    elif survives(make, hi, flux, thres, fb, dfs):
+                    elif survives(make, hi, flux, thres, fb, dfs, asrc):
                         res = ">= 256"
                     else:
                         for _ in range(12):
                             mid = math.sqrt(lo * hi)
-                            if survives(make, mid, flux, thres, fb, dfs):
+                            if survives(make, mid, flux, thres, fb, dfs, asrc):
                                 lo = mid
                             else:
                                 hi = mid

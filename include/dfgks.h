@@ -73,6 +73,12 @@ typedef struct dfgks_config {
                                       0 the reconstructed Gauss-point states (the paper's interface
                                       reconstruction values; default), 1 the cell averages of the two
                                       cells beside the face (an alternative, not the paper's reading) */
+    int alpha_source;              /* where alpha^{n+1} comes from (Alg. 1 "update DF factor", Sect. 3.2):
+                                      0 the Gauss-point states of the step's last stage (default), 1 one
+                                      more reconstruction after the stages, of W^{n+1} itself with alpha^n
+                                      deciding its DF branches (an extra face-line and tangential sweep
+                                      per step).  Single-problem handle only: the batch and the block
+                                      decomposition refuse 1 with DFGKS_EINVAL */
 } dfgks_config;
 
 typedef struct dfgks dfgks;        /* opaque; owns every device buffer it uses */

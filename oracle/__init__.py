@@ -44,7 +44,8 @@ class Cfg(C.Structure):
                 ("alpha_thres", C.c_double), ("dH", C.c_double), ("dL", C.c_double),
                 ("eps", C.c_double), ("C1", C.c_double), ("C2", C.c_double),
                 ("flux", C.c_int), ("time_limiter", C.c_int), ("tau_reading", C.c_int),
-                ("gp_fallback", C.c_int), ("time_scheme", C.c_int), ("dt_rule", C.c_int), ("df_states", C.c_int)]
+                ("gp_fallback", C.c_int), ("time_scheme", C.c_int), ("dt_rule", C.c_int), ("df_states", C.c_int),
+                ("alpha_source", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -108,7 +109,8 @@ def make_cfg(s) -> Cfg:
     """Build the oracle's configuration from an ``inputs.Settings`` (or any object with its fields)."""
     c = Cfg()
     for f in ("nx", "ny", "x0", "x1", "y0", "y1", "gamma", "cfl", "alpha_thres", "dH", "dL", "eps", "C1", "C2",
-              "flux", "time_limiter", "tau_reading", "gp_fallback", "time_scheme", "dt_rule", "df_states"):
+              "flux", "time_limiter", "tau_reading", "gp_fallback", "time_scheme", "dt_rule", "df_states",
+              "alpha_source"):
         setattr(c, f, getattr(s, f))
     for k in range(4):
         c.bc[k] = int(s.bc[k])

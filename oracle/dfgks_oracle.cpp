@@ -71,6 +71,8 @@ typedef struct {
     int dt_rule;          // 0: per-direction minimum, 1: CFL / max((|U|+c)/dx + (|V|+c)/dy)
     int df_states;        // left/right states of a Gauss point's DF factor: 0 the reconstructed
                           // Gauss-point states, 1 the cell averages beside the face
+    int alpha_source;     // alpha^{n+1}: 0 from the last stage's Gauss points, 1 from a reconstruction
+                          // of W^{n+1} itself with alpha^n deciding its DF branches
 } oracle_cfg;
 
 typedef struct {
@@ -1375,6 +1377,17 @@ int oracle_run(const oracle_cfg* cfg, double* W, double* alpha, double* t, int n
             }
             const Counters* cs[3] = {&o1.cnt, &o2.cnt, &o3.cnt};
             for (const Counters* c : cs) { local.fallbacks += c->fallbacks; local.df_normal += c->df_n; local.df_tangential += c->df_t; }
+        }
+        // alpha_source = 1: Algorithm 1's "update DF" read as one more reconstruction after the
+        // stages, of W^{n+1} itself, its DF branches (Eq. 34) decided by alpha^n; alpha^{n+1} is
+        // the product of that reconstruction's Gauss-point factors (Sect. 3.2).  Its branches and
+        // fallbacks are not counted: no flux comes from it.
+        if (!fail && cfg->alpha_source == 1) {
+            Field<double> Fp = Fnext;                  // Fnext kept alpha^n from its copy of Fn
+            fill_ghosts(C, Fp, true);
+            StageOut<double> op;
+            stage_operator(C, Fp, dt, false, op);
+            a_next = op.alpha_next;
         }
         if (fail) { local.fail_step = done; local.fail_i = fi; local.fail_j = fj; rc = 5; break; }
         for (int k = 0; k < 4; ++k) Fn.w[k] = Fnext.w[k];

@@ -23,7 +23,8 @@ class Config(C.Structure):
                 ("alpha_thres", C.c_double), ("dH", C.c_double), ("dL", C.c_double), ("eps", C.c_double),
                 ("C1", C.c_double), ("C2", C.c_double),
                 ("time_limiter", C.c_int), ("tau_reading", C.c_int), ("gp_fallback", C.c_int),
-                ("time_scheme", C.c_int), ("dt_rule", C.c_int), ("df_states", C.c_int)]
+                ("time_scheme", C.c_int), ("dt_rule", C.c_int), ("df_states", C.c_int),
+                ("alpha_source", C.c_int)]
 
 
 class Counters(C.Structure):

@@ -348,7 +348,7 @@ static bool batch_config_ok(const dfgks_config* c) {
     if ((c->bc_xlo != 1 || c->bc_xhi != 1) && c->nx < G) return false;
     if ((c->bc_ylo != 1 || c->bc_yhi != 1) && c->ny < G) return false;
     return c->time_scheme == 0 && (c->tau_reading == 0 || c->tau_reading == 1) && (c->dt_rule == 0 || c->dt_rule == 1)
-        && (c->df_states == 0 || c->df_states == 1);
+        && (c->df_states == 0 || c->df_states == 1) && c->alpha_source == 0;
 }
 
 extern "C" DFGKS_API dfgks_status dfgks_batch_create(const dfgks_config* cfgs, const int* flux, int np, void* stream,

@@ -94,6 +94,7 @@ extern "C" dfgks_status dfgks_config_default(dfgks_config* c, int nx, int ny) {
     c->time_limiter = 1; c->tau_reading = 0; c->gp_fallback = 1; c->time_scheme = DFGKS_TIME_S2O4;
     c->dt_rule = 0;
     c->df_states = 0;
+    c->alpha_source = 0;
     return DFGKS_OK;
 }
 
@@ -114,6 +115,7 @@ static bool config_ok(const dfgks_config* c) {
     if (c->tau_reading != 0 && c->tau_reading != 1) return false;
     if (c->dt_rule != 0 && c->dt_rule != 1) return false;
     if (c->df_states != 0 && c->df_states != 1) return false;
+    if (c->alpha_source != 0 && c->alpha_source != 1) return false;
     return true;
 }
 
@@ -383,6 +385,18 @@ static void enqueue_step(dfgks* h, int s, double dt, int flux, double t_end, int
         launch_sweep_xy(m, S, flux, false, out, ain, dtp, h->B, h->By, h->st, halt, st, T);
         a.Wn = in; a.Win = out; a.Wout = out; a.alpha_out = aout;
         launch_update(UM_RK_3, m, S, a, h->B, dtp, h->st, halt, st, T);
+    }
+    if (h->cfg.alpha_source == 1) {
+        // alpha^{n+1} from one more reconstruction, of W^{n+1} itself with alpha^n deciding its DF
+        // branches (Alg. 1 "update DF factor" read as a pass after the stages): the alpha-only sweep
+        // of alpha^0 on the new state, overwriting the last stage's product.  No counters (no flux
+        // comes from it); a halted step skips it.
+        launch_fill_ghosts(m, out, ain, halt, st, T);
+        launch_sweep_xy(m, S, DFGKS_FLUX_LF, true, out, ain, dtp, h->B, h->By, nullptr, halt, st, T);
+        UpdateArgs aa;
+        memset(&aa, 0, sizeof(aa));
+        aa.alpha_out = aout;
+        launch_update(UM_ALPHA, m, S, aa, h->B, dtp, nullptr, halt, st, T);
     }
     launch_end_step(h->st, t_end, st, T);
 }

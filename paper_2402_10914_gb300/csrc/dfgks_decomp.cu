@@ -60,7 +60,7 @@ bool decomp_config_ok(const dfgks_config* c, int px, int py) {
     if (py == 1 && (c->bc_ylo != 1 || c->bc_yhi != 1) && c->ny < G) return false;
     if (c->time_scheme != DFGKS_TIME_S2O4) return false;
     return (c->tau_reading == 0 || c->tau_reading == 1) && (c->dt_rule == 0 || c->dt_rule == 1)
-        && (c->df_states == 0 || c->df_states == 1);
+        && (c->df_states == 0 || c->df_states == 1) && c->alpha_source == 0;
 }
 
 void make_plan(const dfgks_config* c, int px, int py, int b, dfgks_block_plan* p) {

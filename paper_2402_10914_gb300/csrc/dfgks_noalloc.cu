@@ -61,6 +61,7 @@ bool valid(const dfgks_config* c) {
     if ((c->bc_ylo != 1 || c->bc_yhi != 1) && c->ny < G) return false;
     if (c->tau_reading != 0 && c->tau_reading != 1) return false;
     if (c->df_states != 0 && c->df_states != 1) return false;
+    if (c->alpha_source != 0 && c->alpha_source != 1) return false;    // a step option; no stage effect
     return true;
 }
 

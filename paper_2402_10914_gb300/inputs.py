@@ -65,6 +65,7 @@ class Settings:
     time_scheme: int = S2O4
     dt_rule: int = 0
     df_states: int = 0                 # DF factor from 0: Gauss-point states, 1: the face's cell averages
+    alpha_source: int = 0              # alpha^{n+1} from 0: the last stage, 1: a reconstruction of W^{n+1}
 
     def with_(self, **kw) -> "Settings":
         return replace(self, **kw)

@@ -19,7 +19,8 @@ def make_config(s: Settings) -> _lib.Config:
     c = _lib.Config()
     _lib.check(_lib.lib().dfgks_config_default(C.byref(c), int(s.nx), int(s.ny)), "dfgks_config_default")
     for f in ("nx", "ny", "x0", "x1", "y0", "y1", "gamma", "cfl", "alpha_thres", "dH", "dL", "eps", "C1", "C2",
-              "time_limiter", "tau_reading", "gp_fallback", "time_scheme", "dt_rule", "df_states"):
+              "time_limiter", "tau_reading", "gp_fallback", "time_scheme", "dt_rule", "df_states",
+              "alpha_source"):
         setattr(c, f, getattr(s, f))
     c.bc_xlo, c.bc_xhi, c.bc_ylo, c.bc_yhi = (int(b) for b in s.bc)
     return c

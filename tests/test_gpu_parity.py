@@ -550,6 +550,29 @@ def test_full_run_parity_resolution_workloads(name):
     assert W[0].min() > 0 and p.min() > 0
 
 
+@pytest.mark.parametrize("name", ["quadrants", "p123_gks", "p123_lf"])
+def test_steps_parity_alpha_from_the_new_state(name):
+    # the alternative DF update (alpha_source = 1: alpha^{n+1} from a reconstruction of W^{n+1} with
+    # alpha^n): three steps against the oracle running the same reading -- state, alpha and the
+    # branch counters (the extra reconstruction counts none on either side)
+    if name == "quadrants":
+        w = I.quadrants(96, seed=3)
+    elif name == "p123_gks":
+        w = I.problem_123(3.0, flux=I.GKS)
+    else:
+        w = I.problem_123(3.0, flux=I.LF)
+    w.settings = w.settings.with_(alpha_source=1)
+    (rc, Wo, ao, to, dts_o, st), (done, W, a, t, dts, cnt) = run_both(w, 3)
+    assert rc == 0 and done == 3
+    err = comp_rel_err(W, Wo)
+    if err > 1e-12:
+        _, env, _ = oracle_envelope(w.settings, w.W0, 3)
+        assert err <= 10.0 * env, (err, env)
+    assert comp_rel_err(a[None], ao[None], floor_frac=1e-12) <= 1e-10
+    assert cnt["df_normal"] == st.df_normal and cnt["df_tangential"] == st.df_tangential
+    assert cnt["fallbacks"] == st.fallbacks
+
+
 @pytest.mark.parametrize("name", ["quadrants", "p123_gks", "p123_lf", "blast"])
 def test_one_step_parity_df_from_cell_averages(name):
     # the alternative DF-state reading (df_states = 1): one step against the oracle with the same

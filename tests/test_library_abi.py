@@ -126,8 +126,28 @@ INVALID = {
     "dL_above_one": dict(dL=1.5), "C2_negative": dict(C2=-1.0), "bc_unknown": dict(bc_yhi=3),
     "periodic_one_side": dict(bc_xlo=0), "periodic_two_cells": dict(nx=2, bc_xlo=0, bc_xhi=0),
     "wall_two_cells": dict(ny=2, bc_ylo=2), "tau_reading_2": dict(tau_reading=2), "time_scheme_5": dict(time_scheme=5),
-    "dt_rule_2": dict(dt_rule=2),
+    "dt_rule_2": dict(dt_rule=2), "df_states_2": dict(df_states=2), "alpha_source_2": dict(alpha_source=2),
 }
+
+
+def test_batch_and_decomposition_refuse_alpha_from_the_new_state(libpath):
+    # alpha_source = 1 is built for the single-problem handle only: the batch and the block
+    # decomposition refuse it with EINVAL before any CUDA call (so this runs without a GPU)
+    import ctypes
+    from paper_2402_10914_gb300 import _lib
+    L = _lib.lib()
+    cfg = _lib.Config()
+    assert L.dfgks_config_default(ctypes.byref(cfg), 16, 16) == 0
+    cfg.alpha_source = 1
+    cfgs = (_lib.Config * 1)(cfg)
+    flux = (ctypes.c_int * 1)(0)
+    b = ctypes.c_void_p(1234)
+    assert L.dfgks_batch_create(ctypes.cast(cfgs, ctypes.c_void_p), ctypes.cast(flux, ctypes.c_void_p), 1, None,
+                                ctypes.byref(b)) == _lib.EINVAL
+    assert b.value is None
+    d = ctypes.c_void_p(1234)
+    assert L.dfgks_decomp_create(ctypes.byref(cfg), 2, 1, None, ctypes.byref(d)) == _lib.EINVAL
+    assert d.value is None
 
 
 @pytest.mark.parametrize("name", list(INVALID))

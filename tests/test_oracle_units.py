@@ -470,3 +470,22 @@ def test_df_factor_from_cell_averages_reading():
                 # the fluxes themselves do not depend on where the DF factor comes from
                 assert np.array_equal(faces[t, f, :8], faces0[t, f, :8])
         assert not np.array_equal(faces[..., 9], faces0[..., 9])
+
+
+def test_alpha_from_a_reconstruction_of_the_new_state():
+    # alpha_source = 1 (an alternative reading of Algorithm 1's "update DF factor"): alpha^{n+1} is
+    # the product of the Gauss-point DF factors (Sect. 3.2) of a reconstruction of W^{n+1} with
+    # alpha^n deciding its DF branches -- the stage operator's alpha_next at (W^{n+1}, alpha^n).
+    # W^{n+1} and dt do not depend on where alpha^{n+1} comes from.  S2O4 (GKS) and SSP-RK3 (L-F).
+    from paper_2402_10914_gb300 import inputs as I
+    for w in (I.problem_123(3.0, flux=I.GKS), I.quadrants(24, seed=2), I.problem_123(3.0, flux=I.LF)):
+        s0 = w.settings
+        s1 = s0.with_(alpha_source=1)
+        a0 = oracle.alpha0(s0, w.W0)
+        rc0, W_0, a_0, _, dts0, _ = oracle.run(s0, w.W0, a0, 1)
+        rc1, W_1, a_1, _, dts1, _ = oracle.run(s1, w.W0, a0, 1)
+        assert rc0 == 0 and rc1 == 0
+        assert np.array_equal(W_0, W_1) and np.array_equal(dts0, dts1)
+        want = oracle.residual(s0, W_1, a0, dts1[0])[3]
+        assert np.array_equal(a_1, want)
+        assert not np.array_equal(a_1, a_0)                  # the two sources differ on this data
