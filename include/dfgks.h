@@ -77,8 +77,9 @@ typedef struct dfgks_config {
                                       0 the Gauss-point states of the step's last stage (default), 1 one
                                       more reconstruction after the stages, of W^{n+1} itself with alpha^n
                                       deciding its DF branches (an extra face-line and tangential sweep
-                                      per step).  Single-problem handle only: the batch and the block
-                                      decomposition refuse 1 with DFGKS_EINVAL */
+                                      per step).  Single-problem stepping only: the batch and the block
+                                      decomposition refuse 1 with DFGKS_EINVAL, the checkpointed forward
+                                      and adjoint with DFGKS_ENOTSUP */
 } dfgks_config;
 
 typedef struct dfgks dfgks;        /* opaque; owns every device buffer it uses */
@@ -177,8 +178,9 @@ DFGKS_API dfgks_status dfgks_adjoint_residual(dfgks* h, const double* W, const d
  * (host) or, if dts_in is NULL, the CFL rule; dts_out[n] (host, may be NULL) receives them.  Keeps W
  * and alpha every ckpt_every steps, the step sizes, and the last segment's stage states and (if they
  * fit in half of the free device memory) its sweep records and tapes, in the handle (allocated on
- * demand, freed by dfgks_destroy) for dfgks_adjoint_checkpointed.  Not part of the paper.  S2O4 only
- * (DFGKS_ENOTSUP otherwise); DFGKS_ENONPOS if the trajectory loses positivity.  Synchronises. */
+ * demand, freed by dfgks_destroy) for dfgks_adjoint_checkpointed.  Not part of the paper.  S2O4 with
+ * alpha_source 0 only (DFGKS_ENOTSUP otherwise, also through dfgks_adjoint_steps); DFGKS_ENONPOS if
+ * the trajectory loses positivity.  Synchronises. */
 DFGKS_API dfgks_status dfgks_forward_checkpointed(dfgks* h, const double* W0, int n, const double* dts_in, int flux,
                                                   int ckpt_every, double* dts_out);
 

@@ -790,6 +790,7 @@ extern "C" dfgks_status dfgks_forward_checkpointed(dfgks* h, const double* W0, i
                                                    int ckpt_every, double* dts_out) {
     if (!h || !W0 || n < 1 || ckpt_every < 1 || (flux != 0 && flux != 1)) return DFGKS_EINVAL;
     if (h->cfg.time_scheme != DFGKS_TIME_S2O4) return DFGKS_ENOTSUP;
+    if (h->cfg.alpha_source != 0) return DFGKS_ENOTSUP;    // the recompute's extra DF pass is not covered
     if (dts_in) for (int s = 0; s < n; ++s) if (!(dts_in[s] > 0.0)) return DFGKS_EINVAL;
     const int k = ckpt_every < n ? ckpt_every : n;
     dfgks_status r = forward_checkpointed(h, W0, n, dts_in, k, flux);
